@@ -1,0 +1,162 @@
+"""Pins of the oracle's part builders (Sec. IV) against hand-derived examples,
+the validity conditions of the acyclic partitioning problem and a brute-force
+minimum on tiny DAGs."""
+import json
+import os
+
+import pytest
+
+import synth
+from oracle import partition as pt
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "partition_examples.json")
+
+
+def _load():
+    with open(GOLDEN) as f:
+        ex = json.load(f)["examples"]
+    for e in ex:
+        e["gates"] = [(g[0], tuple(g[1]), g[2]) for g in e["gates"]]
+    return ex
+
+
+@pytest.mark.parametrize("ex", _load(), ids=lambda e: e["name"])
+def test_hand_examples(ex):
+    n, k, g = ex["n"], ex["k"], ex["gates"]
+    assert pt.nat(g, n, k) == ex["nat_part_of_gate"]
+    assert pt.brute_force_min_parts(g, n, k) == ex["optimum_parts"]
+    for m in ("nat", "dfs", "dagp"):
+        pog = pt.partition(g, n, m, k, seed=1)
+        P = pt.check_partition(g, n, k, pog)
+        assert P >= ex["optimum_parts"]
+    assert max(pt.dagp(g, n, k)) + 1 == ex["optimum_parts"]
+
+
+def test_working_set_example_of_sec4():
+    """Gate A on (q0, q1) and gate B on (q0, q2) need 3 qubits together."""
+    g = [("CX", (0, 1), 0.0), ("CZ", (0, 2), 0.0)]
+    dag = pt.Dag(g, 3)
+    assert pt.working_set(dag, [0, 1]) == 3
+    assert pt.working_set_by_edges(dag, [0, 1]) == 3
+    assert pt.working_set_by_edges(dag, [1]) == 2   # in-edge on q0 + entry of q2
+
+
+def _rand(n, G, seed):
+    r = synth.SplitMix64(seed)
+    out = []
+    for _ in range(G):
+        if r.randint(3) == 0:
+            out.append(("H", (r.randint(n),), 0.0))
+        else:
+            a = r.randint(n)
+            b = (a + 1 + r.randint(n - 1)) % n
+            out.append((("CX", "CZ")[r.randint(2)], (a, b), 0.0))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("k", [2, 3, 4, 6])
+def test_validity_random(seed, k):
+    n = 8
+    g = _rand(n, 150, 1000 + seed)
+    for m in ("nat", "dfs", "dagp"):
+        pog = pt.partition(g, n, m, k, seed=seed)
+        pt.check_partition(g, n, k, pog)
+
+
+def test_validity_workloads():
+    n, g = synth.layered_28q(n=16, depth=12)
+    for k in (4, 8):
+        for m in ("nat", "dfs", "dagp"):
+            pt.check_partition(g, n, k, pt.partition(g, n, m, k, seed=3))
+    n, g = 14, synth.qft(14)
+    for m in ("nat", "dfs", "dagp"):
+        pt.check_partition(g, n, 6, pt.partition(g, n, m, 6, seed=3))
+
+
+def test_brute_force_against_heuristics():
+    """Every builder is >= the optimum; dagP reaches it on most tiny DAGs
+    (the paper reports the optimum on 48 of 52 ILP cases)."""
+    hits = total = 0
+    for seed in range(40):
+        n = 5
+        g = _rand(n, 11, 50 + seed)
+        k = 2 + seed % 3
+        opt = pt.brute_force_min_parts(g, n, k)
+        for m in ("nat", "dfs"):
+            assert max(pt.partition(g, n, m, k, seed=seed)) + 1 >= opt
+        d = max(pt.dagp(g, n, k)) + 1
+        assert d >= opt
+        hits += d == opt
+        total += 1
+    assert hits >= 0.75 * total, (hits, total)
+
+
+def test_brute_force_small_cases():
+    # one gate per part when no two gates fit together
+    g = [("CX", (0, 1), 0.0), ("CX", (1, 2), 0.0), ("CX", (2, 3), 0.0)]
+    assert pt.brute_force_min_parts(g, 4, 2) == 3
+    assert pt.brute_force_min_parts(g, 4, 4) == 1
+    assert pt.brute_force_min_parts(g, 4, 3) == 2
+
+
+def test_arity_error():
+    g = [("CX", (0, 1), 0.0)]
+    for m in ("nat", "dfs", "dagp"):
+        with pytest.raises(pt.PartitionError):
+            pt.partition(g, 2, m, 1)
+    with pytest.raises(pt.PartitionError):
+        pt.Dag([("CX", (0, 0), 0.0)], 2)
+    with pytest.raises(pt.PartitionError):
+        pt.Dag([("H", (5,), 0.0)], 2)
+
+
+def test_schedule_is_min_gate_kahn():
+    g = _rand(6, 60, 77)
+    pog = pt.dagp(g, 6, 3)
+    P = max(pog) + 1
+    first = [min(i for i, p in enumerate(pog) if p == q) for q in range(P)]
+    dag = pt.Dag(g, 6)
+    # whenever two parts are both ready, the one with the smaller first gate runs first:
+    # replay Kahn and compare
+    import heapq
+    succ = [set() for _ in range(P)]
+    for a in range(dag.G):
+        for b in dag.succs[a]:
+            if pog[a] != pog[b]:
+                succ[pog[a]].add(pog[b])
+    indeg = [0] * P
+    for a in range(P):
+        for b in succ[a]:
+            indeg[b] += 1
+    h = [(first[a], a) for a in range(P) if indeg[a] == 0]
+    heapq.heapify(h)
+    order = []
+    while h:
+        _, a = heapq.heappop(h)
+        order.append(a)
+        for b in succ[a]:
+            indeg[b] -= 1
+            if indeg[b] == 0:
+                heapq.heappush(h, (first[b], b))
+    assert order == list(range(P))
+
+
+def test_dfs_deterministic_and_trials():
+    n, g = synth.layered_28q(n=12, depth=8)
+    a = pt.dfs(g, n, 5, seed=11, trials=8)
+    b = pt.dfs(g, n, 5, seed=11, trials=8)
+    assert a == b
+    one = max(pt.dfs(g, n, 5, seed=11, trials=1)) + 1
+    many = max(pt.dfs(g, n, 5, seed=11, trials=8)) + 1
+    assert many <= one
+
+
+def test_dagp_quality_on_layered():
+    """dagP gives no more parts than Nat on the layered and QFT families."""
+    n, g = synth.layered_28q(n=20, depth=20)
+    for k in (6, 10):
+        d = max(pt.dagp(g, n, k)) + 1
+        assert d <= max(pt.nat(g, n, k)) + 1
+    g = synth.qft(16)
+    assert max(pt.dagp(g, 16, 6)) + 1 <= max(pt.nat(g, 16, 6)) + 1
