@@ -1,0 +1,158 @@
+/*
+ * hisvsim.h - C ABI of the GB300 hierarchical state-vector simulator.
+ *
+ * The library applies a quantum circuit to a 2^n-amplitude state vector held
+ * in GPU memory, one HBM pass per part of an acyclic partition of the circuit's
+ * gate DAG (the Gather-Execute-Scatter model of Algorithm 1, Sec. III-C, with
+ * the partitioning problem of Sec. IV-A and the Nat / DFS / dagP builders of
+ * Sec. IV-B). The executor is offered as a library, as the paper does for its
+ * own (Sec. III-D: "general interface for other simulators").
+ *
+ * Conventions shared by every entry point
+ *   - Amplitude x of an n-qubit state is stored at index x = sum_q b_q 2^q
+ *     (little-endian, Sec. II-B / Fig. 1), interleaved (re, im):
+ *     SV_C64 = two floats (8 bytes), SV_C128 = two doubles (16 bytes).
+ *   - Handles (sv_state, sv_plan, sv_batch) are opaque, created and destroyed
+ *     by the caller, and not thread-safe: one thread uses a handle at a time.
+ *   - Device work is stream-ordered on the state's CUDA stream and the call
+ *     returns once it is enqueued, unless the entry point says it synchronises.
+ *     A device fault surfaces as SV_ERR_CUDA at the next synchronising call.
+ *   - No entry point throws; every one returns an sv_status, and on a status
+ *     other than SV_OK sv_last_error() describes it (thread-local string).
+ *   - Argument errors are detected on the host before any device work.
+ */
+#ifndef HISVSIM_H
+#define HISVSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SV_OK = 0,
+    SV_ERR_ARG = 1,        /* bad argument: null pointer, size, qubit index, n out of range */
+    SV_ERR_OOM = 2,        /* device or host allocation failed */
+    SV_ERR_CUDA = 3,       /* a CUDA call failed (launch, copy, fault surfaced at a sync) */
+    SV_ERR_PARTITION = 4,  /* a gate has more qubits than the part limit k (Sec. IV-A, L <= L_m) */
+    SV_ERR_TIMEOUT = 5,    /* a bounded device wait gave up (batched persistent kernel) */
+    SV_ERR_BUSY = 6,       /* the handle has work that must complete first */
+    SV_ERR_INTERNAL = 7
+} sv_status;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_precision;
+
+/* Part builders of Sec. IV-B; SV_PART_NONE runs gate by gate (one pass per gate). */
+typedef enum { SV_PART_NONE = 0, SV_PART_NAT = 1, SV_PART_DFS = 2, SV_PART_DAGP = 3 } sv_method;
+
+/* Gate kinds. Matrices (Sec. II-A defines X, Y, Z, H; the rest are the
+ * textbook conventions): RX(t) = [[c,-is],[-is,c]], RY(t) = [[c,-s],[s,c]]
+ * with c = cos t/2, s = sin t/2; RZ(t) = diag(e^{-it/2}, e^{it/2});
+ * P(t) = diag(1, e^{it}); S = P(pi/2); T = P(pi/4); CX(c,t) flips b_t when
+ * b_c = 1; CZ = diag(1,1,1,-1); CP(t) = diag(1,1,1,e^{it}); SWAP exchanges
+ * the two qubits. For two-qubit gates q[0] is the control. */
+typedef enum {
+    SV_GATE_H = 0, SV_GATE_X, SV_GATE_Y, SV_GATE_Z, SV_GATE_S, SV_GATE_T,
+    SV_GATE_RX, SV_GATE_RY, SV_GATE_RZ, SV_GATE_P,
+    SV_GATE_CX, SV_GATE_CZ, SV_GATE_CP, SV_GATE_SWAP,
+    SV_GATE_COUNT
+} sv_gate_kind;
+
+/* One gate (24 bytes). arity must match the kind (1 or 2); q[arity..2] are ignored. */
+typedef struct {
+    uint16_t kind;
+    uint16_t arity;
+    uint32_t q[3];
+    double theta;
+} sv_gate;
+
+typedef struct sv_state sv_state;
+typedef struct sv_plan sv_plan;
+
+/* Flags of sv_apply_parts. */
+#define SV_FLAG_GATEWISE 0x1u   /* ignore the parts: one plain pass per gate (comparator) */
+#define SV_FLAG_SYNC     0x2u   /* synchronise the stream before returning */
+
+/* ---------------------------------------------------------------- state ---
+ * sv_create: make an n-qubit state (1 <= n <= 36) initialised to |0...0>.
+ *   dev_buf       caller-owned device buffer of >= 2^n * amp bytes, or NULL to
+ *                 let the library allocate (and free at sv_destroy). A caller
+ *                 buffer must stay alive until sv_destroy.
+ *   dev_buf_bytes size of dev_buf (ignored when dev_buf is NULL).
+ *   stream        cudaStream_t the state's work is ordered on (NULL = legacy
+ *                 default stream).
+ *   out           receives the handle.
+ * The amplitudes are the paper's state vector (Sec. II-B): 2^n entries. */
+sv_status sv_create(int n_qubits, sv_precision prec, void *dev_buf, size_t dev_buf_bytes,
+                    void *stream, sv_state **out);
+sv_status sv_destroy(sv_state *s);
+/* Set the state to the basis state |index> (index < 2^n). Stream-ordered. */
+sv_status sv_set_basis(sv_state *s, uint64_t index);
+/* Copy 2^n amplitudes from host memory (same layout/precision) into the state.
+ * Stream-ordered; the host buffer must stay valid until the stream reaches the
+ * copy (pinned memory makes it asynchronous). bytes must equal the state size. */
+sv_status sv_upload(sv_state *s, const void *host_src, size_t bytes);
+/* Copy the state to host memory; synchronises the stream. bytes = state size. */
+sv_status sv_copy_state(sv_state *s, void *host_dst, size_t bytes);
+/* Device address of the amplitudes and the number of bytes they occupy. */
+sv_status sv_device_ptr(sv_state *s, void **ptr, size_t *bytes);
+/* Synchronise the state's stream and report any pending device error. */
+sv_status sv_sync(sv_state *s);
+/* CTA tile size used by the part kernels for this state: tile_qubits t in
+ * [10, 13] for SV_C64 and [10, 12] for SV_C128 (2^t amplitudes per CTA); 0
+ * restores the default (13 / 12). The tile always contains the part's qubits
+ * and is padded with the lowest remaining qubits (Sec. IV-B, multi-level:
+ * parts smaller than the limit take extra qubits for spatial locality). */
+sv_status sv_set_tile(sv_state *s, int tile_qubits);
+
+/* ----------------------------------------------------------------- plan ---
+ * sv_plan_build: build the gate DAG (Sec. IV-A) and partition it with method
+ * m into acyclic parts of at most k qubits (Sec. IV-B); host only, synchronous.
+ *   gates, n_gates  the circuit in execution order (copied; caller keeps ownership)
+ *   n_qubits        qubits of the circuit (gate qubits must be < n_qubits)
+ *   k               part qubit limit L_m (ignored for SV_PART_NONE)
+ *   seed, dfs_trials  random DFS orders for SV_PART_DFS (dfs_trials <= 0: 16)
+ * Parts are numbered in execution order: Kahn order of the part graph, ties to
+ * the part holding the smallest gate index; gates of a part keep their order.
+ * Returns SV_ERR_PARTITION if a gate has more than k qubits, SV_ERR_ARG for a
+ * bad kind, arity, repeated or out-of-range qubit. */
+sv_status sv_plan_build(const sv_gate *gates, size_t n_gates, int n_qubits, sv_method m, int k,
+                        uint64_t seed, int dfs_trials, sv_plan **out);
+/* Copy the partition out: part_of_gate[n_gates] (may be NULL) and the number
+ * of parts. n_gates must equal the plan's gate count. */
+sv_status sv_plan_export(const sv_plan *p, uint32_t *part_of_gate, size_t n_gates, uint32_t *n_parts);
+/* Per-part statistics of the compiled device program for a precision/tile:
+ * passes (parts run on the GPU), register phases and smem transposes in total.
+ * Compiles the program on the host if needed; no device work. */
+sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int tile_qubits, uint32_t *passes,
+                        uint32_t *phases, uint32_t *ops);
+sv_status sv_plan_destroy(sv_plan *p);
+
+/* ---------------------------------------------------------------- apply ---
+ * Apply the plan's circuit to the state: for each part in order, one kernel
+ * pass in which every CTA gathers a 2^t-amplitude tile (the part's qubits plus
+ * padding), runs all of the part's gates on it in registers / shared memory,
+ * and scatters it back (Algorithm 1). The plan's qubit count must equal the
+ * state's. Stream-ordered (SV_FLAG_SYNC waits). The first call for a given
+ * precision and tile uploads the part program to device memory (owned by the
+ * plan). States with n < 10 run gate by gate. */
+sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags);
+
+/* -------------------------------------------------------------- measure ---
+ * Probabilities p[x] = |a_x|^2 (Sec. II-A) into dev_out (device memory of
+ * 2^n floats, or doubles when out_fp64 != 0; may be NULL to get the norm only)
+ * and the norm sum_x |a_x|^2 accumulated in FP64 into *norm_out (host, may be
+ * NULL). Synchronises the stream when norm_out is not NULL. */
+sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *norm_out);
+
+/* Thread-local description of the last non-OK status (never NULL). */
+const char *sv_last_error(void);
+/* Library version string. */
+const char *sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HISVSIM_H */

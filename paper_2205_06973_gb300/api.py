@@ -1,0 +1,114 @@
+"""Thin Python front-end over the C ABI: ``Plan`` and ``State`` handles.
+
+PyTorch provides the device memory (a uint8 tensor owns the amplitudes) and
+the CUDA stream; every computation is a call into ``libhisvsim.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native as N
+
+
+class Plan:
+    """sv_plan_build: DAG + partition (Sec. IV) of a circuit, host only."""
+
+    def __init__(self, gates, n, method="dagp", k=10, seed=0, dfs_trials=16):
+        self.n = n
+        self.G = len(gates)
+        self.method = method
+        self.k = k
+        self._arr = N.encode_gates(gates)
+        h = ctypes.c_void_p()
+        N.check(N.lib.sv_plan_build(ctypes.cast(self._arr, ctypes.c_void_p), self.G, n, N.METHODS[method],
+                                    k, seed, dfs_trials, ctypes.byref(h)))
+        self.h = h
+
+    def export(self):
+        import numpy as np
+        pog = np.zeros(max(1, self.G), dtype=np.uint32)
+        P = ctypes.c_uint32()
+        N.check(N.lib.sv_plan_export(self.h, pog.ctypes.data, self.G, ctypes.byref(P)))
+        return pog[: self.G], P.value
+
+    def stats(self, precision="c64", tile=0):
+        a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        N.check(N.lib.sv_plan_stats(self.h, N.SV_C128 if precision == "c128" else N.SV_C64, tile,
+                                    ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"passes": a.value, "phases": b.value, "ops": c.value}
+
+    def close(self):
+        if self.h:
+            N.lib.sv_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class State:
+    """sv_create over a torch-owned device buffer on the current stream."""
+
+    def __init__(self, n, precision="c64", device="cuda", stream=None, tile=0):
+        self.n = n
+        self.precision = precision
+        self.amp_bytes = 16 if precision == "c128" else 8
+        self.nbytes = self.amp_bytes << n
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.buf.device)
+        h = ctypes.c_void_p()
+        N.check(N.lib.sv_create(n, N.SV_C128 if precision == "c128" else N.SV_C64,
+                                ctypes.c_void_p(self.buf.data_ptr()), self.nbytes,
+                                ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        if tile:
+            N.check(N.lib.sv_set_tile(self.h, tile))
+
+    # views of the amplitudes (no copy)
+    def amplitudes(self):
+        dt = torch.complex128 if self.precision == "c128" else torch.complex64
+        return self.buf.view(dt)
+
+    def set_basis(self, x):
+        N.check(N.lib.sv_set_basis(self.h, x))
+
+    def upload(self, host_tensor):
+        t = host_tensor.contiguous()
+        assert t.numel() * t.element_size() == self.nbytes
+        N.check(N.lib.sv_upload(self.h, ctypes.c_void_p(t.data_ptr()), self.nbytes))
+
+    def copy_to_host(self, out=None):
+        dt = torch.complex128 if self.precision == "c128" else torch.complex64
+        if out is None:
+            out = torch.empty(1 << self.n, dtype=dt)
+        N.check(N.lib.sv_copy_state(self.h, ctypes.c_void_p(out.data_ptr()), self.nbytes))
+        return out
+
+    def apply(self, plan: Plan, gatewise=False, sync=False):
+        flags = (N.SV_FLAG_GATEWISE if gatewise else 0) | (N.SV_FLAG_SYNC if sync else 0)
+        N.check(N.lib.sv_apply_parts(self.h, plan.h, flags))
+
+    def probs(self, out=None, fp64=False):
+        norm = ctypes.c_double()
+        ptr = ctypes.c_void_p(out.data_ptr()) if out is not None else None
+        N.check(N.lib.sv_measure_probs(self.h, ptr, 1 if fp64 else 0, ctypes.byref(norm)))
+        return norm.value
+
+    def sync(self):
+        N.check(N.lib.sv_sync(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            N.lib.sv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,385 @@
+// C ABI of the library (declared in include/hisvsim.h).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/hisvsim.h"
+#include "kernels.hpp"
+#include "partition.hpp"
+#include "planner.hpp"
+
+using namespace hisv;
+
+namespace {
+thread_local std::string g_err = "no error";
+
+sv_status fail(sv_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(SV_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+constexpr int kProbBlocks = 152 * 8;
+}  // namespace
+
+struct DevProgram {
+    int dev = -1;
+    Phase *d_phases = nullptr;
+    Op *d_ops = nullptr;
+    void *d_coefs = nullptr;
+};
+
+struct sv_state {
+    int n = 0;
+    sv_precision prec = SV_C64;
+    void *buf = nullptr;
+    size_t bytes = 0;
+    bool owns = false;
+    cudaStream_t stream = nullptr;
+    int tile = 0;
+    int dev = 0;
+    double *d_partials = nullptr;   // kProbBlocks + 1 doubles; the last holds the norm
+    double *h_norm = nullptr;       // pinned
+};
+
+struct sv_plan {
+    int n = 0;
+    sv_method method = SV_PART_NONE;
+    int k = 0;
+    std::vector<GateRef> gates;
+    std::vector<uint32_t> pog;
+    uint32_t n_parts = 0;
+    std::map<std::pair<bool, int>, std::unique_ptr<Program>> host_progs;   // (fp64, t)
+    std::map<std::tuple<int, bool, int>, DevProgram> dev_progs;            // (dev, fp64, t)
+    std::vector<std::vector<double>> mats;                                 // gatewise matrices
+};
+
+static size_t amp_bytes(sv_precision p) { return p == SV_C128 ? 16 : 8; }
+static bool is_fp64(const sv_state *s) { return s->prec == SV_C128; }
+
+static int default_tile(bool fp64) { return part_tmax(fp64); }
+
+extern "C" {
+
+const char *sv_last_error(void) { return g_err.c_str(); }
+const char *sv_version(void) { return "hisvsim-gb300 0.1 (sm_103a)"; }
+
+sv_status sv_create(int n, sv_precision prec, void *dev_buf, size_t dev_buf_bytes, void *stream, sv_state **out) {
+    if (!out) return fail(SV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 36) return fail(SV_ERR_ARG, "n_qubits must be in [1, 36]");
+    if (prec != SV_C64 && prec != SV_C128) return fail(SV_ERR_ARG, "bad precision");
+    const size_t bytes = amp_bytes(prec) << n;
+    if (dev_buf && dev_buf_bytes < bytes) return fail(SV_ERR_ARG, "dev_buf smaller than 2^n amplitudes");
+    if (dev_buf && (reinterpret_cast<uintptr_t>(dev_buf) & 15)) return fail(SV_ERR_ARG, "dev_buf must be 16-byte aligned");
+    std::unique_ptr<sv_state> s(new sv_state());
+    s->n = n;
+    s->prec = prec;
+    s->bytes = bytes;
+    s->stream = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaGetDevice(&s->dev));
+    if (dev_buf) {
+        s->buf = dev_buf;
+    } else {
+        cudaError_t e = cudaMalloc(&s->buf, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SV_ERR_OOM, std::string("cudaMalloc state: ") + cudaGetErrorString(e));
+        }
+        s->owns = true;
+    }
+    cudaError_t e = cudaMalloc(&s->d_partials, sizeof(double) * (kProbBlocks + 1));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_norm, sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (s->owns) cudaFree(s->buf);
+        if (s->d_partials) cudaFree(s->d_partials);
+        return fail(SV_ERR_OOM, std::string("scratch allocation: ") + cudaGetErrorString(e));
+    }
+    e = launch_set_basis(is_fp64(s.get()), s->buf, n, 0, s->stream);
+    if (e != cudaSuccess) {
+        if (s->owns) cudaFree(s->buf);
+        cudaFree(s->d_partials);
+        cudaFreeHost(s->h_norm);
+        return fail(SV_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e));
+    }
+    *out = s.release();
+    return SV_OK;
+}
+
+sv_status sv_destroy(sv_state *s) {
+    if (!s) return fail(SV_ERR_ARG, "state is NULL");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (s->owns) cudaFree(s->buf);
+    cudaFree(s->d_partials);
+    cudaFreeHost(s->h_norm);
+    delete s;
+    if (e != cudaSuccess) return fail(SV_ERR_CUDA, std::string("pending work failed: ") + cudaGetErrorString(e));
+    return SV_OK;
+}
+
+sv_status sv_set_basis(sv_state *s, uint64_t index) {
+    if (!s) return fail(SV_ERR_ARG, "state is NULL");
+    if (index >> s->n) return fail(SV_ERR_ARG, "basis index >= 2^n");
+    CUDA_TRY(launch_set_basis(is_fp64(s), s->buf, s->n, index, s->stream));
+    return SV_OK;
+}
+
+sv_status sv_upload(sv_state *s, const void *src, size_t bytes) {
+    if (!s || !src) return fail(SV_ERR_ARG, "NULL argument");
+    if (bytes != s->bytes) return fail(SV_ERR_ARG, "bytes must equal the state size");
+    CUDA_TRY(cudaMemcpyAsync(s->buf, src, bytes, cudaMemcpyHostToDevice, s->stream));
+    return SV_OK;
+}
+
+sv_status sv_copy_state(sv_state *s, void *dst, size_t bytes) {
+    if (!s || !dst) return fail(SV_ERR_ARG, "NULL argument");
+    if (bytes != s->bytes) return fail(SV_ERR_ARG, "bytes must equal the state size");
+    CUDA_TRY(cudaMemcpyAsync(dst, s->buf, bytes, cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return SV_OK;
+}
+
+sv_status sv_device_ptr(sv_state *s, void **ptr, size_t *bytes) {
+    if (!s) return fail(SV_ERR_ARG, "state is NULL");
+    if (ptr) *ptr = s->buf;
+    if (bytes) *bytes = s->bytes;
+    return SV_OK;
+}
+
+sv_status sv_sync(sv_state *s) {
+    if (!s) return fail(SV_ERR_ARG, "state is NULL");
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return SV_OK;
+}
+
+sv_status sv_set_tile(sv_state *s, int t) {
+    if (!s) return fail(SV_ERR_ARG, "state is NULL");
+    if (t != 0 && (t < part_tmin() || t > part_tmax(is_fp64(s))))
+        return fail(SV_ERR_ARG, "tile_qubits out of range");
+    s->tile = t;
+    return SV_OK;
+}
+
+sv_status sv_plan_build(const sv_gate *gates, size_t n_gates, int n, sv_method m, int k, uint64_t seed,
+                        int dfs_trials, sv_plan **out) {
+    if (!out) return fail(SV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 36) return fail(SV_ERR_ARG, "n_qubits must be in [1, 36]");
+    if (n_gates && !gates) return fail(SV_ERR_ARG, "gates is NULL");
+    if (m < SV_PART_NONE || m > SV_PART_DAGP) return fail(SV_ERR_ARG, "bad method");
+    std::unique_ptr<sv_plan> p(new sv_plan());
+    p->n = n;
+    p->method = m;
+    p->k = k;
+    p->gates.resize(n_gates);
+    int max_arity = 0;
+    for (size_t i = 0; i < n_gates; i++) {
+        const sv_gate &g = gates[i];
+        if (g.kind >= SV_GATE_COUNT) return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": bad kind");
+        const int want = gate_is_two_qubit(g.kind) ? 2 : 1;
+        if (g.arity != want) return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": arity does not match kind");
+        GateRef &r = p->gates[i];
+        r.kind = g.kind;
+        r.arity = g.arity;
+        r.theta = g.theta;
+        for (int j = 0; j < 3; j++) r.q[j] = j < g.arity ? (int)g.q[j] : 0;
+        for (int j = 0; j < g.arity; j++)
+            if (g.q[j] >= (uint32_t)n) return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": qubit out of range");
+        if (g.arity == 2 && g.q[0] == g.q[1]) return fail(SV_ERR_ARG, "gate " + std::to_string(i) + ": repeated qubit");
+        max_arity = std::max(max_arity, (int)g.arity);
+    }
+    if (m != SV_PART_NONE) {
+        if (k < 1) return fail(SV_ERR_ARG, "k must be >= 1");
+        if (max_arity > k) return fail(SV_ERR_PARTITION, "a gate has more qubits than k");
+        Dag dag;
+        std::string err;
+        if (!build_dag(p->gates, n, dag, err)) return fail(SV_ERR_ARG, err);
+        if (m == SV_PART_NAT) p->pog = part_nat(dag, k);
+        else if (m == SV_PART_DFS) p->pog = part_dfs(dag, k, seed, dfs_trials);
+        else p->pog = part_dagp(dag, k);
+        for (uint32_t x : p->pog) p->n_parts = std::max(p->n_parts, x + 1);
+    } else {
+        p->pog.resize(n_gates);
+        for (size_t i = 0; i < n_gates; i++) p->pog[i] = (uint32_t)i;
+        p->n_parts = (uint32_t)n_gates;
+    }
+    *out = p.release();
+    return SV_OK;
+}
+
+sv_status sv_plan_export(const sv_plan *p, uint32_t *pog, size_t n_gates, uint32_t *n_parts) {
+    if (!p) return fail(SV_ERR_ARG, "plan is NULL");
+    if (n_gates != p->gates.size()) return fail(SV_ERR_ARG, "n_gates does not match the plan");
+    if (pog) std::memcpy(pog, p->pog.data(), sizeof(uint32_t) * n_gates);
+    if (n_parts) *n_parts = p->n_parts;
+    return SV_OK;
+}
+
+static sv_status get_host_program(sv_plan *p, bool fp64, int t, const Program **out) {
+    auto key = std::make_pair(fp64, t);
+    auto it = p->host_progs.find(key);
+    if (it == p->host_progs.end()) {
+        std::unique_ptr<Program> prog(new Program());
+        std::string err;
+        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, fp64, t, part_R(fp64), *prog, err))
+            return fail(SV_ERR_PARTITION, err);
+        it = p->host_progs.emplace(key, std::move(prog)).first;
+    }
+    *out = it->second.get();
+    return SV_OK;
+}
+
+sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int t, uint32_t *passes, uint32_t *phases, uint32_t *ops) {
+    if (!p) return fail(SV_ERR_ARG, "plan is NULL");
+    const bool fp64 = prec == SV_C128;
+    if (t == 0) t = default_tile(fp64);
+    if (t < part_tmin() || t > part_tmax(fp64)) return fail(SV_ERR_ARG, "tile_qubits out of range");
+    if (p->method == SV_PART_NONE || p->n < part_tmin()) {
+        if (passes) *passes = (uint32_t)p->gates.size();
+        if (phases) *phases = 0;
+        if (ops) *ops = 0;
+        return SV_OK;
+    }
+    const Program *prog = nullptr;
+    sv_status st = get_host_program(p, fp64, t, &prog);
+    if (st != SV_OK) return st;
+    if (passes) *passes = (uint32_t)prog->parts.size();
+    if (phases) *phases = (uint32_t)prog->phases.size();
+    if (ops) *ops = (uint32_t)prog->ops.size();
+    return SV_OK;
+}
+
+sv_status sv_plan_destroy(sv_plan *p) {
+    if (!p) return fail(SV_ERR_ARG, "plan is NULL");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : p->dev_progs) {
+        cudaSetDevice(kv.second.dev);
+        cudaFree(kv.second.d_phases);
+        cudaFree(kv.second.d_ops);
+        cudaFree(kv.second.d_coefs);
+    }
+    cudaSetDevice(cur);
+    delete p;
+    return SV_OK;
+}
+
+static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, const Program **hp, const DevProgram **dp) {
+    const bool fp64 = is_fp64(s);
+    sv_status st = get_host_program(p, fp64, t, hp);
+    if (st != SV_OK) return st;
+    auto key = std::make_tuple(s->dev, fp64, t);
+    auto it = p->dev_progs.find(key);
+    if (it == p->dev_progs.end()) {
+        const Program &prog = **hp;
+        DevProgram d;
+        d.dev = s->dev;
+        const size_t nph = std::max<size_t>(1, prog.phases.size()), nop = std::max<size_t>(1, prog.ops.size());
+        const size_t ncf = std::max<size_t>(1, prog.coefs.size());
+        const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+        cudaError_t e = cudaMalloc(&d.d_phases, sizeof(Phase) * nph);
+        if (e == cudaSuccess) e = cudaMalloc(&d.d_ops, sizeof(Op) * nop);
+        if (e == cudaSuccess) e = cudaMalloc(&d.d_coefs, rsz * ncf);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(d.d_phases);
+            cudaFree(d.d_ops);
+            cudaFree(d.d_coefs);
+            return fail(SV_ERR_OOM, std::string("program upload: ") + cudaGetErrorString(e));
+        }
+        std::vector<float> cf32;
+        const void *cf = prog.coefs.data();
+        if (!fp64) {
+            cf32.assign(prog.coefs.begin(), prog.coefs.end());
+            cf = cf32.data();
+        }
+        if (!prog.phases.empty()) e = cudaMemcpy(d.d_phases, prog.phases.data(), sizeof(Phase) * prog.phases.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !prog.ops.empty()) e = cudaMemcpy(d.d_ops, prog.ops.data(), sizeof(Op) * prog.ops.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !prog.coefs.empty()) e = cudaMemcpy(d.d_coefs, cf, rsz * prog.coefs.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d.d_phases);
+            cudaFree(d.d_ops);
+            cudaFree(d.d_coefs);
+            return fail(SV_ERR_CUDA, std::string("program upload: ") + cudaGetErrorString(e));
+        }
+        it = p->dev_progs.emplace(key, d).first;
+    }
+    *dp = &it->second;
+    return SV_OK;
+}
+
+static sv_status apply_gatewise(sv_state *s, sv_plan *p) {
+    const bool fp64 = is_fp64(s);
+    if (p->mats.size() != p->gates.size()) {
+        p->mats.assign(p->gates.size(), {});
+        for (size_t i = 0; i < p->gates.size(); i++) {
+            const GateRef &g = p->gates[i];
+            if (g.arity == 1) {
+                p->mats[i].resize(8);
+                gate_matrix_1q(g.kind, g.theta, p->mats[i].data());
+            } else {
+                p->mats[i].resize(32);
+                gate_matrix_2q(g.kind, g.theta, p->mats[i].data());
+            }
+        }
+    }
+    for (size_t i = 0; i < p->gates.size(); i++) {
+        const GateRef &g = p->gates[i];
+        cudaError_t e;
+        if (g.arity == 1) e = launch_gate1(fp64, s->buf, s->n, g.q[0], p->mats[i].data(), s->stream);
+        else e = launch_gate2(fp64, s->buf, s->n, g.q[0], g.q[1], p->mats[i].data(), s->stream);
+        if (e != cudaSuccess) return fail(SV_ERR_CUDA, std::string("gate launch: ") + cudaGetErrorString(e));
+    }
+    return SV_OK;
+}
+
+sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
+    if (!s || !p) return fail(SV_ERR_ARG, "NULL argument");
+    if (p->n != s->n) return fail(SV_ERR_ARG, "plan and state qubit counts differ");
+    sv_status st = SV_OK;
+    if ((flags & SV_FLAG_GATEWISE) || p->method == SV_PART_NONE || s->n < part_tmin()) {
+        st = apply_gatewise(s, p);
+    } else {
+        const bool fp64 = is_fp64(s);
+        const int t = s->tile ? s->tile : default_tile(fp64);
+        const Program *hp = nullptr;
+        const DevProgram *dp = nullptr;
+        st = get_dev_program(s, p, t, &hp, &dp);
+        if (st != SV_OK) return st;
+        for (size_t i = 0; i < hp->parts.size(); i++) {
+            cudaError_t e = launch_part(fp64, hp->t, s->buf, hp->parts[i], dp->d_phases, dp->d_ops, dp->d_coefs,
+                                        hp->n_tiles[i], s->stream);
+            if (e != cudaSuccess) return fail(SV_ERR_CUDA, std::string("part launch: ") + cudaGetErrorString(e));
+        }
+    }
+    if (st != SV_OK) return st;
+    if (flags & SV_FLAG_SYNC) CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return SV_OK;
+}
+
+sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *norm_out) {
+    if (!s) return fail(SV_ERR_ARG, "state is NULL");
+    double *d_norm = s->d_partials + kProbBlocks;
+    CUDA_TRY(launch_probs(is_fp64(s), s->buf, s->n, dev_out, out_fp64, s->d_partials, kProbBlocks, d_norm, s->stream));
+    if (norm_out) {
+        CUDA_TRY(cudaMemcpyAsync(s->h_norm, d_norm, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        *norm_out = *s->h_norm;
+    }
+    return SV_OK;
+}
+
+}  // extern "C"

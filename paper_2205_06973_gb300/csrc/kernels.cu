@@ -1,0 +1,594 @@
+// sm_103a kernels of the hierarchical state-vector simulator.
+//
+//  k_part  : one HBM pass of one part (Algorithm 1, Gather-Execute-Scatter).
+//            Each CTA gathers the 2^t amplitudes of one outer assignment
+//            straight into registers (2^R per thread), runs the part's
+//            register phases, transposing the tile through XOR-swizzled
+//            shared memory between phases, and scatters it back.
+//  k_gate1 / k_gate2 : the plain per-gate pass of Sec. III-A (comparator).
+//  k_probs / k_sum   : |a_x|^2 and the norm with FP64 accumulation.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "kernels.hpp"
+
+namespace hisv {
+
+template <typename Real> struct CT;
+template <> struct CT<float> { typedef float2 T; };
+template <> struct CT<double> { typedef double2 T; };
+
+// ------------------------------------------------------------------------
+// register-bit operations; B, A are compile-time register bits
+// ------------------------------------------------------------------------
+template <int NR, int B, typename C, typename Real>
+__device__ __forceinline__ void op_h(C (&a)[NR], Real r) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        a[i].x = (x.x + y.x) * r; a[i].y = (x.y + y.y) * r;
+        a[j].x = (x.x - y.x) * r; a[j].y = (x.y - y.y) * r;
+    }
+}
+
+template <int NR, int B, typename C, typename Real>
+__device__ __forceinline__ void op_u2(C (&a)[NR], const Real *m) {
+    const Real m00r = m[0], m00i = m[1], m01r = m[2], m01i = m[3];
+    const Real m10r = m[4], m10i = m[5], m11r = m[6], m11i = m[7];
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        a[i].x = m00r * x.x - m00i * x.y + m01r * y.x - m01i * y.y;
+        a[i].y = m00r * x.y + m00i * x.x + m01r * y.y + m01i * y.x;
+        a[j].x = m10r * x.x - m10i * x.y + m11r * y.x - m11i * y.y;
+        a[j].y = m10r * x.y + m10i * x.x + m11r * y.y + m11i * y.x;
+    }
+}
+
+template <int NR, int B, typename C, typename Real>
+__device__ __forceinline__ void op_rx(C (&a)[NR], Real c, Real s) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        a[i].x = c * x.x + s * y.y; a[i].y = c * x.y - s * y.x;
+        a[j].x = s * x.y + c * y.x; a[j].y = c * y.y - s * x.x;
+    }
+}
+
+template <int NR, int B, typename C, typename Real>
+__device__ __forceinline__ void op_ry(C (&a)[NR], Real c, Real s) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        a[i].x = c * x.x - s * y.x; a[i].y = c * x.y - s * y.y;
+        a[j].x = s * x.x + c * y.x; a[j].y = s * x.y + c * y.y;
+    }
+}
+
+template <int NR, int B, typename C>
+__device__ __forceinline__ void op_x(C (&a)[NR]) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i];
+        a[i] = a[j];
+        a[j] = x;
+    }
+}
+
+template <int NR, int B, typename C>
+__device__ __forceinline__ void op_y(C (&a)[NR]) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        a[i].x = y.y; a[i].y = -y.x;
+        a[j].x = -x.y; a[j].y = x.x;
+    }
+}
+
+template <typename C, typename Real>
+__device__ __forceinline__ void cmul_in(C &v, Real dr, Real di) {
+    const Real x = v.x, y = v.y;
+    v.x = x * dr - y * di;
+    v.y = x * di + y * dr;
+}
+
+template <int NR, int B, typename C, typename Real>
+__device__ __forceinline__ void op_d(C (&a)[NR], Real d0r, Real d0i, Real d1r, Real d1i) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) cmul_in(a[i], d1r, d1i);
+        else cmul_in(a[i], d0r, d0i);
+    }
+}
+
+template <int NR, int B, typename C, typename Real>
+__device__ __forceinline__ void op_p(C (&a)[NR], Real dr, Real di) {
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+        if (i & (1 << B)) cmul_in(a[i], dr, di);
+}
+
+template <int NR, int B, typename C>
+__device__ __forceinline__ void op_z(C (&a)[NR]) {
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+        if (i & (1 << B)) { a[i].x = -a[i].x; a[i].y = -a[i].y; }
+}
+
+template <int NR, int A, int B, typename C>
+__device__ __forceinline__ void op_cx(C (&a)[NR]) {   // A control, B target
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (!(i & (1 << A)) || (i & (1 << B))) continue;
+        const int j = i | (1 << B);
+        const C x = a[i];
+        a[i] = a[j];
+        a[j] = x;
+    }
+}
+
+template <int NR, int A, int B, typename C, typename Real>
+__device__ __forceinline__ void op_cp(C (&a)[NR], Real dr, Real di) {
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+        if ((i & (1 << A)) && (i & (1 << B))) cmul_in(a[i], dr, di);
+}
+
+template <int NR, int A, int B, typename C>
+__device__ __forceinline__ void op_cz(C (&a)[NR]) {
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+        if ((i & (1 << A)) && (i & (1 << B))) { a[i].x = -a[i].x; a[i].y = -a[i].y; }
+}
+
+// Call f(integral_constant<int, b>) for a runtime register bit b < R.
+template <int R, int B = 0, typename F>
+__device__ __forceinline__ void with_bit(int b, F &&f) {
+    if constexpr (B < R) {
+        if (b == B) f(std::integral_constant<int, B>());
+        else with_bit<R, B + 1>(b, static_cast<F &&>(f));
+    }
+}
+
+// Swizzled shared-memory index contribution of tile slot p. The swizzle XORs
+// the slot bits above the bank group into the low bits (linear over GF(2)),
+// so a warp whose lane bits sit on slots of distinct residues touches
+// distinct banks: 8-byte elements use 4-bit groups, 16-byte elements 3-bit.
+template <typename Real>
+__device__ __forceinline__ uint32_t swz(int p) {
+    if constexpr (sizeof(Real) == 4) return p < 4 ? (1u << p) : ((1u << p) | (1u << (p & 3)));
+    else return p < 3 ? (1u << p) : ((1u << p) | (1u << (p % 3)));
+}
+
+// ------------------------------------------------------------------------
+// part kernel
+// ------------------------------------------------------------------------
+template <typename Real, int T, int R>
+__global__ void __launch_bounds__(1 << (T - R), (512 >> (T - R)) > 0 ? (512 >> (T - R)) : 1)
+k_part(typename CT<Real>::T *__restrict__ sv, const __grid_constant__ PartLaunch L,
+       const Phase *__restrict__ phases, const Op *__restrict__ ops, const Real *__restrict__ coefs,
+       uint64_t n_tiles) {
+    typedef typename CT<Real>::T C;
+    constexpr int NR = 1 << R;
+    constexpr int TB = T - R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const int tid = threadIdx.x;
+    const Real rsq = Real(0.70710678118654752440);
+
+    C a[NR];
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        // Gather: outer bits of the tile index deposited into the outer qubits
+        uint64_t base = 0;
+        {
+            uint64_t m = L.outer_mask, v = tile;
+            while (m) {
+                const uint64_t low = m & (~m + 1);
+                if (v & 1) base |= low;
+                v >>= 1;
+                m ^= low;
+            }
+        }
+        {
+            uint64_t toff = base;
+#pragma unroll
+            for (int j = 0; j < TB; j++)
+                if ((tid >> j) & 1) toff |= 1ull << L.load_thr_q[j];
+            uint64_t rs[R];
+#pragma unroll
+            for (int b = 0; b < R; b++) rs[b] = 1ull << L.load_reg_q[b];
+#pragma unroll
+            for (int i = 0; i < NR; i++) {
+                uint64_t off = toff;
+#pragma unroll
+                for (int b = 0; b < R; b++)
+                    if (i & (1 << b)) off |= rs[b];
+                a[i] = __ldcs(sv + off);
+            }
+        }
+        Real tpr = Real(1), tpi = Real(0);   // per-thread phase of diagonal gates on thread bits
+        uint32_t s_thr = 0, s_reg[R];
+        for (uint32_t p = 0; p < L.n_phases; p++) {
+            const Phase ph = phases[L.phase_begin + p];
+            if (p > 0) {
+                // transpose: write with the previous layout, read with this one
+#pragma unroll
+                for (int i = 0; i < NR; i++) {
+                    uint32_t o = s_thr;
+#pragma unroll
+                    for (int b = 0; b < R; b++)
+                        if (i & (1 << b)) o ^= s_reg[b];
+                    sm[o] = a[i];
+                }
+                __syncthreads();
+            }
+            s_thr = 0;
+#pragma unroll
+            for (int j = 0; j < TB; j++)
+                if ((tid >> j) & 1) s_thr ^= swz<Real>(ph.thr[j]);
+#pragma unroll
+            for (int b = 0; b < R; b++) s_reg[b] = swz<Real>(ph.reg[b]);
+            if (p > 0) {
+#pragma unroll
+                for (int i = 0; i < NR; i++) {
+                    uint32_t o = s_thr;
+#pragma unroll
+                    for (int b = 0; b < R; b++)
+                        if (i & (1 << b)) o ^= s_reg[b];
+                    a[i] = sm[o];
+                }
+                __syncthreads();
+            }
+            // Execute: the phase's gates
+            for (uint32_t o = 0; o < ph.op_count; o++) {
+                const Op op = ops[ph.op_begin + o];
+                const Real *cf = coefs + op.coef;
+                switch (op.kind) {
+                case OP_H:
+                    with_bit<R>(op.a, [&](auto bc) { op_h<NR, decltype(bc)::value>(a, rsq); });
+                    break;
+                case OP_U2:
+                    with_bit<R>(op.a, [&](auto bc) { op_u2<NR, decltype(bc)::value>(a, cf); });
+                    break;
+                case OP_RX: {
+                    const Real c = cf[0], s = cf[1];
+                    with_bit<R>(op.a, [&](auto bc) { op_rx<NR, decltype(bc)::value>(a, c, s); });
+                } break;
+                case OP_RY: {
+                    const Real c = cf[0], s = cf[1];
+                    with_bit<R>(op.a, [&](auto bc) { op_ry<NR, decltype(bc)::value>(a, c, s); });
+                } break;
+                case OP_X:
+                    with_bit<R>(op.a, [&](auto bc) { op_x<NR, decltype(bc)::value>(a); });
+                    break;
+                case OP_Y:
+                    with_bit<R>(op.a, [&](auto bc) { op_y<NR, decltype(bc)::value>(a); });
+                    break;
+                case OP_D: {
+                    const Real d0r = cf[0], d0i = cf[1], d1r = cf[2], d1i = cf[3];
+                    with_bit<R>(op.a, [&](auto bc) { op_d<NR, decltype(bc)::value>(a, d0r, d0i, d1r, d1i); });
+                } break;
+                case OP_P: {
+                    const Real dr = cf[0], di = cf[1];
+                    with_bit<R>(op.a, [&](auto bc) { op_p<NR, decltype(bc)::value>(a, dr, di); });
+                } break;
+                case OP_Z:
+                    with_bit<R>(op.a, [&](auto bc) { op_z<NR, decltype(bc)::value>(a); });
+                    break;
+                case OP_CX:
+                    with_bit<R>(op.a, [&](auto ac) {
+                        with_bit<R>(op.b, [&](auto bc) {
+                            constexpr int A = decltype(ac)::value, B = decltype(bc)::value;
+                            if constexpr (A != B) op_cx<NR, A, B>(a);
+                        });
+                    });
+                    break;
+                case OP_CP: {
+                    const Real dr = cf[0], di = cf[1];
+                    with_bit<R>(op.a, [&](auto ac) {
+                        with_bit<R>(op.b, [&](auto bc) {
+                            constexpr int A = decltype(ac)::value, B = decltype(bc)::value;
+                            if constexpr (A != B) op_cp<NR, A, B>(a, dr, di);
+                        });
+                    });
+                } break;
+                case OP_CZ:
+                    with_bit<R>(op.a, [&](auto ac) {
+                        with_bit<R>(op.b, [&](auto bc) {
+                            constexpr int A = decltype(ac)::value, B = decltype(bc)::value;
+                            if constexpr (A != B) op_cz<NR, A, B>(a);
+                        });
+                    });
+                    break;
+                case OP_CXT:
+                    if ((tid >> op.tb) & 1)
+                        with_bit<R>(op.b, [&](auto bc) { op_x<NR, decltype(bc)::value>(a); });
+                    break;
+                case OP_CPT:
+                    if ((tid >> op.tb) & 1) {
+                        const Real dr = cf[0], di = cf[1];
+                        with_bit<R>(op.a, [&](auto bc) { op_p<NR, decltype(bc)::value>(a, dr, di); });
+                    }
+                    break;
+                case OP_CZT:
+                    if ((tid >> op.tb) & 1)
+                        with_bit<R>(op.a, [&](auto bc) { op_z<NR, decltype(bc)::value>(a); });
+                    break;
+                case OP_TD: {
+                    const int bit = (tid >> op.tb) & 1;
+                    const Real dr = bit ? cf[2] : cf[0], di = bit ? cf[3] : cf[1];
+                    const Real x = tpr, y = tpi;
+                    tpr = x * dr - y * di;
+                    tpi = x * di + y * dr;
+                } break;
+                case OP_TP2:
+                    if (((tid >> op.tb) & 1) && ((tid >> op.b) & 1)) {
+                        const Real dr = cf[0], di = cf[1];
+                        const Real x = tpr, y = tpi;
+                        tpr = x * dr - y * di;
+                        tpi = x * di + y * dr;
+                    }
+                    break;
+                case OP_TAPPLY:
+#pragma unroll
+                    for (int i = 0; i < NR; i++) cmul_in(a[i], tpr, tpi);
+                    tpr = Real(1);
+                    tpi = Real(0);
+                    break;
+                default:
+                    break;
+                }
+            }
+        }
+        // Scatter: the last phase's layout, with SWAP relabels applied
+        {
+            uint64_t toff = base;
+#pragma unroll
+            for (int j = 0; j < TB; j++)
+                if ((tid >> j) & 1) toff |= 1ull << L.store_thr_q[j];
+            uint64_t rs[R];
+#pragma unroll
+            for (int b = 0; b < R; b++) rs[b] = 1ull << L.store_reg_q[b];
+#pragma unroll
+            for (int i = 0; i < NR; i++) {
+                uint64_t off = toff;
+#pragma unroll
+                for (int b = 0; b < R; b++)
+                    if (i & (1 << b)) off |= rs[b];
+                __stcs(sv + off, a[i]);
+            }
+        }
+        if (L.n_phases > 1) __syncthreads();   // smem reuse by the next tile
+    }
+}
+
+template <typename Real, int T>
+static cudaError_t launch_part_t(void *sv, const PartLaunch &L, const Phase *phases, const Op *ops,
+                                 const void *coefs, uint64_t n_tiles, cudaStream_t st) {
+    constexpr int R = sizeof(Real) == 4 ? 5 : 4;
+    typedef typename CT<Real>::T C;
+    auto kern = k_part<Real, T, R>;
+    const size_t smem = L.n_phases > 1 ? sizeof(C) << T : 0;
+    static uint64_t attr_set = 0;   // devices on which the smem limit was raised (per instantiation)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && !((attr_set >> dev) & 1)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(C) << T));
+        if (e != cudaSuccess) return e;
+        attr_set |= 1ull << dev;
+    }
+    uint64_t grid = n_tiles;
+    if (grid > (1ull << 31) - 1) grid = (1ull << 31) - 1;
+    kern<<<(unsigned)grid, 1 << (T - R), smem, st>>>(reinterpret_cast<C *>(sv), L, phases, ops,
+                                                      reinterpret_cast<const Real *>(coefs), n_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_part(bool fp64, int t, void *sv, const PartLaunch &L, const Phase *phases,
+                        const Op *ops, const void *coefs, uint64_t n_tiles, cudaStream_t st) {
+    if (!fp64) {
+        switch (t) {
+        case 10: return launch_part_t<float, 10>(sv, L, phases, ops, coefs, n_tiles, st);
+        case 11: return launch_part_t<float, 11>(sv, L, phases, ops, coefs, n_tiles, st);
+        case 12: return launch_part_t<float, 12>(sv, L, phases, ops, coefs, n_tiles, st);
+        case 13: return launch_part_t<float, 13>(sv, L, phases, ops, coefs, n_tiles, st);
+        }
+    } else {
+        switch (t) {
+        case 10: return launch_part_t<double, 10>(sv, L, phases, ops, coefs, n_tiles, st);
+        case 11: return launch_part_t<double, 11>(sv, L, phases, ops, coefs, n_tiles, st);
+        case 12: return launch_part_t<double, 12>(sv, L, phases, ops, coefs, n_tiles, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------------
+// plain per-gate kernels
+// ------------------------------------------------------------------------
+template <typename Real> struct M2 { Real m[8]; };
+template <typename Real> struct M4 { Real m[32]; };
+
+template <typename Real>
+__global__ void __launch_bounds__(256) k_gate1(typename CT<Real>::T *__restrict__ sv, int q, uint64_t npairs,
+                                                const __grid_constant__ M2<Real> g) {
+    typedef typename CT<Real>::T C;
+    const uint64_t lomask = (1ull << q) - 1;
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x0 = ((p & ~lomask) << 1) | (p & lomask);
+        const uint64_t x1 = x0 | (1ull << q);
+        const C x = sv[x0], y = sv[x1];
+        C u, v;
+        u.x = g.m[0] * x.x - g.m[1] * x.y + g.m[2] * y.x - g.m[3] * y.y;
+        u.y = g.m[0] * x.y + g.m[1] * x.x + g.m[2] * y.y + g.m[3] * y.x;
+        v.x = g.m[4] * x.x - g.m[5] * x.y + g.m[6] * y.x - g.m[7] * y.y;
+        v.y = g.m[4] * x.y + g.m[5] * x.x + g.m[6] * y.y + g.m[7] * y.x;
+        sv[x0] = u;
+        sv[x1] = v;
+    }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) k_gate2(typename CT<Real>::T *__restrict__ sv, int q0, int q1,
+                                                uint64_t nquads, const __grid_constant__ M4<Real> g) {
+    typedef typename CT<Real>::T C;
+    const int lo = q0 < q1 ? q0 : q1, hi = q0 < q1 ? q1 : q0;
+    const uint64_t m_lo = (1ull << lo) - 1, m_hi = (1ull << hi) - 1;
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nquads;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t x = ((p & ~m_lo) << 1) | (p & m_lo);   // insert a zero bit at lo
+        x = ((x & ~m_hi) << 1) | (x & m_hi);              // then at hi
+        uint64_t idx[4];
+        idx[0] = x;
+        idx[1] = x | (1ull << q0);
+        idx[2] = x | (1ull << q1);
+        idx[3] = x | (1ull << q0) | (1ull << q1);
+        C in[4];
+#pragma unroll
+        for (int l = 0; l < 4; l++) in[l] = sv[idx[l]];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            Real re = 0, im = 0;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const Real mr = g.m[2 * (4 * r + c)], mi = g.m[2 * (4 * r + c) + 1];
+                re += mr * in[c].x - mi * in[c].y;
+                im += mr * in[c].y + mi * in[c].x;
+            }
+            C o;
+            o.x = re;
+            o.y = im;
+            sv[idx[r]] = o;
+        }
+    }
+}
+
+static unsigned grid_for(uint64_t work, int threads) {
+    uint64_t b = (work + threads - 1) / threads;
+    const uint64_t cap = 152ull * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+cudaError_t launch_gate1(bool fp64, void *sv, int n, int q, const double *m, cudaStream_t st) {
+    const uint64_t np = 1ull << (n - 1);
+    if (!fp64) {
+        M2<float> g;
+        for (int i = 0; i < 8; i++) g.m[i] = (float)m[i];
+        k_gate1<float><<<grid_for(np, 256), 256, 0, st>>>((float2 *)sv, q, np, g);
+    } else {
+        M2<double> g;
+        for (int i = 0; i < 8; i++) g.m[i] = m[i];
+        k_gate1<double><<<grid_for(np, 256), 256, 0, st>>>((double2 *)sv, q, np, g);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gate2(bool fp64, void *sv, int n, int q0, int q1, const double *m, cudaStream_t st) {
+    const uint64_t nq = 1ull << (n - 2);
+    if (!fp64) {
+        M4<float> g;
+        for (int i = 0; i < 32; i++) g.m[i] = (float)m[i];
+        k_gate2<float><<<grid_for(nq, 256), 256, 0, st>>>((float2 *)sv, q0, q1, nq, g);
+    } else {
+        M4<double> g;
+        for (int i = 0; i < 32; i++) g.m[i] = m[i];
+        k_gate2<double><<<grid_for(nq, 256), 256, 0, st>>>((double2 *)sv, q0, q1, nq, g);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// probabilities and norm
+// ------------------------------------------------------------------------
+template <typename Real, typename Out>
+__global__ void __launch_bounds__(256) k_probs(const typename CT<Real>::T *__restrict__ sv, uint64_t N,
+                                                Out *__restrict__ out, double *__restrict__ partials) {
+    typedef typename CT<Real>::T C;
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+        const C v = __ldcs(sv + i);
+        const double re = (double)v.x, im = (double)v.y;
+        const double p = re * re + im * im;
+        if (out) out[i] = (Out)p;
+        acc += p;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_sum(const double *__restrict__ partials, int nb, double *__restrict__ out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partials[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+cudaError_t launch_probs(bool fp64, const void *sv, int n, void *out, int out_fp64, double *partials,
+                         int nblocks, double *d_norm, cudaStream_t st) {
+    const uint64_t N = 1ull << n;
+    uint64_t need = (N + 255) / 256;
+    int nb = (int)(need < (uint64_t)nblocks ? need : (uint64_t)nblocks);
+    if (nb < 1) nb = 1;
+    if (!fp64) {
+        if (out_fp64) k_probs<float, double><<<nb, 256, 0, st>>>((const float2 *)sv, N, (double *)out, partials);
+        else k_probs<float, float><<<nb, 256, 0, st>>>((const float2 *)sv, N, (float *)out, partials);
+    } else {
+        if (out_fp64) k_probs<double, double><<<nb, 256, 0, st>>>((const double2 *)sv, N, (double *)out, partials);
+        else k_probs<double, float><<<nb, 256, 0, st>>>((const double2 *)sv, N, (float *)out, partials);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sum<<<1, 256, 0, st>>>(partials, nb, d_norm);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+__global__ void k_set_one(typename CT<Real>::T *sv, uint64_t idx) {
+    typename CT<Real>::T v;
+    v.x = Real(1);
+    v.y = Real(0);
+    sv[idx] = v;
+}
+
+cudaError_t launch_set_basis(bool fp64, void *sv, int n, uint64_t idx, cudaStream_t st) {
+    const size_t bytes = (fp64 ? 16ull : 8ull) << n;
+    cudaError_t e = cudaMemsetAsync(sv, 0, bytes, st);
+    if (e != cudaSuccess) return e;
+    if (fp64) k_set_one<double><<<1, 1, 0, st>>>((double2 *)sv, idx);
+    else k_set_one<float><<<1, 1, 0, st>>>((float2 *)sv, idx);
+    return cudaGetLastError();
+}
+
+}  // namespace hisv

@@ -1,0 +1,539 @@
+// Gate DAG and the Nat / DFS / dagP part builders (Sec. IV of the paper).
+//
+// Readings of details the paper leaves open (shared with the design notes):
+//  * Nat (Sec. IV-B): gate g joins the open part iff L(part + g) <= k; else
+//    the part is closed and g opens the next one.
+//  * DFS (Sec. IV-B): trial r draws from SplitMix64(seed ^ r*0x9E3779B97F4A7C15);
+//    the order is a LIFO Kahn traversal: source gates shuffled (Fisher-Yates)
+//    onto a stack, each popped gate emitted, its successors that become ready
+//    (operand order) shuffled and pushed. Fewest parts wins, ties to lowest r.
+//  * dagP (Sec. IV-B): (1) acyclic agglomerative clustering from single gates
+//    over pairs that share a qubit; (2) recursive bisection of the clusters,
+//    taken in Kahn order keyed by smallest gate, by the prefix cut minimising
+//    L(V1) + L(V2) with the larger side at most floor(3W/4) gates (imbalance
+//    ratio 1.5), refined by single-cluster moves of positive gain that keep V1
+//    a down-set, until every piece has L <= k; (3) merge phase on the part
+//    graph over all pairs. A merge takes the valid pair (L(a u b) <= k and no
+//    path of length >= 2 between a and b, so the part graph stays acyclic)
+//    with the most shared qubits, ties to the smaller (min gate, max gate) key.
+//  * Schedule: Kahn order of the part graph, ties to the part holding the
+//    smallest gate index (parts run in topological order, Sec. IV-A).
+#include "partition.hpp"
+
+#include <algorithm>
+#include <functional>
+#include <map>
+#include <queue>
+#include <set>
+#include <tuple>
+
+namespace hisv {
+
+static inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+bool build_dag(const std::vector<GateRef> &gates, int n, Dag &dag, std::string &err) {
+    dag.n = n;
+    dag.G = (int)gates.size();
+    dag.qmask.assign(dag.G, 0);
+    dag.preds.assign(dag.G, {});
+    dag.succs.assign(dag.G, {});
+    dag.qubits.assign(dag.G, {});
+    std::vector<int> last(n, -1);
+    // next[g][j]: gate after g on its j-th operand wire
+    std::vector<std::vector<int>> next(dag.G);
+    for (int g = 0; g < dag.G; g++) {
+        const GateRef &gr = gates[g];
+        uint64_t m = 0;
+        next[g].assign(gr.arity, -1);
+        for (int j = 0; j < gr.arity; j++) {
+            int q = gr.q[j];
+            if (q < 0 || q >= n) {
+                err = "gate " + std::to_string(g) + ": qubit " + std::to_string(q) + " out of range";
+                return false;
+            }
+            if ((m >> q) & 1) {
+                err = "gate " + std::to_string(g) + ": repeated qubit " + std::to_string(q);
+                return false;
+            }
+            m |= 1ull << q;
+            dag.qubits[g].push_back(q);
+            int p = last[q];
+            if (p >= 0) {
+                if (std::find(dag.preds[g].begin(), dag.preds[g].end(), p) == dag.preds[g].end())
+                    dag.preds[g].push_back(p);
+                for (int jj = 0; jj < (int)dag.qubits[p].size(); jj++)
+                    if (dag.qubits[p][jj] == q) next[p][jj] = g;
+            }
+        }
+        for (int j = 0; j < gr.arity; j++) last[gr.q[j]] = g;
+        dag.qmask[g] = m;
+    }
+    for (int p = 0; p < dag.G; p++)
+        for (int s : next[p])
+            if (s >= 0 && std::find(dag.succs[p].begin(), dag.succs[p].end(), s) == dag.succs[p].end())
+                dag.succs[p].push_back(s);
+    return true;
+}
+
+// ------------------------------------------------------------ schedule ---
+std::vector<uint32_t> schedule_parts(const Dag &dag, const std::vector<uint32_t> &pog) {
+    if (dag.G == 0) return {};
+    uint32_t P = 0;
+    for (uint32_t p : pog) P = std::max(P, p + 1);
+    std::vector<int> mg(P, -1);
+    for (int g = 0; g < dag.G; g++)
+        if (mg[pog[g]] < 0) mg[pog[g]] = g;
+    std::vector<std::set<uint32_t>> succ(P);
+    for (int g = 0; g < dag.G; g++)
+        for (int s : dag.succs[g])
+            if (pog[s] != pog[g]) succ[pog[g]].insert(pog[s]);
+    std::vector<int> indeg(P, 0);
+    for (uint32_t a = 0; a < P; a++)
+        for (uint32_t b : succ[a]) indeg[b]++;
+    typedef std::pair<int, uint32_t> E;
+    std::priority_queue<E, std::vector<E>, std::greater<E>> h;
+    for (uint32_t a = 0; a < P; a++)
+        if (indeg[a] == 0) h.push({mg[a], a});
+    std::vector<uint32_t> newid(P, UINT32_MAX);
+    uint32_t nxt = 0;
+    while (!h.empty()) {
+        uint32_t a = h.top().second;
+        h.pop();
+        newid[a] = nxt++;
+        for (uint32_t b : succ[a])
+            if (--indeg[b] == 0) h.push({mg[b], b});
+    }
+    std::vector<uint32_t> out(dag.G);
+    for (int g = 0; g < dag.G; g++) out[g] = newid[pog[g]];
+    return out;
+}
+
+static std::vector<std::vector<int>> cut_order(const Dag &dag, const std::vector<int> &order, int k) {
+    std::vector<std::vector<int>> parts;
+    std::vector<int> cur;
+    uint64_t m = 0;
+    for (int g : order) {
+        uint64_t gm = dag.qmask[g];
+        if (!cur.empty() && popc(m | gm) > k) {
+            parts.push_back(cur);
+            cur.clear();
+            m = 0;
+        }
+        cur.push_back(g);
+        m |= gm;
+    }
+    if (!cur.empty()) parts.push_back(cur);
+    return parts;
+}
+
+static std::vector<uint32_t> parts_to_pog(int G, const std::vector<std::vector<int>> &parts) {
+    std::vector<uint32_t> pog(G, 0);
+    for (size_t i = 0; i < parts.size(); i++)
+        for (int g : parts[i]) pog[g] = (uint32_t)i;
+    return pog;
+}
+
+std::vector<uint32_t> part_nat(const Dag &dag, int k) {
+    std::vector<int> order(dag.G);
+    for (int i = 0; i < dag.G; i++) order[i] = i;
+    return schedule_parts(dag, parts_to_pog(dag.G, cut_order(dag, order, k)));
+}
+
+// ----------------------------------------------------------------- DFS ---
+namespace {
+struct SplitMix64 {  // Steele, Lea, Flood (2014)
+    uint64_t s;
+    explicit SplitMix64(uint64_t seed) : s(seed) {}
+    uint64_t next() {
+        s += 0x9E3779B97F4A7C15ull;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    void shuffle(std::vector<int> &a) {
+        for (int i = (int)a.size() - 1; i > 0; i--) {
+            int j = (int)(next() % (uint64_t)(i + 1));
+            std::swap(a[i], a[j]);
+        }
+    }
+};
+}  // namespace
+
+std::vector<uint32_t> part_dfs(const Dag &dag, int k, uint64_t seed, int trials) {
+    if (trials <= 0) trials = 16;
+    std::vector<std::vector<int>> best;
+    bool have = false;
+    for (int r = 0; r < trials; r++) {
+        SplitMix64 rng(seed ^ ((uint64_t)r * 0x9E3779B97F4A7C15ull));
+        std::vector<int> indeg(dag.G);
+        for (int g = 0; g < dag.G; g++) indeg[g] = (int)dag.preds[g].size();
+        std::vector<int> stack;
+        for (int g = 0; g < dag.G; g++)
+            if (indeg[g] == 0) stack.push_back(g);
+        rng.shuffle(stack);
+        std::vector<int> order;
+        order.reserve(dag.G);
+        while (!stack.empty()) {
+            int g = stack.back();
+            stack.pop_back();
+            order.push_back(g);
+            std::vector<int> newly;
+            for (int s : dag.succs[g])
+                if (--indeg[s] == 0) newly.push_back(s);
+            rng.shuffle(newly);
+            stack.insert(stack.end(), newly.begin(), newly.end());
+        }
+        auto parts = cut_order(dag, order, k);
+        if (!have || parts.size() < best.size()) {
+            best = parts;
+            have = true;
+        }
+    }
+    return schedule_parts(dag, parts_to_pog(dag.G, best));
+}
+
+// ---------------------------------------------------------------- dagP ---
+namespace {
+
+// Units: groups of gates with their part graph and reachability bitsets.
+struct Units {
+    const Dag *dag;
+    int words = 0;
+    std::vector<char> alive;
+    std::vector<std::vector<int>> gates;
+    std::vector<uint64_t> qm;
+    std::vector<int> mg;
+    std::vector<std::set<int>> succ, pred;
+    std::vector<std::vector<uint64_t>> reach;  // units reachable by >= 1 edge
+    int next_id = 0;
+
+    bool bit(const std::vector<uint64_t> &r, int i) const { return (r[i >> 6] >> (i & 63)) & 1; }
+
+    Units(const Dag &d, const std::vector<std::vector<int>> &groups) : dag(&d) {
+        int U = (int)groups.size();
+        int cap = 2 * U + 2;
+        words = (cap + 63) / 64;
+        alive.assign(cap, 0);
+        gates.assign(cap, {});
+        qm.assign(cap, 0);
+        mg.assign(cap, 0);
+        succ.assign(cap, {});
+        pred.assign(cap, {});
+        reach.assign(cap, std::vector<uint64_t>());
+        std::vector<int> unit_of(d.G, 0);
+        for (int i = 0; i < U; i++) {
+            gates[i] = groups[i];
+            std::sort(gates[i].begin(), gates[i].end());
+            uint64_t m = 0;
+            for (int g : gates[i]) {
+                m |= d.qmask[g];
+                unit_of[g] = i;
+            }
+            qm[i] = m;
+            mg[i] = gates[i][0];
+            alive[i] = 1;
+        }
+        next_id = U;
+        for (int g = 0; g < d.G; g++)
+            for (int t : d.succs[g]) {
+                int a = unit_of[g], b = unit_of[t];
+                if (a != b) {
+                    succ[a].insert(b);
+                    pred[b].insert(a);
+                }
+            }
+        std::vector<int> order = topo();
+        for (int i = (int)order.size() - 1; i >= 0; i--) {
+            int u = order[i];
+            reach[u].assign(words, 0);
+            for (int v : succ[u]) {
+                reach[u][v >> 6] |= 1ull << (v & 63);
+                for (int w = 0; w < words; w++) reach[u][w] |= reach[v][w];
+            }
+        }
+    }
+
+    std::vector<int> live() const {
+        std::vector<int> out;
+        for (int i = 0; i < next_id; i++)
+            if (alive[i]) out.push_back(i);
+        return out;
+    }
+
+    // Kahn order keyed by each unit's smallest gate.
+    std::vector<int> topo() const {
+        std::vector<int> L = live();
+        std::map<int, int> indeg;
+        for (int u : L) indeg[u] = 0;
+        for (int u : L)
+            for (int v : succ[u]) indeg[v]++;
+        typedef std::pair<int, int> E;
+        std::priority_queue<E, std::vector<E>, std::greater<E>> h;
+        for (int u : L)
+            if (indeg[u] == 0) h.push({mg[u], u});
+        std::vector<int> out;
+        while (!h.empty()) {
+            int u = h.top().second;
+            h.pop();
+            out.push_back(u);
+            for (int v : succ[u])
+                if (--indeg[v] == 0) h.push({mg[v], v});
+        }
+        return out;
+    }
+
+    bool long_path(int a, int b) const {
+        for (int c : succ[a])
+            if (bit(reach[c], b)) return true;
+        for (int c : succ[b])
+            if (bit(reach[c], a)) return true;
+        return false;
+    }
+
+    int merge(int a, int b) {
+        int c = next_id++;
+        std::vector<int> g;
+        std::merge(gates[a].begin(), gates[a].end(), gates[b].begin(), gates[b].end(), std::back_inserter(g));
+        gates[c] = std::move(g);
+        gates[a].clear();
+        gates[b].clear();
+        qm[c] = qm[a] | qm[b];
+        mg[c] = std::min(mg[a], mg[b]);
+        alive[a] = alive[b] = 0;
+        alive[c] = 1;
+        std::set<int> sc, pc;
+        for (int x : succ[a]) if (x != a && x != b) sc.insert(x);
+        for (int x : succ[b]) if (x != a && x != b) sc.insert(x);
+        for (int x : pred[a]) if (x != a && x != b) pc.insert(x);
+        for (int x : pred[b]) if (x != a && x != b) pc.insert(x);
+        succ[a].clear(); succ[b].clear(); pred[a].clear(); pred[b].clear();
+        for (int x : sc) { pred[x].erase(a); pred[x].erase(b); pred[x].insert(c); }
+        for (int x : pc) { succ[x].erase(a); succ[x].erase(b); succ[x].insert(c); }
+        succ[c] = std::move(sc);
+        pred[c] = std::move(pc);
+        std::vector<uint64_t> rc(words, 0);
+        for (int w = 0; w < words; w++) rc[w] = reach[a][w] | reach[b][w];
+        rc[a >> 6] &= ~(1ull << (a & 63));
+        rc[b >> 6] &= ~(1ull << (b & 63));
+        for (int x = 0; x < next_id; x++) {
+            if (!alive[x] || x == c) continue;
+            std::vector<uint64_t> &r = reach[x];
+            if (bit(r, a) || bit(r, b)) {
+                r[a >> 6] &= ~(1ull << (a & 63));
+                r[b >> 6] &= ~(1ull << (b & 63));
+                r[c >> 6] |= 1ull << (c & 63);
+                for (int w = 0; w < words; w++) r[w] |= rc[w];
+            }
+        }
+        reach[a].clear();
+        reach[b].clear();
+        reach[c] = std::move(rc);
+        return c;
+    }
+
+    // Merge rule: smallest key (-shared, min mg, max mg) among valid pairs.
+    void merge_loop(int k, bool zero_shared) {
+        typedef std::tuple<int, int, int, int, int> Key;
+        std::priority_queue<Key, std::vector<Key>, std::greater<Key>> heap;
+        int n = dag->n;
+        std::vector<std::set<int>> byq(n);
+        for (int u : live())
+            for (int q = 0; q < n; q++)
+                if ((qm[u] >> q) & 1) byq[q].insert(u);
+        auto push = [&](int a, int b) {
+            if (popc(qm[a] | qm[b]) > k) return;
+            int m1 = std::min(mg[a], mg[b]), m2 = std::max(mg[a], mg[b]);
+            heap.push(Key(-popc(qm[a] & qm[b]), m1, m2, a, b));
+        };
+        auto sharing = [&](int u) {
+            std::set<int> out;
+            for (int q = 0; q < n; q++)
+                if ((qm[u] >> q) & 1) out.insert(byq[q].begin(), byq[q].end());
+            out.erase(u);
+            return out;
+        };
+        for (int u : live())
+            for (int v : sharing(u))
+                if (v > u) push(u, v);
+        bool zero_done = false;
+        while (true) {
+            if (heap.empty()) {
+                if (!zero_shared || zero_done) break;
+                zero_done = true;
+                std::vector<int> L = live();
+                for (size_t i = 0; i < L.size(); i++)
+                    for (size_t j = i + 1; j < L.size(); j++)
+                        if (!(qm[L[i]] & qm[L[j]])) push(L[i], L[j]);
+                if (heap.empty()) break;
+                continue;
+            }
+            Key top = heap.top();
+            heap.pop();
+            int a = std::get<3>(top), b = std::get<4>(top);
+            if (!alive[a] || !alive[b]) continue;
+            if (long_path(a, b)) continue;
+            uint64_t m = qm[a] | qm[b];
+            int c = merge(a, b);
+            for (int q = 0; q < n; q++)
+                if ((m >> q) & 1) {
+                    byq[q].erase(a);
+                    byq[q].erase(b);
+                    byq[q].insert(c);
+                }
+            if (zero_done) {
+                for (int v : live())
+                    if (v != c) push(v, c);
+            } else {
+                for (int v : sharing(c)) push(v, c);
+            }
+        }
+    }
+};
+
+// Prefix cut of a unit sequence (see the file header).
+static void bisect_units(const Units &U, const std::vector<int> &seq, std::vector<int> &V1,
+                         std::vector<int> &V2, long &cap) {
+    int m = (int)seq.size();
+    std::vector<long> w(m), prew(m + 1, 0);
+    std::vector<int> pre(m + 1, 0), suf(m + 1, 0);
+    long W = 0;
+    uint64_t mask = 0;
+    for (int i = 0; i < m; i++) {
+        w[i] = (long)U.gates[seq[i]].size();
+        W += w[i];
+        mask |= U.qm[seq[i]];
+        pre[i + 1] = popc(mask);
+        prew[i + 1] = prew[i] + w[i];
+    }
+    mask = 0;
+    for (int i = m - 1; i >= 0; i--) {
+        mask |= U.qm[seq[i]];
+        suf[i] = popc(mask);
+    }
+    cap = (3 * W) / 4;
+    bool have = false;
+    std::tuple<long, long, int> best;
+    for (int pass = 0; pass < 2 && !have; pass++) {
+        for (int c = 1; c < m; c++) {
+            if (pass == 0 && std::max(prew[c], W - prew[c]) > cap) continue;
+            std::tuple<long, long, int> key((long)pre[c] + suf[c], std::labs(2 * prew[c] - W), c);
+            if (!have || key < best) {
+                best = key;
+                have = true;
+            }
+        }
+    }
+    int c = std::get<2>(best);
+    cap = std::max(cap, std::max(prew[c], W - prew[c]));
+    V1.assign(seq.begin(), seq.begin() + c);
+    V2.assign(seq.begin() + c, seq.end());
+}
+
+static void refine_units(const Units &U, const std::vector<int> &seq, std::vector<int> &V1,
+                         std::vector<int> &V2, long cap) {
+    int n = U.dag->n;
+    std::map<int, int> side;
+    std::set<int> inP(seq.begin(), seq.end());
+    for (int u : V1) side[u] = 1;
+    for (int u : V2) side[u] = 2;
+    std::vector<long> cnt[3];
+    cnt[1].assign(n, 0);
+    cnt[2].assign(n, 0);
+    std::map<int, std::vector<std::pair<int, long>>> use;  // unit -> (qubit, gate count)
+    for (int u : seq) {
+        std::vector<long> uq(n, 0);
+        for (int g : U.gates[u])
+            for (int q : U.dag->qubits[g]) uq[q]++;
+        for (int q = 0; q < n; q++)
+            if (uq[q]) {
+                use[u].push_back({q, uq[q]});
+                cnt[side[u]][q] += uq[q];
+            }
+    }
+    long size[3] = {0, (long)V1.size(), (long)V2.size()};
+    long wt[3] = {0, 0, 0};
+    for (int u : V1) wt[1] += (long)U.gates[u].size();
+    for (int u : V2) wt[2] += (long)U.gates[u].size();
+    std::vector<int> order(seq);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return U.mg[a] < U.mg[b]; });
+    long moves = 0, limit = 4 * (long)seq.size();
+    while (moves < limit) {
+        int bestg = 0, bestu = -1;
+        for (int u : order) {
+            int s = side[u], o = 3 - s;
+            if (size[s] == 1 || wt[o] + (long)U.gates[u].size() > cap) continue;
+            bool blocked = false;
+            if (s == 1) {
+                for (int x : U.succ[u])
+                    if (inP.count(x) && side[x] == 1) { blocked = true; break; }
+            } else {
+                for (int x : U.pred[u])
+                    if (inP.count(x) && side[x] == 2) { blocked = true; break; }
+            }
+            if (blocked) continue;
+            int gain = 0;
+            for (auto &qc : use[u]) {
+                if (cnt[s][qc.first] == qc.second) gain++;
+                if (cnt[o][qc.first] == 0) gain--;
+            }
+            if (gain > 0 && (bestu < 0 || gain > bestg)) {
+                bestg = gain;
+                bestu = u;
+            }
+        }
+        if (bestu < 0) break;
+        int u = bestu, s = side[u], o = 3 - s;
+        for (auto &qc : use[u]) {
+            cnt[s][qc.first] -= qc.second;
+            cnt[o][qc.first] += qc.second;
+        }
+        side[u] = o;
+        size[s]--;
+        size[o]++;
+        wt[s] -= (long)U.gates[u].size();
+        wt[o] += (long)U.gates[u].size();
+        moves++;
+    }
+    V1.clear();
+    V2.clear();
+    for (int u : seq) (side[u] == 1 ? V1 : V2).push_back(u);
+}
+
+}  // namespace
+
+std::vector<uint32_t> part_dagp(const Dag &dag, int k) {
+    if (dag.G == 0) return {};
+    std::vector<std::vector<int>> singles(dag.G);
+    for (int g = 0; g < dag.G; g++) singles[g] = {g};
+    Units U(dag, singles);
+    U.merge_loop(k, false);                       // (1) coarsening
+    std::vector<std::vector<int>> leaves;         // (2) recursive bisection
+    std::vector<std::vector<int>> stack;
+    stack.push_back(U.topo());
+    while (!stack.empty()) {
+        std::vector<int> seq = std::move(stack.back());
+        stack.pop_back();
+        uint64_t m = 0;
+        for (int u : seq) m |= U.qm[u];
+        if (popc(m) <= k) {
+            std::vector<int> leaf;
+            for (int u : seq) leaf.insert(leaf.end(), U.gates[u].begin(), U.gates[u].end());
+            leaves.push_back(leaf);
+            continue;
+        }
+        std::vector<int> V1, V2;
+        long cap = 0;
+        bisect_units(U, seq, V1, V2, cap);
+        refine_units(U, seq, V1, V2, cap);
+        stack.push_back(V2);
+        stack.push_back(V1);
+    }
+    Units M(dag, leaves);                         // (3) merge phase
+    M.merge_loop(k, true);
+    std::vector<std::vector<int>> parts;
+    for (int u : M.live()) parts.push_back(M.gates[u]);
+    return schedule_parts(dag, parts_to_pog(dag.G, parts));
+}
+
+}  // namespace hisv

@@ -1,0 +1,310 @@
+// Part planner (host): for each part of the partition, fix its tile, split
+// its gates into register phases and emit the kernel's op stream.
+//
+//  * Tile: the part's qubits S (|S| <= k) padded with the lowest qubits not
+//    in S up to t (Sec. IV-B, multi-level partitioning: a part smaller than
+//    the limit takes extra qubits for spatial locality). Slot p of the tile
+//    holds the p-th smallest tile qubit; the n - t others are the outer
+//    qubits of Algorithm 1, one CTA per binary assignment of them.
+//  * Phases: a second partitioning level inside the part, with limit R on
+//    the qubits that need register residency (targets of non-diagonal
+//    gates). Gates are taken greedily along the part's gate order; a gate
+//    that does not fit blocks its qubits for the rest of the phase, so every
+//    qubit keeps its gate order (the schedule rule of Sec. IV-A).
+//    Diagonal gates and CX controls need no residency: on a thread bit they
+//    become per-thread conditions or a per-thread phase.
+//  * SWAP gates cost nothing: they exchange the slots of their two qubits
+//    for the rest of the part, and the store uses the final slot map.
+#include "planner.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "../../include/hisvsim.h"
+
+namespace hisv {
+
+static inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+bool gate_is_two_qubit(int kind) {
+    return kind == SV_GATE_CX || kind == SV_GATE_CZ || kind == SV_GATE_CP || kind == SV_GATE_SWAP;
+}
+
+void gate_matrix_1q(int kind, double th, double m[8]) {
+    for (int i = 0; i < 8; i++) m[i] = 0.0;
+    const double c = std::cos(th / 2), s = std::sin(th / 2), r = std::sqrt(0.5);
+    switch (kind) {
+    case SV_GATE_H: m[0] = r; m[2] = r; m[4] = r; m[6] = -r; break;
+    case SV_GATE_X: m[2] = 1; m[4] = 1; break;
+    case SV_GATE_Y: m[3] = -1; m[5] = 1; break;          // [[0,-i],[i,0]]
+    case SV_GATE_Z: m[0] = 1; m[6] = -1; break;
+    case SV_GATE_S: m[0] = 1; m[7] = 1; break;
+    case SV_GATE_T: m[0] = 1; m[6] = r; m[7] = r; break;
+    case SV_GATE_RX: m[0] = c; m[3] = -s; m[5] = -s; m[6] = c; break;
+    case SV_GATE_RY: m[0] = c; m[2] = -s; m[4] = s; m[6] = c; break;
+    case SV_GATE_RZ: m[0] = c; m[1] = -s; m[6] = c; m[7] = s; break;
+    case SV_GATE_P: m[0] = 1; m[6] = std::cos(th); m[7] = std::sin(th); break;
+    default: break;
+    }
+}
+
+void gate_matrix_2q(int kind, double th, double m[32]) {
+    for (int i = 0; i < 32; i++) m[i] = 0.0;
+    auto set = [&](int r, int c, double re, double im) { m[2 * (4 * r + c)] = re; m[2 * (4 * r + c) + 1] = im; };
+    switch (kind) {
+    case SV_GATE_CX:   // l = b_c + 2 b_t: l=1 <-> l=3
+        set(0, 0, 1, 0); set(2, 2, 1, 0); set(1, 3, 1, 0); set(3, 1, 1, 0); break;
+    case SV_GATE_CZ:
+        set(0, 0, 1, 0); set(1, 1, 1, 0); set(2, 2, 1, 0); set(3, 3, -1, 0); break;
+    case SV_GATE_CP:
+        set(0, 0, 1, 0); set(1, 1, 1, 0); set(2, 2, 1, 0); set(3, 3, std::cos(th), std::sin(th)); break;
+    case SV_GATE_SWAP:
+        set(0, 0, 1, 0); set(1, 2, 1, 0); set(2, 1, 1, 0); set(3, 3, 1, 0); break;
+    default: break;
+    }
+}
+
+// slots that must be register bits for this gate
+static uint32_t needed_slots(const GateRef &g, const int *slot_of) {
+    switch (g.kind) {
+    case SV_GATE_H: case SV_GATE_X: case SV_GATE_Y: case SV_GATE_RX: case SV_GATE_RY:
+        return 1u << slot_of[g.q[0]];
+    case SV_GATE_CX:
+        return 1u << slot_of[g.q[1]];
+    default:
+        return 0u;
+    }
+}
+
+// Thread-bit order of a phase: lane bits first. The first lanes cover
+// distinct slot residues (mod 4 for 8-byte, mod 3 for 16-byte amplitudes) so
+// the swizzled shared-memory accesses are conflict free; otherwise slots
+// follow the preference key (lowest global qubit first for the phases that
+// load or store, for coalescing).
+static std::vector<int> order_thread_slots(std::vector<int> cand, const std::vector<int> &key, bool fp64) {
+    std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) { return key[a] < key[b]; });
+    const int mod = fp64 ? 3 : 4;
+    std::vector<int> lanes, rest;
+    std::vector<char> used(cand.size(), 0);
+    uint32_t covered = 0;
+    for (size_t i = 0; i < cand.size() && (int)lanes.size() < mod; i++) {
+        int r = cand[i] % mod;
+        if (!((covered >> r) & 1)) {
+            covered |= 1u << r;
+            lanes.push_back(cand[i]);
+            used[i] = 1;
+        }
+    }
+    for (size_t i = 0; i < cand.size(); i++)
+        if (!used[i]) rest.push_back(cand[i]);
+    // fill to a full warp of lanes, then warp bits, in key order
+    std::vector<int> out = lanes;
+    for (int s : rest) out.push_back(s);
+    return out;
+}
+
+bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector<uint32_t> &pog,
+                     uint32_t n_parts, bool fp64, int t_cfg, int R, Program &prog, std::string &err) {
+    prog = Program();
+    prog.fp64 = fp64;
+    prog.R = R;
+    const int t = std::min(n, t_cfg);
+    prog.t = t;
+    if (t - R > MAX_TB || R > MAX_R || t < R + 5) {
+        err = "tile configuration out of range";
+        return false;
+    }
+    std::vector<std::vector<int>> members(n_parts);
+    for (size_t g = 0; g < gates.size(); g++) {
+        if (pog[g] >= n_parts) {
+            err = "part id out of range";
+            return false;
+        }
+        members[pog[g]].push_back((int)g);
+    }
+    std::vector<uint64_t> gmask(gates.size());
+    for (size_t g = 0; g < gates.size(); g++) {
+        uint64_t m = 0;
+        for (int j = 0; j < gates[g].arity; j++) m |= 1ull << gates[g].q[j];
+        gmask[g] = m;
+    }
+    const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    for (uint32_t pi = 0; pi < n_parts; pi++) {
+        const std::vector<int> &gl = members[pi];
+        if (gl.empty()) continue;
+        uint64_t S = 0;
+        for (int g : gl) S |= gmask[g];
+        if (popc(S) > t) {
+            err = "part " + std::to_string(pi) + " has " + std::to_string(popc(S)) + " qubits > tile " + std::to_string(t);
+            return false;
+        }
+        uint64_t Tm = S;
+        for (int q = 0; q < n && popc(Tm) < t; q++) Tm |= 1ull << q;
+        int slot_of[64], q_at[64];
+        for (int q = 0, p = 0; q < n; q++)
+            if ((Tm >> q) & 1) {
+                slot_of[q] = p;
+                q_at[p] = q;
+                p++;
+            }
+        PartLaunch L;
+        std::memset(&L, 0, sizeof(L));
+        L.outer_mask = all & ~Tm;
+        L.n = n;
+        L.t = t;
+        L.phase_begin = (uint32_t)prog.phases.size();
+        std::vector<int> remaining = gl;
+        bool first = true;
+        while (!remaining.empty()) {
+            // pass 1: choose the register slots and the gates of this phase
+            int sim_slot[64];
+            std::memcpy(sim_slot, slot_of, sizeof(slot_of));
+            uint32_t Rset = 0;
+            uint64_t blocked = 0;
+            std::vector<int> sched, rest;
+            for (int g : remaining) {
+                const GateRef &gr = gates[g];
+                if (gmask[g] & blocked) {
+                    blocked |= gmask[g];
+                    rest.push_back(g);
+                    continue;
+                }
+                uint32_t need = needed_slots(gr, sim_slot);
+                if ((need & ~Rset) && popc(Rset | need) > R) {
+                    blocked |= gmask[g];
+                    rest.push_back(g);
+                    continue;
+                }
+                Rset |= need;
+                sched.push_back(g);
+                if (gr.kind == SV_GATE_SWAP) std::swap(sim_slot[gr.q[0]], sim_slot[gr.q[1]]);
+            }
+            for (int p = t - 1; p >= 0 && popc(Rset) < R; p--) Rset |= 1u << p;
+            const bool last = rest.empty();
+            // slot -> qubit at the start and at the end of this phase
+            int q_start[64], q_end[64];
+            for (int q = 0; q < n; q++)
+                if ((Tm >> q) & 1) {
+                    q_start[slot_of[q]] = q;
+                    q_end[sim_slot[q]] = q;
+                }
+            Phase ph;
+            std::memset(&ph, 0, sizeof(ph));
+            int rb[64], tbit[64];
+            for (int p = 0, b = 0; p < t; p++)
+                if ((Rset >> p) & 1) {
+                    ph.reg[b] = (uint8_t)p;
+                    rb[p] = b++;
+                }
+            std::vector<int> cand;
+            std::vector<int> key(t, 0);
+            for (int p = 0; p < t; p++) {
+                if (!((Rset >> p) & 1)) cand.push_back(p);
+                key[p] = first ? q_start[p] : (last ? q_end[p] : p);
+            }
+            std::vector<int> thr = order_thread_slots(cand, key, fp64);
+            for (size_t j = 0; j < thr.size(); j++) {
+                ph.thr[j] = (uint8_t)thr[j];
+                tbit[thr[j]] = (int)j;
+            }
+            if (first) {
+                for (int b = 0; b < R; b++) L.load_reg_q[b] = (uint8_t)q_start[ph.reg[b]];
+                for (int j = 0; j < t - R; j++) L.load_thr_q[j] = (uint8_t)q_start[ph.thr[j]];
+            }
+            // pass 2: emit ops
+            ph.op_begin = (uint32_t)prog.ops.size();
+            bool tphase = false;
+            auto coef = [&](std::initializer_list<double> v) {
+                uint32_t at = (uint32_t)prog.coefs.size();
+                prog.coefs.insert(prog.coefs.end(), v.begin(), v.end());
+                return at;
+            };
+            auto emit = [&](uint8_t kind, int a, int b, int tb, uint32_t c) {
+                Op op;
+                op.kind = kind;
+                op.a = (uint8_t)a;
+                op.b = (uint8_t)b;
+                op.tb = (uint8_t)tb;
+                op.coef = c;
+                prog.ops.push_back(op);
+            };
+            for (int g : sched) {
+                const GateRef &gr = gates[g];
+                const double th = gr.theta;
+                const int s0 = slot_of[gr.q[0]];
+                const bool r0 = (Rset >> s0) & 1;
+                switch (gr.kind) {
+                case SV_GATE_H: emit(OP_H, rb[s0], 0, 0, 0); break;
+                case SV_GATE_X: emit(OP_X, rb[s0], 0, 0, 0); break;
+                case SV_GATE_Y: emit(OP_Y, rb[s0], 0, 0, 0); break;
+                case SV_GATE_RX: emit(OP_RX, rb[s0], 0, 0, coef({std::cos(th / 2), std::sin(th / 2)})); break;
+                case SV_GATE_RY: emit(OP_RY, rb[s0], 0, 0, coef({std::cos(th / 2), std::sin(th / 2)})); break;
+                case SV_GATE_Z: case SV_GATE_S: case SV_GATE_T: case SV_GATE_P: {
+                    double ang = gr.kind == SV_GATE_Z ? M_PI : gr.kind == SV_GATE_S ? M_PI / 2 : gr.kind == SV_GATE_T ? M_PI / 4 : th;
+                    double dr = gr.kind == SV_GATE_Z ? -1.0 : std::cos(ang), di = gr.kind == SV_GATE_Z ? 0.0 : std::sin(ang);
+                    if (gr.kind == SV_GATE_S) { dr = 0.0; di = 1.0; }
+                    if (r0) {
+                        if (gr.kind == SV_GATE_Z) emit(OP_Z, rb[s0], 0, 0, 0);
+                        else emit(OP_P, rb[s0], 0, 0, coef({dr, di}));
+                    } else {
+                        emit(OP_TD, 0, 0, tbit[s0], coef({1.0, 0.0, dr, di}));
+                        tphase = true;
+                    }
+                } break;
+                case SV_GATE_RZ: {
+                    const double c = std::cos(th / 2), s = std::sin(th / 2);
+                    if (r0) emit(OP_D, rb[s0], 0, 0, coef({c, -s, c, s}));
+                    else {
+                        emit(OP_TD, 0, 0, tbit[s0], coef({c, -s, c, s}));
+                        tphase = true;
+                    }
+                } break;
+                case SV_GATE_CX: {
+                    const int s1 = slot_of[gr.q[1]];
+                    if (r0) emit(OP_CX, rb[s0], rb[s1], 0, 0);
+                    else emit(OP_CXT, 0, rb[s1], tbit[s0], 0);
+                } break;
+                case SV_GATE_CZ: case SV_GATE_CP: {
+                    const int s1 = slot_of[gr.q[1]];
+                    const bool r1 = (Rset >> s1) & 1;
+                    const bool cz = gr.kind == SV_GATE_CZ;
+                    const double dr = cz ? -1.0 : std::cos(th), di = cz ? 0.0 : std::sin(th);
+                    if (r0 && r1) {
+                        if (cz) emit(OP_CZ, rb[s0], rb[s1], 0, 0);
+                        else emit(OP_CP, rb[s0], rb[s1], 0, coef({dr, di}));
+                    } else if (r0 || r1) {
+                        const int rs = r0 ? s0 : s1, ts = r0 ? s1 : s0;
+                        if (cz) emit(OP_CZT, rb[rs], 0, tbit[ts], 0);
+                        else emit(OP_CPT, rb[rs], 0, tbit[ts], coef({dr, di}));
+                    } else {
+                        emit(OP_TP2, 0, tbit[s1], tbit[s0], coef({dr, di}));
+                        tphase = true;
+                    }
+                } break;
+                case SV_GATE_SWAP:
+                    std::swap(slot_of[gr.q[0]], slot_of[gr.q[1]]);
+                    break;
+                default:
+                    err = "unknown gate kind";
+                    return false;
+                }
+            }
+            if (tphase) emit(OP_TAPPLY, 0, 0, 0, 0);
+            ph.op_count = (uint32_t)prog.ops.size() - ph.op_begin;
+            prog.phases.push_back(ph);
+            if (last) {
+                for (int b = 0; b < R; b++) L.store_reg_q[b] = (uint8_t)q_end[ph.reg[b]];
+                for (int j = 0; j < t - R; j++) L.store_thr_q[j] = (uint8_t)q_end[ph.thr[j]];
+            }
+            remaining.swap(rest);
+            first = false;
+        }
+        L.n_phases = (uint32_t)prog.phases.size() - L.phase_begin;
+        prog.parts.push_back(L);
+        prog.n_tiles.push_back(1ull << (n - t));
+    }
+    return true;
+}
+
+}  // namespace hisv

@@ -1,0 +1,33 @@
+// Part planner: turns a partition into the device program of the part kernel.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "partition.hpp"
+#include "program.hpp"
+
+namespace hisv {
+
+struct Program {
+    bool fp64 = false;
+    int t = 0;                           // tile qubits
+    int R = 0;                           // register bits per thread
+    std::vector<PartLaunch> parts;       // in execution order
+    std::vector<uint64_t> n_tiles;       // CTAs (outer assignments) per part
+    std::vector<Phase> phases;
+    std::vector<Op> ops;
+    std::vector<double> coefs;
+};
+
+// Gate matrices of the library (row-major complex, interleaved re/im):
+// 2x2 for 1-qubit kinds, 4x4 with local index l = b_q0 + 2 b_q1 for 2-qubit.
+void gate_matrix_1q(int kind, double theta, double m[8]);
+void gate_matrix_2q(int kind, double theta, double m[32]);
+bool gate_is_two_qubit(int kind);
+
+// Compile the parts (part_of_gate numbered in execution order) for a tile of
+// t_cfg qubits (t = min(n, t_cfg)) and R register bits.
+bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector<uint32_t> &pog,
+                     uint32_t n_parts, bool fp64, int t_cfg, int R, Program &prog, std::string &err);
+
+}  // namespace hisv

@@ -1,0 +1,138 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry
+point declared in include/hisvsim.h, the host partitioners agree bit-exactly
+with the oracle's, and argument errors come back as status codes."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import partition as pt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2205_06973_gb300 import build
+    build.build()
+    from paper_2205_06973_gb300 import _native
+    return _native
+
+
+def header_symbols():
+    syms = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            syms |= set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(sv_\w+)\s*\(", txt, flags=re.M))
+    return sorted(syms)
+
+
+def test_exports_every_declared_symbol(native):
+    syms = header_symbols()
+    assert "sv_create" in syms and "sv_apply_parts" in syms and "sv_measure_probs" in syms
+    for s in syms:
+        assert hasattr(native.lib, s), s
+
+
+def test_version(native):
+    assert b"sm_103a" in native.lib.sv_version()
+
+
+def _plan(native, gates, n, method, k, seed=0, trials=16):
+    from paper_2205_06973_gb300.api import Plan
+    return Plan(gates, n, method, k, seed=seed, dfs_trials=trials)
+
+
+def _rand(n, G, seed):
+    r = synth.SplitMix64(seed)
+    out = []
+    for _ in range(G):
+        c = r.randint(4)
+        if c == 0:
+            out.append((("H", "RX", "RZ", "T")[r.randint(4)], (r.randint(n),), r.angle()))
+        else:
+            a = r.randint(n)
+            b = (a + 1 + r.randint(n - 1)) % n
+            out.append((("CX", "CZ", "CP", "SWAP")[r.randint(4)], (a, b), r.angle()))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("method", ["nat", "dfs", "dagp"])
+def test_partition_bit_exact_random(native, seed, method):
+    n = 9 + seed % 5
+    k = 2 + seed % 6
+    g = _rand(n, 200 + 30 * seed, 500 + seed)
+    p = _plan(native, g, n, method, k, seed=seed, trials=4 + seed)
+    pog, P = p.export()
+    ref = pt.partition(g, n, method, k, seed=seed, trials=4 + seed)
+    assert list(pog) == ref
+    assert P == max(ref) + 1
+    pt.check_partition(g, n, k, ref)
+
+
+@pytest.mark.parametrize("k", [8, 10, 12])
+@pytest.mark.parametrize("method", ["nat", "dfs", "dagp"])
+def test_partition_bit_exact_layered_28(native, method, k):
+    n, g = synth.layered_28q()
+    pog, P = _plan(native, g, n, method, k).export()
+    assert list(pog) == pt.partition(g, n, method, k, seed=0)
+
+
+@pytest.mark.parametrize("k", [6, 12])
+def test_partition_bit_exact_qft_33(native, k):
+    n, g, _ = synth.qft_basis(33)
+    for method in ("nat", "dfs", "dagp"):
+        pog, P = _plan(native, g, n, method, k).export()
+        assert list(pog) == pt.partition(g, n, method, k, seed=0)
+
+
+def test_partition_bit_exact_param_batch(native):
+    for i in range(6):
+        n, g = synth.batch_circuit(i)
+        for method in ("nat", "dagp"):
+            pog, _ = _plan(native, g, n, method, 10).export()
+            assert list(pog) == pt.partition(g, n, method, 10)
+
+
+def test_plan_errors(native):
+    from paper_2205_06973_gb300.api import Plan
+    with pytest.raises(native.SvError) as e:
+        Plan([("CX", (0, 1), 0.0)], 2, "dagp", 1)
+    assert e.value.status == native.SV_ERR_PARTITION
+    with pytest.raises(native.SvError) as e:
+        Plan([("H", (3,), 0.0)], 2, "nat", 2)
+    assert e.value.status == native.SV_ERR_ARG
+    with pytest.raises(native.SvError) as e:
+        Plan([("CX", (1, 1), 0.0)], 2, "nat", 2)
+    assert e.value.status == native.SV_ERR_ARG
+    arr = native.encode_gates([("CX", (0, 1), 0.0)])
+    arr[0].arity = 1
+    h = ctypes.c_void_p()
+    st = native.lib.sv_plan_build(ctypes.cast(arr, ctypes.c_void_p), 1, 2, native.SV_PART_NAT, 2, 0, 0,
+                                  ctypes.byref(h))
+    assert st == native.SV_ERR_ARG
+    assert b"arity" in native.lib.sv_last_error()
+
+
+def test_plan_stats_counts(native):
+    n, g = synth.layered_28q(n=16, depth=10)
+    p = _plan(native, g, n, "dagp", 8)
+    s = p.stats("c64", 12)
+    pog, P = p.export()
+    assert s["passes"] == P
+    assert s["phases"] >= P
+    # every gate but SWAP becomes at least one op
+    assert s["ops"] >= len(g)
+
+
+def test_plan_tile_too_small(native):
+    n, g = synth.layered_28q(n=20, depth=4)
+    p = _plan(native, g, n, "dagp", 12)
+    with pytest.raises(native.SvError):
+        p.stats("c128", 11)    # a 12-qubit part cannot fit an 11-qubit tile

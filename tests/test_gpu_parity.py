@@ -1,0 +1,162 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle,
+element by element, at sizes the oracle finishes in seconds. Tolerances:
+max-abs 1e-5 for the complex64 state, 1e-12 for complex128."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import closed_form as cf
+from oracle import sim
+from tests.gpu_util import TOL, max_abs, native, random_state, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _all_kinds(n, G, seed):
+    r = synth.SplitMix64(seed)
+    gates = []
+    for _ in range(G):
+        name = synth.GATE_NAMES[r.randint(len(synth.GATE_NAMES))]
+        if name in synth.TWO_QUBIT:
+            a = r.randint(n)
+            b = (a + 1 + r.randint(n - 1)) % n
+            gates.append((name, (a, b), r.angle()))
+        else:
+            gates.append((name, (r.randint(n),), r.angle()))
+    return gates
+
+
+def test_cuda_available():
+    assert torch.cuda.is_available()
+
+
+@pytest.mark.parametrize("precision", ["c128", "c64"])
+def test_plain_layered_14q_gatewise(precision):
+    """14 qubits, 840 gates, one pass per gate, all 16384 amplitudes."""
+    n, g = synth.plain_layered_14q()
+    ref = sim.run(n, g)
+    out = run_gpu(n, g, gatewise=True, precision=precision)
+    assert max_abs(out, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["c128", "c64"])
+@pytest.mark.parametrize("method", ["nat", "dfs", "dagp"])
+def test_plain_layered_14q_parts(precision, method):
+    n, g = synth.plain_layered_14q()
+    ref = sim.run(n, g)
+    for k in (4, 8, 10):
+        out = run_gpu(n, g, method=method, k=k, precision=precision)
+        assert max_abs(out, ref) <= TOL[precision], (method, k)
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("n", [10, 11, 13, 15])
+def test_all_gate_kinds_parts(precision, n):
+    g = _all_kinds(n, 300, 40 + n)
+    psi = random_state(n, 3 + n)
+    ref = sim.run(n, g, psi)
+    for method, k in (("nat", 3), ("dfs", 5), ("dagp", 8), ("dagp", 10)):
+        out = run_gpu(n, g, method=method, k=k, precision=precision, psi=psi)
+        assert max_abs(out, ref) <= TOL[precision], (method, k)
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_all_gate_kinds_gatewise(precision):
+    n = 12
+    g = _all_kinds(n, 200, 9)
+    psi = random_state(n, 10)
+    ref = sim.run(n, g, psi)
+    out = run_gpu(n, g, gatewise=True, precision=precision, psi=psi)
+    assert max_abs(out, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("tile", [10, 11, 12, 13])
+def test_tiles_c64(tile):
+    n = 17
+    n_, g = synth.layered_28q(n=n, depth=12)
+    psi = random_state(n, 77)
+    ref = sim.run(n, g, psi)
+    for k in (6, min(tile, 10)):
+        out = run_gpu(n, g, method="dagp", k=k, precision="c64", tile=tile, psi=psi)
+        assert max_abs(out, ref) <= TOL["c64"], k
+
+
+@pytest.mark.parametrize("tile", [10, 11, 12])
+def test_tiles_c128(tile):
+    n = 16
+    _, g = synth.layered_28q(n=n, depth=10)
+    psi = random_state(n, 78)
+    ref = sim.run(n, g, psi)
+    out = run_gpu(n, g, method="dfs", k=min(tile, 9), precision="c128", tile=tile, psi=psi)
+    assert max_abs(out, ref) <= TOL["c128"]
+
+
+@pytest.mark.parametrize("method", ["nat", "dfs", "dagp"])
+@pytest.mark.parametrize("k", [8, 10, 12])
+def test_layered_20q_parts(method, k):
+    """The 28-qubit layered workload's recipe at 20 qubits (depth 20)."""
+    n, g = synth.layered_28q(n=20, depth=20)
+    ref = sim.run(n, g)
+    for precision in ("c64", "c128"):
+        if precision == "c128" and k > 12:
+            continue
+        out = run_gpu(n, g, method=method, k=k, precision=precision)
+        assert max_abs(out, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("n", [10, 14, 18])
+def test_qft_basis_closed_form(n):
+    x = synth.SplitMix64(3 + n).randint(1 << n)
+    g = synth.qft(n)
+    ref = cf.qft_basis_amplitude(n, x, np.arange(1 << n))
+    for method, k in (("nat", 6), ("dagp", 10)):
+        out = run_gpu(n, g, method=method, k=k, precision="c64", basis=x)
+        assert max_abs(out, ref) <= TOL["c64"]
+        out = run_gpu(n, g, method=method, k=k, precision="c128", basis=x)
+        assert max_abs(out, ref) <= TOL["c128"]
+
+
+def test_param_family():
+    for i in range(3):
+        n, g = synth.batch_circuit(i)
+        if n > 16:
+            continue
+        ref = sim.run(n, g)
+        out = run_gpu(n, g, method="dagp", k=10, precision="c64")
+        assert max_abs(out, ref) <= TOL["c64"]
+
+
+def test_small_n_runs_gatewise():
+    n = 6
+    g = _all_kinds(n, 80, 5)
+    ref = sim.run(n, g)
+    out = run_gpu(n, g, method="dagp", k=4, precision="c128")
+    assert max_abs(out, ref) <= TOL["c128"]
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_probs_and_norm(precision):
+    N_, api = native()
+    n = 16
+    _, g = synth.layered_28q(n=n, depth=6)
+    ref = sim.run(n, g)
+    plan = api.Plan(g, n, "dagp", 8)
+    st = api.State(n, precision)
+    st.apply(plan)
+    for fp64 in (False, True):
+        out = torch.empty(1 << n, dtype=torch.float64 if fp64 else torch.float32, device="cuda")
+        norm = st.probs(out, fp64=fp64)
+        p = out.cpu().numpy()
+        assert abs(norm - 1.0) < (1e-5 if precision == "c64" else 1e-12)
+        assert np.abs(p - np.abs(ref) ** 2).max() < (1e-6 if precision == "c64" else 1e-13)
+    assert abs(st.probs() - 1.0) < 1e-5
+    st.close()
+    plan.close()
+
+
+def test_empty_circuit_and_basis():
+    out = run_gpu(12, [], method="dagp", k=8, basis=37)
+    ref = np.zeros(1 << 12)
+    ref[37] = 1
+    assert max_abs(out, ref) == 0.0
