@@ -1,0 +1,364 @@
+"""Benchmark of the hierarchical state-vector hot path on GB300.
+
+One step = every part pass of the 28-qubit random layered circuit (depth 60,
+H/RX/RZ on every qubit then CX/CZ on a random disjoint pairing; 2520 gates)
+applied to a complex64 state resident in HBM, through the C ABI
+(sv_apply_parts). The metric is the part passes' algorithmic HBM traffic
+(2 x state bytes per pass) per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0. Under torchrun each rank runs an independent
+replica on its own GPU (the path has no exchange step on one GPU per state);
+value = all ranks' bytes / max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "state-vector part passes GB/s (HBM traffic of the passes / time)"
+UNIT = "GB/s"
+WORKLOAD = ("random layered circuit, 28 qubits, depth 60 (H/RX/RZ on every qubit, then CX/CZ on a "
+            "random disjoint pairing; 2520 gates, seed 2), complex64 state, part-fused passes")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--method", default="dagp", choices=["nat", "dfs", "dagp"])
+    ap.add_argument("--k", type=int, default=0, help="part qubit limit (0: autotuned default)")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--n", type=int, default=28)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "program.hpp", "planner.cpp"):
+        with open(os.path.join(ROOT, "paper_2205_06973_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(workload_key):
+    """DRAM bytes per part-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_part_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = kernel_source_hash()
+    with open(path) as f:
+        for line in f:
+            parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+            if parts.get("source") == cur and parts.get("workload") == workload_key:
+                try:
+                    return float(parts["bytes_per_launch"])
+                except (KeyError, ValueError):
+                    return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x, device):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def choose_k(method, k):
+    """Part limit: explicit, else the value the tuner cache holds, else 10."""
+    if k:
+        return k
+    try:
+        from paper_2205_06973_gb300 import autotune
+        return autotune.cached_k("layered28", method, "c64") or 10
+    except Exception:
+        return 10
+
+
+def cpu_baseline_oracle(n, gates, pog, n_parts, max_parts, budget_s=20.0):
+    """The oracle's Algorithm 1 mode (complex128, OpenMP on the host cores) on
+    the first parts of the same plan, until about budget_s of CPU time."""
+    import numpy as np
+    from oracle import sim
+    pog = np.asarray(pog, dtype=np.uint32)
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[0] = 1.0
+    done = 0
+    t0 = time.perf_counter()
+    while done < min(max_parts, n_parts):
+        sel = pog == done
+        sub = [g for g, s in zip(gates, sel) if s]
+        psi = sim.run_alg1(n, sub, [0] * len(sub), 1, psi)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    bytes_per_pass = 2 * 16 * (1 << n)
+    return {"value": bytes_per_pass * done / dt / 1e9, "unit": UNIT, "cores": sim.num_threads(),
+            "kind": "oracle",
+            "sample": f"first {done} of {n_parts} parts of the same plan, Algorithm 1 mode, complex128 "
+                      f"(32 B/amplitude per pass), {dt:.1f} s"}
+
+
+def run_ours(a):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import synth
+    from paper_2205_06973_gb300 import api
+
+    n, gates = synth.layered_28q(n=a.n)
+    k = choose_k(a.method, a.k)
+    plan = api.Plan(gates, n, a.method, k)
+    st = api.State(n, "c64", tile=a.tile)
+    stats = plan.stats("c64", a.tile)
+    passes = stats["passes"]
+    bytes_per_pass = 2 * st.nbytes
+    bytes_per_step = passes * bytes_per_pass
+
+    for _ in range(max(a.warmup, 3)):
+        st.apply(plan)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st.stream)
+    for _ in range(a.steps):
+        st.apply(plan)
+    e1.record(st.stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    ms = max_over_ranks(ws, ms, dev)
+    value = ws * bytes_per_step / (ms / 1e3) / 1e9
+    norm = st.probs()
+
+    # the step launches only the part kernel, back to back on the state's stream
+    launch_ms = ms / passes
+    peak, peak_kind = peaks()
+    achieved = bytes_per_pass / (launch_ms / 1e3) / 1e9
+    wkey = f"layered{n}_{a.method}_k{k}_c64_t{a.tile or 'auto'}"
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "traffic": traffic_from_profile(wkey), "kernel": "k_part",
+                "algorithmic_bytes_per_launch": bytes_per_pass, "launch_ms": round(launch_ms, 4)}
+
+    e2e = None
+    if not a.no_e2e:
+        host_in = torch.zeros(1 << n, dtype=torch.complex64).pin_memory()
+        host_in[0] = 1.0
+        host_out = torch.empty(1 << n, dtype=torch.complex64).pin_memory()
+        reps = 3
+        st.upload(host_in)
+        st.apply(plan)
+        st.copy_to_host(host_out)
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            st.upload(host_in)
+            st.apply(plan)
+            st.copy_to_host(host_out)       # synchronises the stream
+        dt = (time.perf_counter() - t0) / reps
+        dt = max_over_ranks(ws, dt, dev)
+        e2e = {"value": round(ws * bytes_per_step / dt / 1e9, 1), "unit": UNIT,
+               "h2d_bytes_per_step": st.nbytes, "d2h_bytes_per_step": st.nbytes,
+               "ms_per_step": round(dt * 1e3, 3),
+               "api": "sv_upload + sv_apply_parts + sv_copy_state (pinned host buffers)"}
+
+    compare = None
+    if not a.no_compare:
+        st.apply(plan, gatewise=True)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(st.stream)
+        st.apply(plan, gatewise=True)
+        g1.record(st.stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1)
+        compare = {"gate_by_gate_ms_per_step": round(gms, 3), "gate_passes": len(gates),
+                   "gate_by_gate_GBs": round(len(gates) * bytes_per_pass / (gms / 1e3) / 1e9, 1),
+                   "speedup_vs_gate_by_gate": round(gms / ms, 3)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu:
+        pog, P = plan.export()
+        cpu = cpu_baseline_oracle(n, gates, pog, P, max_parts=64, budget_s=20.0)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+                "warmup": max(a.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 arithmetic)", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_qubits": n, "gates": len(gates), "method": a.method,
+                           "k": k, "passes": passes, "phases": stats["phases"], "ops": stats["ops"],
+                           "state_bytes": st.nbytes, "parallelism": f"replicas x{ws}",
+                           "l2": "state (2 GiB) larger than L2 (129 MB); no flush needed"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": passes * a.steps, "compare": compare, "norm": norm}
+        print(json.dumps(line), flush=True)
+    st.close()
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(a):
+    """The oracle timed on the host cores: each step is one part pass of the
+    same plan in the oracle's Algorithm 1 mode (complex128)."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import synth
+    from oracle import partition as opart
+    from oracle import sim
+    import numpy as np
+    n, gates = synth.layered_28q(n=a.n)
+    k = choose_k(a.method, a.k)
+    pog = np.asarray(opart.partition(gates, n, a.method, k, seed=0), dtype=np.uint32)
+    P = int(pog.max()) + 1
+    parts = [[g for g, s in zip(gates, pog == p) if s] for p in range(P)]
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[0] = 1.0
+    step = 0
+
+    def one():
+        nonlocal psi, step
+        sub = parts[step % P]
+        psi = sim.run_alg1(n, sub, [0] * len(sub), 1, psi)
+        step += 1
+
+    for _ in range(a.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        one()
+    dt = (time.perf_counter() - t0) / a.steps
+    bytes_per_pass = 2 * 16 * (1 << n)
+    value = bytes_per_pass / dt / 1e9
+    cpu = {"value": round(value, 3), "unit": UNIT, "cores": sim.num_threads(), "kind": "oracle",
+           "sample": f"one part pass per step ({a.steps} steps) of the {a.method} k={k} plan, "
+                     "Algorithm 1 mode, complex128"}
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64 arithmetic)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": n, "method": a.method, "k": k, "passes": P,
+                       "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

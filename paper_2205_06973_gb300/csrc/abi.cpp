@@ -61,6 +61,7 @@ struct sv_plan {
     std::vector<GateRef> gates;
     std::vector<uint32_t> pog;
     uint32_t n_parts = 0;
+    int max_part = 0;                                                      // qubits of the largest part
     std::map<std::pair<bool, int>, std::unique_ptr<Program>> host_progs;   // (fp64, t)
     std::map<std::tuple<int, bool, int>, DevProgram> dev_progs;            // (dev, fp64, t)
     std::vector<std::vector<double>> mats;                                 // gatewise matrices
@@ -69,7 +70,13 @@ struct sv_plan {
 static size_t amp_bytes(sv_precision p) { return p == SV_C128 ? 16 : 8; }
 static bool is_fp64(const sv_state *s) { return s->prec == SV_C128; }
 
-static int default_tile(bool fp64) { return part_tmax(fp64); }
+// Default tile: 2^12 complex64 / 2^11 complex128 amplitudes per CTA (two
+// 64 KiB shared buffers, three CTAs per SM), grown to the plan's largest part.
+static int default_tile(bool fp64, int max_part) {
+    int t = fp64 ? 11 : 12;
+    if (max_part > t) t = max_part;
+    return t > part_tmax(fp64) ? part_tmax(fp64) : t;
+}
 
 extern "C" {
 
@@ -211,6 +218,9 @@ sv_status sv_plan_build(const sv_gate *gates, size_t n_gates, int n, sv_method m
         else if (m == SV_PART_DFS) p->pog = part_dfs(dag, k, seed, dfs_trials);
         else p->pog = part_dagp(dag, k);
         for (uint32_t x : p->pog) p->n_parts = std::max(p->n_parts, x + 1);
+        std::vector<uint64_t> pm(p->n_parts, 0);
+        for (size_t i = 0; i < n_gates; i++) pm[p->pog[i]] |= dag.qmask[i];
+        for (uint64_t m : pm) p->max_part = std::max(p->max_part, __builtin_popcountll(m));
     } else {
         p->pog.resize(n_gates);
         for (size_t i = 0; i < n_gates; i++) p->pog[i] = (uint32_t)i;
@@ -245,7 +255,7 @@ static sv_status get_host_program(sv_plan *p, bool fp64, int t, const Program **
 sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int t, uint32_t *passes, uint32_t *phases, uint32_t *ops) {
     if (!p) return fail(SV_ERR_ARG, "plan is NULL");
     const bool fp64 = prec == SV_C128;
-    if (t == 0) t = default_tile(fp64);
+    if (t == 0) t = default_tile(fp64, p->max_part);
     if (t < part_tmin() || t > part_tmax(fp64)) return fail(SV_ERR_ARG, "tile_qubits out of range");
     if (p->method == SV_PART_NONE || p->n < part_tmin()) {
         if (passes) *passes = (uint32_t)p->gates.size();
@@ -354,7 +364,7 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
         st = apply_gatewise(s, p);
     } else {
         const bool fp64 = is_fp64(s);
-        const int t = s->tile ? s->tile : default_tile(fp64);
+        const int t = s->tile ? s->tile : default_tile(fp64, p->max_part);
         const Program *hp = nullptr;
         const DevProgram *dp = nullptr;
         st = get_dev_program(s, p, t, &hp, &dp);

@@ -1,10 +1,12 @@
 // sm_103a kernels of the hierarchical state-vector simulator.
 //
 //  k_part  : one HBM pass of one part (Algorithm 1, Gather-Execute-Scatter).
-//            Each CTA gathers the 2^t amplitudes of one outer assignment
-//            straight into registers (2^R per thread), runs the part's
-//            register phases, transposing the tile through XOR-swizzled
-//            shared memory between phases, and scatters it back.
+//            Persistent CTAs gather the 2^t amplitudes of one outer
+//            assignment with cp.async into shared memory (the next tile's
+//            copy overlaps the current tile's compute), run the part's
+//            register phases (2^R amplitudes per thread), transposing the
+//            tile through XOR-swizzled shared memory between phases, and
+//            scatter it back from registers.
 //  k_gate1 / k_gate2 : the plain per-gate pass of Sec. III-A (comparator).
 //  k_probs / k_sum   : |a_x|^2 and the norm with FP64 accumulation.
 #include <cuda_runtime.h>
@@ -23,15 +25,17 @@ template <> struct CT<double> { typedef double2 T; };
 // ------------------------------------------------------------------------
 // register-bit operations; B, A are compile-time register bits
 // ------------------------------------------------------------------------
-template <int NR, int B, typename C, typename Real>
-__device__ __forceinline__ void op_h(C (&a)[NR], Real r) {
+// Hadamard without its 1/sqrt2: the planner folds the factor into the part's
+// store factor, so each H costs one add and one subtract per amplitude pair.
+template <int NR, int B, typename C>
+__device__ __forceinline__ void op_h(C (&a)[NR]) {
 #pragma unroll
     for (int i = 0; i < NR; i++) {
         if (i & (1 << B)) continue;
         const int j = i | (1 << B);
         const C x = a[i], y = a[j];
-        a[i].x = (x.x + y.x) * r; a[i].y = (x.y + y.y) * r;
-        a[j].x = (x.x - y.x) * r; a[j].y = (x.y - y.y) * r;
+        a[i].x = x.x + y.x; a[i].y = x.y + y.y;
+        a[j].x = x.x - y.x; a[j].y = x.y - y.y;
     }
 }
 
@@ -177,62 +181,123 @@ __device__ __forceinline__ uint32_t swz(int p) {
 // ------------------------------------------------------------------------
 // part kernel
 // ------------------------------------------------------------------------
+// Asynchronous global -> shared copies (sm_80+ cp.async); 8-byte elements use
+// the L1-allocating form, 16-byte elements the L2-only form.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Deposit the bits of v, lowest first, into the set bits of mask.
+__device__ __forceinline__ uint64_t deposit64(uint64_t v, uint64_t mask) {
+    uint64_t out = 0;
+    while (mask) {
+        const uint64_t low = mask & (~mask + 1);
+        if (v & 1) out |= low;
+        v >>= 1;
+        mask ^= low;
+    }
+    return out;
+}
+
+// Minimum resident CTAs for the launch bound: two tile buffers of 2^T
+// amplitudes in shared memory and about 168 registers per thread.
 template <typename Real, int T, int R>
-__global__ void __launch_bounds__(1 << (T - R), (512 >> (T - R)) > 0 ? (512 >> (T - R)) : 1)
+struct PartCfg {
+    static constexpr int NT = 1 << (T - R);
+    static constexpr int SMEM = 2 * (1 << T) * 2 * (int)sizeof(Real);
+    static constexpr int BY_REG = 65536 / (168 * NT);
+    static constexpr int BY_SMEM = (227 * 1024) / SMEM;
+    static constexpr int MINB0 = BY_REG < BY_SMEM ? BY_REG : BY_SMEM;
+    static constexpr int MINB = MINB0 < 1 ? 1 : MINB0;
+};
+
+// One part pass. Persistent CTAs walk the tiles (outer assignments) with a
+// two-stage pipeline: while tile i is computed from registers, the
+// cp.async copy of tile i+1 streams into the other shared buffer.
+template <typename Real, int T, int R>
+__global__ void __launch_bounds__(PartCfg<Real, T, R>::NT, PartCfg<Real, T, R>::MINB)
 k_part(typename CT<Real>::T *__restrict__ sv, const __grid_constant__ PartLaunch L,
        const Phase *__restrict__ phases, const Op *__restrict__ ops, const Real *__restrict__ coefs,
        uint64_t n_tiles) {
     typedef typename CT<Real>::T C;
     constexpr int NR = 1 << R;
     constexpr int TB = T - R;
+    constexpr int TILE = 1 << T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *sm = reinterpret_cast<C *>(smem_raw);
+    C *const buf0 = reinterpret_cast<C *>(smem_raw);
+    C *const buf1 = buf0 + TILE;
     const int tid = threadIdx.x;
-    const Real rsq = Real(0.70710678118654752440);
+
+    // copy layout: tile index = tid | (c << TB); thread bits on the lowest slots
+    uint64_t c_thr = 0;
+    uint32_t s_cthr = 0;
+#pragma unroll
+    for (int j = 0; j < TB; j++)
+        if ((tid >> j) & 1) {
+            c_thr |= 1ull << L.tile_q[j];
+            s_cthr ^= swz<Real>(j);
+        }
+    uint64_t c_rs[R];
+    uint32_t s_crs[R];
+#pragma unroll
+    for (int b = 0; b < R; b++) {
+        c_rs[b] = 1ull << L.tile_q[TB + b];
+        s_crs[b] = swz<Real>(TB + b);
+    }
+    auto issue = [&](uint64_t base, C *dst) {
+        const C *src = sv + (base | c_thr);
+#pragma unroll
+        for (int i = 0; i < NR; i++) {
+            uint64_t go = 0;
+            uint32_t so = s_cthr;
+#pragma unroll
+            for (int b = 0; b < R; b++)
+                if (i & (1 << b)) {
+                    go |= c_rs[b];
+                    so ^= s_crs[b];
+                }
+            cp_async<(int)sizeof(C)>(dst + so, src + go);
+        }
+    };
 
     C a[NR];
-    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        // Gather: outer bits of the tile index deposited into the outer qubits
-        uint64_t base = 0;
-        {
-            uint64_t m = L.outer_mask, v = tile;
-            while (m) {
-                const uint64_t low = m & (~m + 1);
-                if (v & 1) base |= low;
-                v >>= 1;
-                m ^= low;
-            }
-        }
-        {
-            uint64_t toff = base;
-#pragma unroll
-            for (int j = 0; j < TB; j++)
-                if ((tid >> j) & 1) toff |= 1ull << L.load_thr_q[j];
-            uint64_t rs[R];
-#pragma unroll
-            for (int b = 0; b < R; b++) rs[b] = 1ull << L.load_reg_q[b];
-#pragma unroll
-            for (int i = 0; i < NR; i++) {
-                uint64_t off = toff;
-#pragma unroll
-                for (int b = 0; b < R; b++)
-                    if (i & (1 << b)) off |= rs[b];
-                a[i] = __ldcs(sv + off);
-            }
-        }
+    uint64_t tile = blockIdx.x;
+    uint64_t base = tile < n_tiles ? deposit64(tile, L.outer_mask) : 0;
+    if (tile < n_tiles) issue(base, buf0);
+    cp_async_commit();
+    for (uint32_t it = 0; tile < n_tiles; tile += gridDim.x, it++) {
+        C *const cur = (it & 1) ? buf1 : buf0;
+        C *const nxt = (it & 1) ? buf0 : buf1;
+        __syncthreads();   // every thread is done with nxt (it was cur two stages ago)
+        const uint64_t ntile = tile + gridDim.x;
+        const uint64_t nbase = ntile < n_tiles ? deposit64(ntile, L.outer_mask) : 0;
+        if (ntile < n_tiles) issue(nbase, nxt);
+        cp_async_commit();
+        cp_async_wait<1>();  // this tile's copies have landed
+        __syncthreads();
+
         Real tpr = Real(1), tpi = Real(0);   // per-thread phase of diagonal gates on thread bits
         uint32_t s_thr = 0, s_reg[R];
         for (uint32_t p = 0; p < L.n_phases; p++) {
             const Phase ph = phases[L.phase_begin + p];
             if (p > 0) {
-                // transpose: write with the previous layout, read with this one
+                // transpose through shared memory: write with the previous layout
+                __syncthreads();
 #pragma unroll
                 for (int i = 0; i < NR; i++) {
                     uint32_t o = s_thr;
 #pragma unroll
                     for (int b = 0; b < R; b++)
                         if (i & (1 << b)) o ^= s_reg[b];
-                    sm[o] = a[i];
+                    cur[o] = a[i];
                 }
                 __syncthreads();
             }
@@ -242,16 +307,13 @@ k_part(typename CT<Real>::T *__restrict__ sv, const __grid_constant__ PartLaunch
                 if ((tid >> j) & 1) s_thr ^= swz<Real>(ph.thr[j]);
 #pragma unroll
             for (int b = 0; b < R; b++) s_reg[b] = swz<Real>(ph.reg[b]);
-            if (p > 0) {
 #pragma unroll
-                for (int i = 0; i < NR; i++) {
-                    uint32_t o = s_thr;
+            for (int i = 0; i < NR; i++) {
+                uint32_t o = s_thr;
 #pragma unroll
-                    for (int b = 0; b < R; b++)
-                        if (i & (1 << b)) o ^= s_reg[b];
-                    a[i] = sm[o];
-                }
-                __syncthreads();
+                for (int b = 0; b < R; b++)
+                    if (i & (1 << b)) o ^= s_reg[b];
+                a[i] = cur[o];
             }
             // Execute: the phase's gates
             for (uint32_t o = 0; o < ph.op_count; o++) {
@@ -259,7 +321,7 @@ k_part(typename CT<Real>::T *__restrict__ sv, const __grid_constant__ PartLaunch
                 const Real *cf = coefs + op.coef;
                 switch (op.kind) {
                 case OP_H:
-                    with_bit<R>(op.a, [&](auto bc) { op_h<NR, decltype(bc)::value>(a, rsq); });
+                    with_bit<R>(op.a, [&](auto bc) { op_h<NR, decltype(bc)::value>(a); });
                     break;
                 case OP_U2:
                     with_bit<R>(op.a, [&](auto bc) { op_u2<NR, decltype(bc)::value>(a, cf); });
@@ -354,7 +416,14 @@ k_part(typename CT<Real>::T *__restrict__ sv, const __grid_constant__ PartLaunch
                 }
             }
         }
-        // Scatter: the last phase's layout, with SWAP relabels applied
+        // Scatter: the last phase's layout, with SWAP relabels applied; the
+        // part factor and the last phase's per-thread phase are applied here
+        if (L.flags & PL_STORE_FACTOR) {
+            const Real gr = (Real)L.gr, gi = (Real)L.gi;
+            const Real fr = gr * tpr - gi * tpi, fi = gr * tpi + gi * tpr;
+#pragma unroll
+            for (int i = 0; i < NR; i++) cmul_in(a[i], fr, fi);
+        }
         {
             uint64_t toff = base;
 #pragma unroll
@@ -372,8 +441,9 @@ k_part(typename CT<Real>::T *__restrict__ sv, const __grid_constant__ PartLaunch
                 __stcs(sv + off, a[i]);
             }
         }
-        if (L.n_phases > 1) __syncthreads();   // smem reuse by the next tile
+        base = nbase;
     }
+    cp_async_wait<0>();
 }
 
 template <typename Real, int T>
@@ -381,21 +451,34 @@ static cudaError_t launch_part_t(void *sv, const PartLaunch &L, const Phase *pha
                                  const void *coefs, uint64_t n_tiles, cudaStream_t st) {
     constexpr int R = sizeof(Real) == 4 ? 5 : 4;
     typedef typename CT<Real>::T C;
+    typedef PartCfg<Real, T, R> Cfg;
     auto kern = k_part<Real, T, R>;
-    const size_t smem = L.n_phases > 1 ? sizeof(C) << T : 0;
-    static uint64_t attr_set = 0;   // devices on which the smem limit was raised (per instantiation)
+    const size_t smem = 2 * (sizeof(C) << T);
+    // per instantiation: devices on which the shared-memory limit was raised,
+    // and the resident CTAs per SM found there
+    static uint64_t attr_set = 0;
+    static int resident[64];
+    static int sms[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 64 && !((attr_set >> dev) & 1)) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(C) << T));
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    if (!((attr_set >> dev) & 1)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, Cfg::NT, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        resident[dev] = nb < 1 ? 1 : nb;
         attr_set |= 1ull << dev;
     }
-    uint64_t grid = n_tiles;
-    if (grid > (1ull << 31) - 1) grid = (1ull << 31) - 1;
-    kern<<<(unsigned)grid, 1 << (T - R), smem, st>>>(reinterpret_cast<C *>(sv), L, phases, ops,
-                                                      reinterpret_cast<const Real *>(coefs), n_tiles);
+    uint64_t grid = (uint64_t)sms[dev] * resident[dev];
+    if (grid > n_tiles) grid = n_tiles;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, Cfg::NT, smem, st>>>(reinterpret_cast<C *>(sv), L, phases, ops,
+                                                reinterpret_cast<const Real *>(coefs), n_tiles);
     return cudaGetLastError();
 }
 
@@ -417,6 +500,7 @@ cudaError_t launch_part(bool fp64, int t, void *sv, const PartLaunch &L, const P
     }
     return cudaErrorInvalidValue;
 }
+
 
 // ------------------------------------------------------------------------
 // plain per-gate kernels

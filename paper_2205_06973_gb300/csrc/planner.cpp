@@ -154,6 +154,15 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
         L.n = n;
         L.t = t;
         L.phase_begin = (uint32_t)prog.phases.size();
+        for (int p = 0; p < t; p++) L.tile_q[p] = (uint8_t)q_at[p];
+        // part factor: 1/sqrt2 per (unnormalised) H and e^{-i theta/2} per RZ
+        double fr = 1.0, fi = 0.0;
+        auto fmul = [&](double dr, double di) {
+            const double x = fr, y = fi;
+            fr = x * dr - y * di;
+            fi = x * di + y * dr;
+        };
+        bool last_tphase = false;
         std::vector<int> remaining = gl;
         bool first = true;
         while (!remaining.empty()) {
@@ -183,12 +192,9 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
             for (int p = t - 1; p >= 0 && popc(Rset) < R; p--) Rset |= 1u << p;
             const bool last = rest.empty();
             // slot -> qubit at the start and at the end of this phase
-            int q_start[64], q_end[64];
+            int q_end[64];
             for (int q = 0; q < n; q++)
-                if ((Tm >> q) & 1) {
-                    q_start[slot_of[q]] = q;
-                    q_end[sim_slot[q]] = q;
-                }
+                if ((Tm >> q) & 1) q_end[sim_slot[q]] = q;
             Phase ph;
             std::memset(&ph, 0, sizeof(ph));
             int rb[64], tbit[64];
@@ -201,16 +207,12 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
             std::vector<int> key(t, 0);
             for (int p = 0; p < t; p++) {
                 if (!((Rset >> p) & 1)) cand.push_back(p);
-                key[p] = first ? q_start[p] : (last ? q_end[p] : p);
+                key[p] = last ? q_end[p] : p;   // the last phase stores: lanes on the lowest qubits
             }
             std::vector<int> thr = order_thread_slots(cand, key, fp64);
             for (size_t j = 0; j < thr.size(); j++) {
                 ph.thr[j] = (uint8_t)thr[j];
                 tbit[thr[j]] = (int)j;
-            }
-            if (first) {
-                for (int b = 0; b < R; b++) L.load_reg_q[b] = (uint8_t)q_start[ph.reg[b]];
-                for (int j = 0; j < t - R; j++) L.load_thr_q[j] = (uint8_t)q_start[ph.thr[j]];
             }
             // pass 2: emit ops
             ph.op_begin = (uint32_t)prog.ops.size();
@@ -235,7 +237,10 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
                 const int s0 = slot_of[gr.q[0]];
                 const bool r0 = (Rset >> s0) & 1;
                 switch (gr.kind) {
-                case SV_GATE_H: emit(OP_H, rb[s0], 0, 0, 0); break;
+                case SV_GATE_H:
+                    emit(OP_H, rb[s0], 0, 0, 0);
+                    fmul(std::sqrt(0.5), 0.0);
+                    break;
                 case SV_GATE_X: emit(OP_X, rb[s0], 0, 0, 0); break;
                 case SV_GATE_Y: emit(OP_Y, rb[s0], 0, 0, 0); break;
                 case SV_GATE_RX: emit(OP_RX, rb[s0], 0, 0, coef({std::cos(th / 2), std::sin(th / 2)})); break;
@@ -253,10 +258,11 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
                     }
                 } break;
                 case SV_GATE_RZ: {
-                    const double c = std::cos(th / 2), s = std::sin(th / 2);
-                    if (r0) emit(OP_D, rb[s0], 0, 0, coef({c, -s, c, s}));
+                    // RZ(t) = e^{-it/2} diag(1, e^{it}): the global phase joins the part factor
+                    fmul(std::cos(th / 2), -std::sin(th / 2));
+                    if (r0) emit(OP_P, rb[s0], 0, 0, coef({std::cos(th), std::sin(th)}));
                     else {
-                        emit(OP_TD, 0, 0, tbit[s0], coef({c, -s, c, s}));
+                        emit(OP_TD, 0, 0, tbit[s0], coef({1.0, 0.0, std::cos(th), std::sin(th)}));
                         tphase = true;
                     }
                 } break;
@@ -290,7 +296,9 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
                     return false;
                 }
             }
-            if (tphase) emit(OP_TAPPLY, 0, 0, 0, 0);
+            // the last phase's per-thread phase is applied with the part factor at the store
+            if (tphase && !last) emit(OP_TAPPLY, 0, 0, 0, 0);
+            if (last) last_tphase = tphase;
             ph.op_count = (uint32_t)prog.ops.size() - ph.op_begin;
             prog.phases.push_back(ph);
             if (last) {
@@ -301,6 +309,9 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
             first = false;
         }
         L.n_phases = (uint32_t)prog.phases.size() - L.phase_begin;
+        L.gr = fr;
+        L.gi = fi;
+        L.flags = (last_tphase || fr != 1.0 || fi != 0.0) ? PL_STORE_FACTOR : 0u;
         prog.parts.push_back(L);
         prog.n_tiles.push_back(1ull << (n - t));
     }

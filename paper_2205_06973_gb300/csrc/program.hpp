@@ -19,14 +19,14 @@
 namespace hisv {
 
 enum OpKind : uint8_t {
-    OP_H = 0,    // a: reg bit
+    OP_H = 0,    // a: reg bit; unnormalised (a+b, a-b), the 1/sqrt2 goes into the part factor
     OP_U2,       // a; coef: m00 m01 m10 m11 (re, im each) -> 8 reals
     OP_RX,       // a; coef: c, s
     OP_RY,       // a; coef: c, s
     OP_X,        // a
     OP_Y,        // a
     OP_D,        // a; coef: d0 (re, im), d1 (re, im)  (diagonal)
-    OP_P,        // a; coef: d1 (re, im)               (diag(1, d1))
+    OP_P,        // a; coef: d1 (re, im)               (diag(1, d1); RZ = e^{-it/2} P(t))
     OP_Z,        // a                                  (diag(1, -1))
     OP_CX,       // a = control reg bit, b = target reg bit
     OP_CP,       // a, b reg bits; coef: d (re, im) on |11>
@@ -66,10 +66,14 @@ struct PartLaunch {
     uint32_t n_phases;
     int32_t n;
     int32_t t;
-    uint8_t load_reg_q[8];   // global qubit of register bit b in the first phase
-    uint8_t load_thr_q[MAX_TB];
+    uint32_t flags;          // PL_STORE_FACTOR: multiply by (gr, gi) x per-thread phase at the store
+    uint32_t pad;
+    double gr, gi;           // part factor: 2^{-h/2} for h unnormalised H gates times RZ global phases
+    uint8_t tile_q[32];      // global qubit of tile slot p (p < t); the gather/copy layout
     uint8_t store_reg_q[8];  // global qubit of register bit b in the last phase (after SWAP relabels)
     uint8_t store_thr_q[MAX_TB];
 };
+
+constexpr uint32_t PL_STORE_FACTOR = 1u;
 
 }  // namespace hisv

@@ -149,7 +149,9 @@ def test_probs_and_norm(precision):
         norm = st.probs(out, fp64=fp64)
         p = out.cpu().numpy()
         assert abs(norm - 1.0) < (1e-5 if precision == "c64" else 1e-12)
-        assert np.abs(p - np.abs(ref) ** 2).max() < (1e-6 if precision == "c64" else 1e-13)
+        # float32 output rounds each probability to 24 bits
+        tol = 1e-13 if (precision == "c128" and fp64) else 1e-6
+        assert np.abs(p - np.abs(ref) ** 2).max() < tol
     assert abs(st.probs() - 1.0) < 1e-5
     st.close()
     plan.close()
