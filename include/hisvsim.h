@@ -74,6 +74,8 @@ typedef struct sv_plan sv_plan;
 /* Flags of sv_apply_parts. */
 #define SV_FLAG_GATEWISE 0x1u   /* ignore the parts: one plain pass per gate (comparator) */
 #define SV_FLAG_SYNC     0x2u   /* synchronise the stream before returning */
+#define SV_FLAG_TC_DENSE 0x4u   /* complex64: parts of at most 6 qubits run as one fused 64x64
+                                   unitary on the tensor cores (split BF16, FP32 accumulation) */
 
 /* ---------------------------------------------------------------- state ---
  * sv_create: make an n-qubit state (1 <= n <= 36) initialised to |0...0>.
@@ -98,7 +100,8 @@ sv_status sv_upload(sv_state *s, const void *host_src, size_t bytes);
 sv_status sv_copy_state(sv_state *s, void *host_dst, size_t bytes);
 /* Device address of the amplitudes and the number of bytes they occupy. */
 sv_status sv_device_ptr(sv_state *s, void **ptr, size_t *bytes);
-/* Synchronise the state's stream and report any pending device error. */
+/* Synchronise the state's stream and report any pending device error; a
+ * bounded device wait that gave up (tensor-core path) returns SV_ERR_TIMEOUT. */
 sv_status sv_sync(sv_state *s);
 /* CTA tile size used by the part kernels for this state: tile_qubits t in
  * [10, 13] for SV_C64 and [10, 12] for SV_C128 (2^t amplitudes per CTA); 0
@@ -123,11 +126,13 @@ sv_status sv_plan_build(const sv_gate *gates, size_t n_gates, int n_qubits, sv_m
 /* Copy the partition out: part_of_gate[n_gates] (may be NULL) and the number
  * of parts. n_gates must equal the plan's gate count. */
 sv_status sv_plan_export(const sv_plan *p, uint32_t *part_of_gate, size_t n_gates, uint32_t *n_parts);
-/* Per-part statistics of the compiled device program for a precision/tile:
- * passes (parts run on the GPU), register phases and smem transposes in total.
- * Compiles the program on the host if needed; no device work. */
-sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int tile_qubits, uint32_t *passes,
-                        uint32_t *phases, uint32_t *ops);
+/* Statistics of the compiled device program for a precision, tile and apply
+ * flags (SV_FLAG_TC_DENSE changes the program): passes = parts run on the
+ * GPU, phases = register phases of the gate-list parts, ops = their kernel
+ * ops, dense = parts run as fused unitaries on the tensor cores (any output
+ * pointer may be NULL). Compiles on the host if needed; no device work. */
+sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int tile_qubits, uint32_t flags, uint32_t *passes,
+                        uint32_t *phases, uint32_t *ops, uint32_t *dense);
 sv_status sv_plan_destroy(sv_plan *p);
 
 /* ---------------------------------------------------------------- apply ---

@@ -18,6 +18,7 @@ SV_PART_NONE, SV_PART_NAT, SV_PART_DFS, SV_PART_DAGP = 0, 1, 2, 3
 METHODS = {"none": SV_PART_NONE, "nat": SV_PART_NAT, "dfs": SV_PART_DFS, "dagp": SV_PART_DAGP}
 SV_FLAG_GATEWISE = 0x1
 SV_FLAG_SYNC = 0x2
+SV_FLAG_TC_DENSE = 0x4
 
 GATE_KINDS = ("H", "X", "Y", "Z", "S", "T", "RX", "RY", "RZ", "P", "CX", "CZ", "CP", "SWAP")
 KIND = {name: i for i, name in enumerate(GATE_KINDS)}
@@ -58,7 +59,7 @@ _SIGS = {
     "sv_plan_build": ([_vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                        ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
     "sv_plan_export": ([_vp, _vp, ctypes.c_size_t, _u32p], ctypes.c_int),
-    "sv_plan_stats": ([_vp, ctypes.c_int, ctypes.c_int, _u32p, _u32p, _u32p], ctypes.c_int),
+    "sv_plan_stats": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p], ctypes.c_int),
     "sv_plan_destroy": ([_vp], ctypes.c_int),
     "sv_apply_parts": ([_vp, _vp, ctypes.c_uint32], ctypes.c_int),
     "sv_measure_probs": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),

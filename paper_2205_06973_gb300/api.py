@@ -33,11 +33,12 @@ class Plan:
         N.check(N.lib.sv_plan_export(self.h, pog.ctypes.data, self.G, ctypes.byref(P)))
         return pog[: self.G], P.value
 
-    def stats(self, precision="c64", tile=0):
-        a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    def stats(self, precision="c64", tile=0, tc=False):
+        a, b, c, d = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
         N.check(N.lib.sv_plan_stats(self.h, N.SV_C128 if precision == "c128" else N.SV_C64, tile,
-                                    ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-        return {"passes": a.value, "phases": b.value, "ops": c.value}
+                                    N.SV_FLAG_TC_DENSE if tc else 0,
+                                    ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+        return {"passes": a.value, "phases": b.value, "ops": c.value, "dense": d.value}
 
     def close(self):
         if self.h:
@@ -89,8 +90,9 @@ class State:
         N.check(N.lib.sv_copy_state(self.h, ctypes.c_void_p(out.data_ptr()), self.nbytes))
         return out
 
-    def apply(self, plan: Plan, gatewise=False, sync=False):
-        flags = (N.SV_FLAG_GATEWISE if gatewise else 0) | (N.SV_FLAG_SYNC if sync else 0)
+    def apply(self, plan: Plan, gatewise=False, sync=False, tc=False):
+        flags = ((N.SV_FLAG_GATEWISE if gatewise else 0) | (N.SV_FLAG_SYNC if sync else 0)
+                 | (N.SV_FLAG_TC_DENSE if tc else 0))
         N.check(N.lib.sv_apply_parts(self.h, plan.h, flags))
 
     def probs(self, out=None, fp64=False):

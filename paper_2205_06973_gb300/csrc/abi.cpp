@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/hisvsim.h"
+#include "dense.hpp"
 #include "kernels.hpp"
 #include "partition.hpp"
 #include "planner.hpp"
@@ -39,6 +40,7 @@ struct DevProgram {
     Phase *d_phases = nullptr;
     Op *d_ops = nullptr;
     void *d_coefs = nullptr;
+    uint8_t *d_aimg = nullptr;      // A images of the dense parts
 };
 
 struct sv_state {
@@ -52,6 +54,7 @@ struct sv_state {
     int dev = 0;
     double *d_partials = nullptr;   // kProbBlocks + 1 doubles; the last holds the norm
     double *h_norm = nullptr;       // pinned
+    int *d_err = nullptr;           // device error word of bounded waits (0 = none)
 };
 
 struct sv_plan {
@@ -62,8 +65,8 @@ struct sv_plan {
     std::vector<uint32_t> pog;
     uint32_t n_parts = 0;
     int max_part = 0;                                                      // qubits of the largest part
-    std::map<std::pair<bool, int>, std::unique_ptr<Program>> host_progs;   // (fp64, t)
-    std::map<std::tuple<int, bool, int>, DevProgram> dev_progs;            // (dev, fp64, t)
+    std::map<std::tuple<bool, int, int>, std::unique_ptr<Program>> host_progs;   // (fp64, t, dense)
+    std::map<std::tuple<int, bool, int, int>, DevProgram> dev_progs;             // (dev, fp64, t, dense)
     std::vector<std::vector<double>> mats;                                 // gatewise matrices
 };
 
@@ -109,10 +112,14 @@ sv_status sv_create(int n, sv_precision prec, void *dev_buf, size_t dev_buf_byte
     }
     cudaError_t e = cudaMalloc(&s->d_partials, sizeof(double) * (kProbBlocks + 1));
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_norm, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (s->owns) cudaFree(s->buf);
         if (s->d_partials) cudaFree(s->d_partials);
+        if (s->h_norm) cudaFreeHost(s->h_norm);
+        if (s->d_err) cudaFree(s->d_err);
         return fail(SV_ERR_OOM, std::string("scratch allocation: ") + cudaGetErrorString(e));
     }
     e = launch_set_basis(is_fp64(s.get()), s->buf, n, 0, s->stream);
@@ -132,6 +139,7 @@ sv_status sv_destroy(sv_state *s) {
     if (s->owns) cudaFree(s->buf);
     cudaFree(s->d_partials);
     cudaFreeHost(s->h_norm);
+    cudaFree(s->d_err);
     delete s;
     if (e != cudaSuccess) return fail(SV_ERR_CUDA, std::string("pending work failed: ") + cudaGetErrorString(e));
     return SV_OK;
@@ -166,10 +174,21 @@ sv_status sv_device_ptr(sv_state *s, void **ptr, size_t *bytes) {
     return SV_OK;
 }
 
+static sv_status check_device_error(sv_state *s) {
+    int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (h) {
+        CUDA_TRY(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+        return fail(SV_ERR_TIMEOUT, "a bounded device wait of the tensor-core kernel gave up");
+    }
+    return SV_OK;
+}
+
 sv_status sv_sync(sv_state *s) {
     if (!s) return fail(SV_ERR_ARG, "state is NULL");
     CUDA_TRY(cudaStreamSynchronize(s->stream));
-    return SV_OK;
+    return check_device_error(s);
 }
 
 sv_status sv_set_tile(sv_state *s, int t) {
@@ -238,13 +257,13 @@ sv_status sv_plan_export(const sv_plan *p, uint32_t *pog, size_t n_gates, uint32
     return SV_OK;
 }
 
-static sv_status get_host_program(sv_plan *p, bool fp64, int t, const Program **out) {
-    auto key = std::make_pair(fp64, t);
+static sv_status get_host_program(sv_plan *p, bool fp64, int t, int dense, const Program **out) {
+    auto key = std::make_tuple(fp64, t, dense);
     auto it = p->host_progs.find(key);
     if (it == p->host_progs.end()) {
         std::unique_ptr<Program> prog(new Program());
         std::string err;
-        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, fp64, t, part_R(fp64), *prog, err))
+        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, fp64, t, part_R(fp64), dense, *prog, err))
             return fail(SV_ERR_PARTITION, err);
         it = p->host_progs.emplace(key, std::move(prog)).first;
     }
@@ -252,23 +271,28 @@ static sv_status get_host_program(sv_plan *p, bool fp64, int t, const Program **
     return SV_OK;
 }
 
-sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int t, uint32_t *passes, uint32_t *phases, uint32_t *ops) {
+static int dense_mode(uint32_t flags, bool fp64) { return ((flags & SV_FLAG_TC_DENSE) && !fp64) ? 1 : 0; }
+
+sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int t, uint32_t flags, uint32_t *passes, uint32_t *phases,
+                        uint32_t *ops, uint32_t *dense) {
     if (!p) return fail(SV_ERR_ARG, "plan is NULL");
     const bool fp64 = prec == SV_C128;
     if (t == 0) t = default_tile(fp64, p->max_part);
     if (t < part_tmin() || t > part_tmax(fp64)) return fail(SV_ERR_ARG, "tile_qubits out of range");
-    if (p->method == SV_PART_NONE || p->n < part_tmin()) {
+    if (p->method == SV_PART_NONE || p->n < part_tmin() || (flags & SV_FLAG_GATEWISE)) {
         if (passes) *passes = (uint32_t)p->gates.size();
         if (phases) *phases = 0;
         if (ops) *ops = 0;
+        if (dense) *dense = 0;
         return SV_OK;
     }
     const Program *prog = nullptr;
-    sv_status st = get_host_program(p, fp64, t, &prog);
+    sv_status st = get_host_program(p, fp64, t, dense_mode(flags, fp64), &prog);
     if (st != SV_OK) return st;
-    if (passes) *passes = (uint32_t)prog->parts.size();
+    if (passes) *passes = (uint32_t)prog->kind.size();
     if (phases) *phases = (uint32_t)prog->phases.size();
     if (ops) *ops = (uint32_t)prog->ops.size();
+    if (dense) *dense = (uint32_t)prog->dense.size();
     return SV_OK;
 }
 
@@ -281,33 +305,41 @@ sv_status sv_plan_destroy(sv_plan *p) {
         cudaFree(kv.second.d_phases);
         cudaFree(kv.second.d_ops);
         cudaFree(kv.second.d_coefs);
+        cudaFree(kv.second.d_aimg);
     }
     cudaSetDevice(cur);
     delete p;
     return SV_OK;
 }
 
-static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, const Program **hp, const DevProgram **dp) {
+static void free_dev(DevProgram &d) {
+    cudaFree(d.d_phases);
+    cudaFree(d.d_ops);
+    cudaFree(d.d_coefs);
+    cudaFree(d.d_aimg);
+}
+
+static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, int dense, const Program **hp,
+                                 const DevProgram **dp) {
     const bool fp64 = is_fp64(s);
-    sv_status st = get_host_program(p, fp64, t, hp);
+    sv_status st = get_host_program(p, fp64, t, dense, hp);
     if (st != SV_OK) return st;
-    auto key = std::make_tuple(s->dev, fp64, t);
+    auto key = std::make_tuple(s->dev, fp64, t, dense);
     auto it = p->dev_progs.find(key);
     if (it == p->dev_progs.end()) {
         const Program &prog = **hp;
         DevProgram d;
         d.dev = s->dev;
         const size_t nph = std::max<size_t>(1, prog.phases.size()), nop = std::max<size_t>(1, prog.ops.size());
-        const size_t ncf = std::max<size_t>(1, prog.coefs.size());
+        const size_t ncf = std::max<size_t>(1, prog.coefs.size()), nim = std::max<size_t>(16, prog.a_img.size());
         const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
         cudaError_t e = cudaMalloc(&d.d_phases, sizeof(Phase) * nph);
         if (e == cudaSuccess) e = cudaMalloc(&d.d_ops, sizeof(Op) * nop);
         if (e == cudaSuccess) e = cudaMalloc(&d.d_coefs, rsz * ncf);
+        if (e == cudaSuccess) e = cudaMalloc(&d.d_aimg, nim);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(d.d_phases);
-            cudaFree(d.d_ops);
-            cudaFree(d.d_coefs);
+            free_dev(d);
             return fail(SV_ERR_OOM, std::string("program upload: ") + cudaGetErrorString(e));
         }
         std::vector<float> cf32;
@@ -319,10 +351,9 @@ static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, const Program *
         if (!prog.phases.empty()) e = cudaMemcpy(d.d_phases, prog.phases.data(), sizeof(Phase) * prog.phases.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && !prog.ops.empty()) e = cudaMemcpy(d.d_ops, prog.ops.data(), sizeof(Op) * prog.ops.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && !prog.coefs.empty()) e = cudaMemcpy(d.d_coefs, cf, rsz * prog.coefs.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !prog.a_img.empty()) e = cudaMemcpy(d.d_aimg, prog.a_img.data(), prog.a_img.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
-            cudaFree(d.d_phases);
-            cudaFree(d.d_ops);
-            cudaFree(d.d_coefs);
+            free_dev(d);
             return fail(SV_ERR_CUDA, std::string("program upload: ") + cudaGetErrorString(e));
         }
         it = p->dev_progs.emplace(key, d).first;
@@ -367,16 +398,25 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
         const int t = s->tile ? s->tile : default_tile(fp64, p->max_part);
         const Program *hp = nullptr;
         const DevProgram *dp = nullptr;
-        st = get_dev_program(s, p, t, &hp, &dp);
+        st = get_dev_program(s, p, t, dense_mode(flags, fp64), &hp, &dp);
         if (st != SV_OK) return st;
-        for (size_t i = 0; i < hp->parts.size(); i++) {
-            cudaError_t e = launch_part(fp64, hp->t, s->buf, hp->parts[i], dp->d_phases, dp->d_ops, dp->d_coefs,
-                                        hp->n_tiles[i], s->stream);
+        for (size_t i = 0; i < hp->kind.size(); i++) {
+            const uint32_t j = hp->index[i];
+            cudaError_t e;
+            if (hp->kind[i] == 0)
+                e = launch_part(fp64, hp->t, s->buf, hp->parts[j], dp->d_phases, dp->d_ops, dp->d_coefs,
+                                hp->n_tiles[j], s->stream);
+            else
+                e = launch_dense6(s->buf, hp->dense[j], dp->d_aimg + (size_t)j * DENSE_A_BYTES, hp->dense_tiles[j],
+                                  s->d_err, s->stream);
             if (e != cudaSuccess) return fail(SV_ERR_CUDA, std::string("part launch: ") + cudaGetErrorString(e));
         }
     }
     if (st != SV_OK) return st;
-    if (flags & SV_FLAG_SYNC) CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (flags & SV_FLAG_SYNC) {
+        CUDA_TRY(cudaStreamSynchronize(s->stream));
+        return check_device_error(s);
+    }
     return SV_OK;
 }
 

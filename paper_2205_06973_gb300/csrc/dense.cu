@@ -1,0 +1,406 @@
+// Dense fused-part kernel on the sm_103a tensor cores (tcgen05 + TMEM).
+//
+// A part on 6 qubits is the 64x64 complex matrix U (the product of its
+// gates). With amplitudes stored as interleaved (re, im) floats, the part
+// maps every column x (64 amplitudes that share the other n - 6 bits) to
+// R x, R the 128x128 real block form R[2i+c][2j+d] of U. One CTA tile is
+// 128 columns (the lowest 7 non-part qubits) and the GEMM
+//     D[128 x 128] = R[128 x 128] . X^T     (M = 128, N = 128, K = 128)
+// runs as split BF16: R = R_hi + R_lo, X = X_hi + X_lo, and
+// D = R_hi X_hi + R_hi X_lo + R_lo X_hi with FP32 accumulation in tensor
+// memory (the dropped R_lo X_lo term is below 2^-16 relative).
+//
+// Warp-specialised persistent CTA (13 warps): 8 producer warps gather tile i
+// from HBM, split it to BF16 and write it K-major with the 128-byte swizzle
+// into shared stage i%2; one thread of the MMA warp issues the 24 MMAs of
+// tile i into TMEM accumulator i%2; 4 epilogue warps drain the accumulator
+// (tcgen05.ld, one TMEM lane quarter each) and scatter the tile back to HBM.
+// The roles hand stages and accumulators over with mbarriers (full/empty per
+// stage, full/empty per accumulator), so loads, MMAs and stores overlap.
+// Every mbarrier wait is bounded; on expiry the role records an error code
+// and leaves its loop, and the TMEM the CTA holds is freed on exit.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "dense.hpp"
+
+namespace hisv {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 ::"r"(smem_u32(slot)), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void proxy_fence_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// One bounded poll of the barrier phase with the given parity.
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// D[tmem] (+)= A[smem desc] . B[smem desc]^T, BF16 in, FP32 accumulate.
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
+}
+// Plain arrive of this thread on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait for the phase of the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; i++)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+// Arrive on the mbarrier once all previously issued MMAs of this thread complete.
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+// 32 consecutive TMEM columns of this thread's lane (32x32b shape).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                   "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle: start address,
+// leading byte offset (unused for this layout, 1), stride byte offset 1024
+// (between 8-row groups), descriptor version 1, layout type 2 (128B swizzle).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D format F32 (bits 4-5 = 1), A and B
+// BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element k (0..63 within a 64-element k-block) of row r in a
+// K-major 128-byte-swizzled block: 16-byte chunk index XOR (row mod 8).
+__device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t k) {
+    return r * 128u + ((((k >> 3) ^ (r & 7u)) & 7u) << 4) + ((k & 7u) << 1);
+}
+
+}  // namespace
+
+
+constexpr int EPI_WARPS = 4;     // TMEM lane quarters 0..3
+constexpr int PROD_WARPS = 8;
+constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
+constexpr int DENSE_THREADS = (MMA_WARP + 1) * 32;
+constexpr int PROD_THREADS = PROD_WARPS * 32;
+constexpr uint32_t DENSE_SMEM = 3 * 65536 + 1024 + 1024 + 512;   // A + 2 B stages + align + column table + bars
+constexpr uint32_t DENSE_TMEM_COLS = 256;                         // two 128-column FP32 accumulators
+constexpr uint32_t WAIT_LIMIT = 1u << 24;                         // bounded mbarrier polls
+
+__global__ void __launch_bounds__(DENSE_THREADS, 1)
+k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const uint8_t *__restrict__ a_img,
+         uint64_t n_tiles, int *__restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *const base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *const sA = base;
+    uint8_t *const sB0 = base + 65536;
+    uint64_t *const colg = reinterpret_cast<uint64_t *>(base + 3 * 65536);          // 128 column offsets
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(base + 3 * 65536 + 1024);   // 8 barriers
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(base + 3 * 65536 + 1024 + 64);
+    uint64_t *const full = bars, *const empty = bars + 2, *const accfull = bars + 4, *const accempty = bars + 6;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int i = tid; i < DENSE_A_BYTES / 16; i += DENSE_THREADS)
+        reinterpret_cast<uint4 *>(sA)[i] = reinterpret_cast<const uint4 *>(a_img)[i];
+    if (tid < 128) {   // global offset of each column of a tile
+        uint64_t g = 0;
+        for (int b = 0; b < DENSE_COLS; b++)
+            if ((tid >> b) & 1) g |= 1ull << L.col_q[b];
+        colg[tid] = g;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2; s++) {
+            mbar_init(&full[s], PROD_THREADS);
+            mbar_init(&empty[s], 1);
+            mbar_init(&accfull[s], 1);
+            mbar_init(&accempty[s], EPI_WARPS * 32);
+        }
+        mbar_init_fence();
+    }
+    if (warp == MMA_WARP) {
+        tmem_alloc(tslot, DENSE_TMEM_COLS);
+        tmem_relinquish();
+    }
+    proxy_fence_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp >= EPI_WARPS && warp < MMA_WARP) {
+        // ------------------------------------------------------ producers
+        const int ptid = tid - EPI_WARPS * 32;
+        uint64_t g_t = 0;
+        uint32_t l_t = 0, n_t = 0;
+        {
+            int pl = 0, cl = 0;
+            for (int s = 0; s < 13; s++) {
+                const bool part = (L.slot_part >> s) & 1;
+                if (s < 8 && ((ptid >> s) & 1)) {
+                    g_t |= 1ull << L.slot_q[s];
+                    if (part) l_t |= 1u << pl;
+                    else n_t |= 1u << cl;
+                }
+                if (part) pl++;
+                else cl++;
+            }
+        }
+        uint64_t g_hi[5];
+#pragma unroll
+        for (int b = 0; b < 5; b++) g_hi[b] = 1ull << L.slot_q[8 + b];
+        uint32_t i = 0;
+        for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
+            const uint32_t s = i & 1;
+            if (i >= 2 && !mbar_wait(&empty[s], ((i >> 1) - 1) & 1, WAIT_LIMIT)) {
+                atomicExch(err, 1);
+                break;
+            }
+            uint64_t tbase = 0;
+            {
+                uint64_t m = L.outer_mask, v = tile;
+                while (m) {
+                    const uint64_t low = m & (~m + 1);
+                    if (v & 1) tbase |= low;
+                    v >>= 1;
+                    m ^= low;
+                }
+            }
+            uint8_t *const sB = sB0 + s * 65536;
+            const int pl0 = __popc(L.slot_part & 0xFF);
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+            float2 x[16];
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) {
+                const int j = 16 * half + jj;
+                uint64_t g = tbase | g_t;
+#pragma unroll
+                for (int b = 0; b < 5; b++)
+                    if ((j >> b) & 1) g |= g_hi[b];
+                x[jj] = __ldcs(sv + g);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) {
+                const int j = 16 * half + jj;
+                uint32_t l = l_t, nn = n_t;
+                {
+                    int pl = pl0, cl = 8 - pl0;
+#pragma unroll
+                    for (int b = 0; b < 5; b++) {
+                        const bool part = (L.slot_part >> (8 + b)) & 1;
+                        if ((j >> b) & 1) {
+                            if (part) l |= 1u << pl;
+                            else nn |= 1u << cl;
+                        }
+                        if (part) pl++;
+                        else cl++;
+                    }
+                }
+                const __nv_bfloat16 hr = __float2bfloat16_rn(x[jj].x), hi = __float2bfloat16_rn(x[jj].y);
+                const __nv_bfloat16 lr = __float2bfloat16_rn(x[jj].x - __bfloat162float(hr));
+                const __nv_bfloat16 li = __float2bfloat16_rn(x[jj].y - __bfloat162float(hi));
+                const uint32_t kb = l >> 5, kin = (2 * l) & 63;
+                const uint32_t off = sw128_off(nn, kin);
+                __nv_bfloat162 ph, plo;
+                ph.x = hr; ph.y = hi;
+                plo.x = lr; plo.y = li;
+                *reinterpret_cast<__nv_bfloat162 *>(sB + kb * 16384 + off) = ph;
+                *reinterpret_cast<__nv_bfloat162 *>(sB + (2 + kb) * 16384 + off) = plo;
+            }
+            }
+            proxy_fence_smem();
+            mbar_arrive(&full[s]);
+        }
+    } else if (warp == MMA_WARP) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_f32(128, 128);
+            uint32_t i = 0;
+            for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
+                const uint32_t s = i & 1, u = i >> 1;
+                if (!mbar_wait(&full[s], u & 1, WAIT_LIMIT) ||
+                    (i >= 2 && !mbar_wait(&accempty[s], (u - 1) & 1, WAIT_LIMIT))) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(sA), sb = smem_u32(sB0 + s * 65536);
+                const uint32_t d = tmem + s * 128;
+                uint32_t acc = 0;
+#pragma unroll
+                for (int p = 0; p < 3; p++) {
+                    const uint32_t asel = p == 2 ? 1 : 0, bsel = p == 1 ? 1 : 0;
+#pragma unroll
+                    for (int ks = 0; ks < 8; ks++) {
+                        const uint32_t aa = sa + (asel * 2 + (ks >> 2)) * 16384 + (ks & 3) * 32;
+                        const uint32_t ba = sb + (bsel * 2 + (ks >> 2)) * 16384 + (ks & 3) * 32;
+                        umma_bf16(d, sw128_desc(aa), sw128_desc(ba), idesc, acc);
+                        acc = 1;
+                    }
+                }
+                umma_commit(&empty[s]);     // the stage's shared memory is free again
+                umma_commit(&accfull[s]);   // the accumulator holds the tile
+            }
+        }
+    } else {
+        // ------------------------------------------------------ epilogue
+        const uint32_t r_out = tid;                 // output real index 2m + c (TMEM lane)
+        const uint32_t m_out = r_out >> 1, c_out = r_out & 1;
+        uint64_t g_m = 0;
+#pragma unroll
+        for (int j = 0; j < DENSE_K; j++)
+            if ((m_out >> j) & 1) g_m |= 1ull << L.part_q[j];
+        float *const svf = reinterpret_cast<float *>(sv);
+        uint32_t i = 0;
+        for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
+            const uint32_t a = i & 1, u = i >> 1;
+            if (!mbar_wait(&accfull[a], u & 1, WAIT_LIMIT)) {
+                atomicExch(err, 1);
+                break;
+            }
+            tc_fence_after();
+            uint64_t tbase = 0;
+            {
+                uint64_t m = L.outer_mask, v = tile;
+                while (m) {
+                    const uint64_t low = m & (~m + 1);
+                    if (v & 1) tbase |= low;
+                    v >>= 1;
+                    m ^= low;
+                }
+            }
+            const uint64_t rowg = tbase | g_m;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + a * 128 + c * 32, v);
+#pragma unroll
+                for (int k = 0; k < 32; k++) __stcs(svf + 2 * (rowg | colg[c * 32 + k]) + c_out, v[k]);
+            }
+            tc_fence_before();
+            mbar_arrive(&accempty[a]);
+        }
+    }
+    __syncthreads();
+    if (warp == MMA_WARP) {
+        tc_fence_after();
+        tmem_dealloc(tmem, DENSE_TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- host ---
+static uint16_t bf16_rne(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)(u >> 16);   // inf / nan
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+static float bf16_to_f(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+static uint32_t sw128_off_host(uint32_t r, uint32_t k) {
+    return r * 128u + ((((k >> 3) ^ (r & 7u)) & 7u) << 4) + ((k & 7u) << 1);
+}
+
+void dense_a_image(const double *U, std::vector<uint8_t> &img) {
+    img.assign(DENSE_A_BYTES, 0);
+    for (int r = 0; r < 128; r++)
+        for (int k = 0; k < 128; k++) {
+            const int i = r >> 1, c = r & 1, j = k >> 1, d = k & 1;
+            const double ur = U[2 * (64 * i + j)], ui = U[2 * (64 * i + j) + 1];
+            const double R = (c == d) ? ur : (c == 0 ? -ui : ui);
+            const uint16_t hi = bf16_rne((float)R);
+            const uint16_t lo = bf16_rne((float)(R - (double)bf16_to_f(hi)));
+            const uint32_t kb = (uint32_t)k >> 6, off = sw128_off_host((uint32_t)r, (uint32_t)k & 63u);
+            std::memcpy(&img[(0 * 2 + kb) * 16384 + off], &hi, 2);
+            std::memcpy(&img[(1 * 2 + kb) * 16384 + off], &lo, 2);
+        }
+}
+
+cudaError_t launch_dense6(void *sv, const DenseLaunch &L, const void *a_img, uint64_t n_tiles, int *d_err,
+                          cudaStream_t st) {
+    static uint64_t attr_set = 0;
+    static int sms[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    if (!((attr_set >> dev) & 1)) {
+        e = cudaFuncSetAttribute(k_dense6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        attr_set |= 1ull << dev;
+    }
+    uint64_t grid = (uint64_t)sms[dev];
+    if (grid > n_tiles) grid = n_tiles;
+    if (grid < 1) grid = 1;
+    k_dense6<<<(unsigned)grid, DENSE_THREADS, DENSE_SMEM, st>>>(reinterpret_cast<float2 *>(sv), L,
+                                                                 reinterpret_cast<const uint8_t *>(a_img), n_tiles,
+                                                                 d_err);
+    return cudaGetLastError();
+}
+
+}  // namespace hisv

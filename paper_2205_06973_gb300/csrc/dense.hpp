@@ -1,0 +1,37 @@
+// Dense fused-part path: a part acting on 6 qubits is applied as one 64x64
+// complex matrix, i.e. a 128x128 real GEMM on interleaved (re, im) data, on
+// the tcgen05 tensor cores in split BF16 (A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// FP32 accumulation in tensor memory).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+namespace hisv {
+
+constexpr int DENSE_K = 6;                    // qubits of a dense part
+constexpr int DENSE_COLS = 7;                 // column qubits of one tile (128 columns)
+constexpr int DENSE_A_BYTES = 64 * 1024;      // A image: [hi, lo] x [k-block 0, 1] x 128 rows x 128 B
+
+// Launch record of one dense part (by value).
+struct DenseLaunch {
+    uint64_t outer_mask;       // qubits outside the tile: the tile index is deposited here
+    int32_t n;
+    uint8_t part_q[DENSE_K];   // qubit of local bit j of the 64-amplitude vector (ascending)
+    uint8_t col_q[DENSE_COLS]; // qubit of column bit j (ascending)
+    uint8_t slot_q[16];        // the 13 tile qubits in ascending order (gather layout)
+    uint16_t slot_part;        // bit s set: slot s is a part qubit
+    uint16_t pad;
+};
+
+// Host: build the A image of a 64x64 complex unitary U (row-major, interleaved
+// re/im doubles): real block form R[2i+c][2j+d], split to BF16 hi/lo, laid out
+// K-major with the 128-byte swizzle the tensor-core descriptors expect.
+void dense_a_image(const double *U, std::vector<uint8_t> &img);
+
+// Whether the tensor-core kernel can run: compute capability 10.3 device.
+cudaError_t launch_dense6(void *sv, const DenseLaunch &L, const void *a_img, uint64_t n_tiles,
+                          int *d_err, cudaStream_t st);
+
+}  // namespace hisv

@@ -104,8 +104,66 @@ static std::vector<int> order_thread_slots(std::vector<int> cand, const std::vec
     return out;
 }
 
+void fused_unitary(const std::vector<GateRef> &gates, const std::vector<int> &ids, const int *qs, int k,
+                   std::vector<double> &U) {
+    const int D = 1 << k;
+    U.assign((size_t)2 * D * D, 0.0);
+    for (int i = 0; i < D; i++) U[2 * (D * i + i)] = 1.0;
+    std::vector<double> v(2 * D), w(2 * D);
+    for (int g : ids) {
+        const GateRef &gr = gates[g];
+        int loc[2] = {0, 0};
+        for (int a = 0; a < gr.arity; a++)
+            for (int j = 0; j < k; j++)
+                if (qs[j] == gr.q[a]) loc[a] = j;
+        double m[32];
+        if (gr.arity == 1) gate_matrix_1q(gr.kind, gr.theta, m);
+        else gate_matrix_2q(gr.kind, gr.theta, m);
+        for (int c = 0; c < D; c++) {   // column c of U is the image of basis state c
+            for (int r = 0; r < D; r++) {
+                v[2 * r] = U[2 * (D * r + c)];
+                v[2 * r + 1] = U[2 * (D * r + c) + 1];
+            }
+            w = v;
+            if (gr.arity == 1) {
+                const int s = 1 << loc[0];
+                for (int x = 0; x < D; x++) {
+                    if (x & s) continue;
+                    const double ar = v[2 * x], ai = v[2 * x + 1], br = v[2 * (x + s)], bi = v[2 * (x + s) + 1];
+                    for (int o = 0; o < 2; o++) {
+                        const double *mr = m + 4 * o;
+                        w[2 * (x + o * s)] = mr[0] * ar - mr[1] * ai + mr[2] * br - mr[3] * bi;
+                        w[2 * (x + o * s) + 1] = mr[0] * ai + mr[1] * ar + mr[2] * bi + mr[3] * br;
+                    }
+                }
+            } else {
+                const int s0 = 1 << loc[0], s1 = 1 << loc[1];
+                for (int x = 0; x < D; x++) {
+                    if ((x & s0) || (x & s1)) continue;
+                    const int idx[4] = {x, x + s0, x + s1, x + s0 + s1};
+                    for (int r = 0; r < 4; r++) {
+                        double re = 0, im = 0;
+                        for (int cc = 0; cc < 4; cc++) {
+                            const double mr = m[2 * (4 * r + cc)], mi = m[2 * (4 * r + cc) + 1];
+                            re += mr * v[2 * idx[cc]] - mi * v[2 * idx[cc] + 1];
+                            im += mr * v[2 * idx[cc] + 1] + mi * v[2 * idx[cc]];
+                        }
+                        w[2 * idx[r]] = re;
+                        w[2 * idx[r] + 1] = im;
+                    }
+                }
+            }
+            for (int r = 0; r < D; r++) {
+                U[2 * (D * r + c)] = w[2 * r];
+                U[2 * (D * r + c) + 1] = w[2 * r + 1];
+            }
+        }
+    }
+}
+
 bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector<uint32_t> &pog,
-                     uint32_t n_parts, bool fp64, int t_cfg, int R, Program &prog, std::string &err) {
+                     uint32_t n_parts, bool fp64, int t_cfg, int R, int dense_mode, Program &prog,
+                     std::string &err) {
     prog = Program();
     prog.fp64 = fp64;
     prog.R = R;
@@ -135,6 +193,40 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
         if (gl.empty()) continue;
         uint64_t S = 0;
         for (int g : gl) S |= gmask[g];
+        if (dense_mode == 1 && !fp64 && popc(S) <= DENSE_K && n >= DENSE_K + DENSE_COLS) {
+            // dense part: the part's qubits padded with the lowest others to 6,
+            // columns on the lowest 7 remaining qubits
+            uint64_t P = S, C = 0;
+            for (int q = 0; q < n && popc(P) < DENSE_K; q++) P |= 1ull << q;
+            for (int q = 0; q < n && popc(C) < DENSE_COLS; q++)
+                if (!((P >> q) & 1)) C |= 1ull << q;
+            DenseLaunch D;
+            std::memset(&D, 0, sizeof(D));
+            D.n = n;
+            D.outer_mask = all & ~(P | C);
+            int qs[DENSE_K], jp = 0, jc = 0, js = 0;
+            for (int q = 0; q < n; q++) {
+                if ((P >> q) & 1) {
+                    qs[jp] = q;
+                    D.part_q[jp++] = (uint8_t)q;
+                    D.slot_part |= (uint16_t)(1u << js);
+                    D.slot_q[js++] = (uint8_t)q;
+                } else if ((C >> q) & 1) {
+                    D.col_q[jc++] = (uint8_t)q;
+                    D.slot_q[js++] = (uint8_t)q;
+                }
+            }
+            std::vector<double> U;
+            fused_unitary(gates, gl, qs, DENSE_K, U);
+            std::vector<uint8_t> img;
+            dense_a_image(U.data(), img);
+            prog.kind.push_back(1);
+            prog.index.push_back((uint32_t)prog.dense.size());
+            prog.dense.push_back(D);
+            prog.dense_tiles.push_back(1ull << (n - DENSE_K - DENSE_COLS));
+            prog.a_img.insert(prog.a_img.end(), img.begin(), img.end());
+            continue;
+        }
         if (popc(S) > t) {
             err = "part " + std::to_string(pi) + " has " + std::to_string(popc(S)) + " qubits > tile " + std::to_string(t);
             return false;
@@ -312,6 +404,8 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
         L.gr = fr;
         L.gi = fi;
         L.flags = (last_tphase || fr != 1.0 || fi != 0.0) ? PL_STORE_FACTOR : 0u;
+        prog.kind.push_back(0);
+        prog.index.push_back((uint32_t)prog.parts.size());
         prog.parts.push_back(L);
         prog.n_tiles.push_back(1ull << (n - t));
     }

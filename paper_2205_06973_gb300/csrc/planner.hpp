@@ -3,6 +3,7 @@
 #include <string>
 #include <vector>
 
+#include "dense.hpp"
 #include "partition.hpp"
 #include "program.hpp"
 
@@ -17,6 +18,13 @@ struct Program {
     std::vector<Phase> phases;
     std::vector<Op> ops;
     std::vector<double> coefs;
+    // execution order over all parts: kind 0 = gate-list part parts[index],
+    // kind 1 = dense tensor-core part dense[index] (A image a_img[index])
+    std::vector<uint8_t> kind;
+    std::vector<uint32_t> index;
+    std::vector<DenseLaunch> dense;
+    std::vector<uint64_t> dense_tiles;
+    std::vector<uint8_t> a_img;           // DENSE_A_BYTES per dense part
 };
 
 // Gate matrices of the library (row-major complex, interleaved re/im):
@@ -27,7 +35,15 @@ bool gate_is_two_qubit(int kind);
 
 // Compile the parts (part_of_gate numbered in execution order) for a tile of
 // t_cfg qubits (t = min(n, t_cfg)) and R register bits.
+// dense_mode: 0 = gate lists only; 1 = every part of at most 6 qubits runs
+// as a dense tensor-core part (complex64, n >= 13).
 bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector<uint32_t> &pog,
-                     uint32_t n_parts, bool fp64, int t_cfg, int R, Program &prog, std::string &err);
+                     uint32_t n_parts, bool fp64, int t_cfg, int R, int dense_mode, Program &prog,
+                     std::string &err);
+
+// Fused unitary of gates acting on the qubits qs[0..k) (local bit j <-> qs[j]):
+// U = G_last ... G_first as a 2^k x 2^k row-major interleaved complex matrix.
+void fused_unitary(const std::vector<GateRef> &gates, const std::vector<int> &ids, const int *qs, int k,
+                   std::vector<double> &U);
 
 }  // namespace hisv

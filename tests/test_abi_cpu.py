@@ -125,7 +125,9 @@ def test_plan_stats_counts(native):
     p = _plan(native, g, n, "dagp", 8)
     s = p.stats("c64", 12)
     pog, P = p.export()
-    assert s["passes"] == P
+    assert s["passes"] == P and s["dense"] == 0
+    d = p.stats("c64", 12, tc=True)
+    assert d["passes"] == P and 0 < d["dense"] <= P
     assert s["phases"] >= P
     # every gate but SWAP becomes at least one op
     assert s["ops"] >= len(g)
