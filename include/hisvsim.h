@@ -152,6 +152,35 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags);
  * NULL). Synchronises the stream when norm_out is not NULL. */
 sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *norm_out);
 
+/* ------------------------------------------------- allocation-free probs ---
+ * sv_probs_noalloc: the same probabilities and FP64-accumulated norm as
+ * sv_measure_probs, for callers that must not allocate device memory: a host
+ * framework that owns all device memory through its own pool under a fixed
+ * budget, or a latency-critical loop where a device allocation could stall
+ * the device. It allocates nothing (no cudaMalloc/cudaFree, no allocating
+ * library call); its partial sums live in one static device array of
+ * SV_NOALLOC_MAX_BLOCKS + 1 doubles (32 KiB) inside this library, which every
+ * GPU that loads the library keeps until the process exits. The paper has no
+ * counterpart; it is an interface addition of this library.
+ *   dev_state  device pointer to 2^n amplitudes (layout of prec), caller-owned
+ *   dev_probs  device output of 2^n floats (doubles if out_fp64), or NULL
+ *   dev_norm   device output of one double (sum |a_x|^2), or NULL
+ *   n_blocks   width of the FP64 reduction = partial sums used, 0 for the
+ *              default (SV_NOALLOC_DEFAULT_BLOCKS); larger than
+ *              SV_NOALLOC_MAX_BLOCKS is rejected with SV_ERR_ARG
+ *   stream     cudaStream_t (NULL = legacy default stream); stream-ordered,
+ *              no synchronisation.
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call shares the one array, which keeps
+ * the last call's contents; each call writes every partial sum it reads, so
+ * nothing needs clearing, but calls that overlap on the GPU (different
+ * streams, or threads without ordering) race on it. */
+#define SV_NOALLOC_MAX_BLOCKS 4096
+#define SV_NOALLOC_DEFAULT_BLOCKS 1216
+sv_status sv_probs_noalloc(const void *dev_state, int n_qubits, sv_precision prec, void *dev_probs,
+                           int out_fp64, double *dev_norm, int n_blocks, void *stream);
+
 /* Thread-local description of the last non-OK status (never NULL). */
 const char *sv_last_error(void);
 /* Library version string. */

@@ -19,6 +19,7 @@ METHODS = {"none": SV_PART_NONE, "nat": SV_PART_NAT, "dfs": SV_PART_DFS, "dagp":
 SV_FLAG_GATEWISE = 0x1
 SV_FLAG_SYNC = 0x2
 SV_FLAG_TC_DENSE = 0x4
+SV_NOALLOC_MAX_BLOCKS = 4096
 
 GATE_KINDS = ("H", "X", "Y", "Z", "S", "T", "RX", "RY", "RZ", "P", "CX", "CZ", "CP", "SWAP")
 KIND = {name: i for i, name in enumerate(GATE_KINDS)}
@@ -63,6 +64,7 @@ _SIGS = {
     "sv_plan_destroy": ([_vp], ctypes.c_int),
     "sv_apply_parts": ([_vp, _vp, ctypes.c_uint32], ctypes.c_int),
     "sv_measure_probs": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "sv_probs_noalloc": ([_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "sv_last_error": ([], ctypes.c_char_p),
     "sv_version": ([], ctypes.c_char_p),
 }

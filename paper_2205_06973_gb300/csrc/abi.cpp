@@ -35,6 +35,10 @@ sv_status fail(sv_status st, const std::string &msg) {
 constexpr int kProbBlocks = 152 * 8;
 }  // namespace
 
+namespace hisv {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}
+
 struct DevProgram {
     int dev = -1;
     Phase *d_phases = nullptr;
