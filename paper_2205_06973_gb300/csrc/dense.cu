@@ -4,21 +4,26 @@
 // gates). With amplitudes stored as interleaved (re, im) floats, the part
 // maps every column x (64 amplitudes that share the other n - 6 bits) to
 // R x, R the 128x128 real block form R[2i+c][2j+d] of U. One CTA tile is
-// 128 columns (the lowest 7 non-part qubits) and the GEMM
-//     D[128 x 128] = R[128 x 128] . X^T     (M = 128, N = 128, K = 128)
+// 64 columns (the lowest 6 non-part qubits) and the GEMM
+//     D[128 x 64] = R[128 x 128] . X^T      (M = 128, N = 64, K = 128)
 // runs as split BF16: R = R_hi + R_lo, X = X_hi + X_lo, and
 // D = R_hi X_hi + R_hi X_lo + R_lo X_hi with FP32 accumulation in tensor
 // memory (the dropped R_lo X_lo term is below 2^-16 relative).
 //
-// Warp-specialised persistent CTA (13 warps): 8 producer warps gather tile i
-// from HBM, split it to BF16 and write it K-major with the 128-byte swizzle
-// into shared stage i%2; one thread of the MMA warp issues the 24 MMAs of
-// tile i into TMEM accumulator i%2; 4 epilogue warps drain the accumulator
-// (tcgen05.ld, one TMEM lane quarter each) and scatter the tile back to HBM.
-// The roles hand stages and accumulators over with mbarriers (full/empty per
-// stage, full/empty per accumulator), so loads, MMAs and stores overlap.
-// Every mbarrier wait is bounded; on expiry the role records an error code
-// and leaves its loop, and the TMEM the CTA holds is freed on exit.
+// Warp-specialised persistent CTA (13 warps), four pipeline stages:
+//  * 8 producer warps gather tiles from HBM (warming L2 two tiles ahead with
+//    prefetches), split them to BF16 and write them K-major with the 128-byte
+//    swizzle into shared stage i%4;
+//  * one thread of the MMA warp issues the 24 MMAs of tile i into TMEM
+//    accumulator i%4 and commits them;
+//  * 8 epilogue warps drain the accumulator (tcgen05.ld; two warps per TMEM
+//    lane quarter, 32 columns each), stage the FP32 tile in the freed shared
+//    stage in address order (XOR-swizzled), and write it back with coalesced
+//    8-byte stores.
+// Stages and accumulators are handed over with mbarriers (full / empty per
+// stage, full / empty per accumulator). Every mbarrier wait is bounded; on
+// expiry the role records an error code and leaves its loop, and the TMEM
+// the CTA holds is freed on exit.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -136,14 +141,34 @@ __device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t k) {
 }  // namespace
 
 
-constexpr int EPI_WARPS = 4;     // TMEM lane quarters 0..3
+
+constexpr int EPI_WARPS = 8;     // two per TMEM lane quarter (warp w: quarter w % 4, column half w / 4)
 constexpr int PROD_WARPS = 8;
 constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
 constexpr int DENSE_THREADS = (MMA_WARP + 1) * 32;
 constexpr int PROD_THREADS = PROD_WARPS * 32;
-constexpr uint32_t DENSE_SMEM = 3 * 65536 + 1024 + 1024 + 512;   // A + 2 B stages + align + column table + bars
-constexpr uint32_t DENSE_TMEM_COLS = 256;                         // two 128-column FP32 accumulators
+constexpr int EPI_THREADS = EPI_WARPS * 32;
+constexpr int NSTAGE = 4;
+constexpr int STAGE_BYTES = 32768;    // B_hi, B_lo x 2 k-blocks x 64 rows x 128 B; or the FP32 output tile
+constexpr int KBLK_BYTES = 8192;      // 64 rows x 128 B
+constexpr uint32_t DENSE_SMEM = 65536 + NSTAGE * STAGE_BYTES + 1024 + 512 + 256;
+constexpr uint32_t DENSE_TMEM_COLS = 256;                         // four 64-column FP32 accumulators
 constexpr uint32_t WAIT_LIMIT = 1u << 24;                         // bounded mbarrier polls
+
+// swizzled word index of tile element L (12 bits, address order over the
+// tile's slots): the high nibbles are folded into the low one
+__device__ __forceinline__ uint32_t stage_phys(uint32_t L) { return L ^ (((L >> 4) ^ (L >> 8)) & 15u); }
+
+__device__ __forceinline__ uint64_t deposit_tile(uint64_t v, uint64_t mask) {
+    uint64_t out = 0;
+    while (mask) {
+        const uint64_t low = mask & (~mask + 1);
+        if (v & 1) out |= low;
+        v >>= 1;
+        mask ^= low;
+    }
+    return out;
+}
 
 __global__ void __launch_bounds__(DENSE_THREADS, 1)
 k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const uint8_t *__restrict__ a_img,
@@ -152,26 +177,30 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
     uint8_t *const base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *const sA = base;
     uint8_t *const sB0 = base + 65536;
-    uint64_t *const colg = reinterpret_cast<uint64_t *>(base + 3 * 65536);          // 128 column offsets
-    uint64_t *const bars = reinterpret_cast<uint64_t *>(base + 3 * 65536 + 1024);   // 8 barriers
-    uint32_t *const tslot = reinterpret_cast<uint32_t *>(base + 3 * 65536 + 1024 + 64);
-    uint64_t *const full = bars, *const empty = bars + 2, *const accfull = bars + 4, *const accempty = bars + 6;
+    uint32_t *const colL = reinterpret_cast<uint32_t *>(base + 65536 + NSTAGE * STAGE_BYTES);   // 64 entries
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(base + 65536 + NSTAGE * STAGE_BYTES + 256);
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(base + 65536 + NSTAGE * STAGE_BYTES + 256 + 16 * 8);
+    uint64_t *const full = bars, *const empty = bars + NSTAGE, *const accfull = bars + 2 * NSTAGE,
+                    *const accempty = bars + 3 * NSTAGE;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (int i = tid; i < DENSE_A_BYTES / 16; i += DENSE_THREADS)
         reinterpret_cast<uint4 *>(sA)[i] = reinterpret_cast<const uint4 *>(a_img)[i];
-    if (tid < 128) {   // global offset of each column of a tile
-        uint64_t g = 0;
-        for (int b = 0; b < DENSE_COLS; b++)
-            if ((tid >> b) & 1) g |= 1ull << L.col_q[b];
-        colg[tid] = g;
+    if (tid < 64) {   // swizzled staging index of column n (its bits deposited into the column slots)
+        uint32_t l = 0;
+        for (int s = 0, cb = 0; s < 12; s++)
+            if (!((L.slot_part >> s) & 1)) {
+                if ((tid >> cb) & 1) l |= 1u << s;
+                cb++;
+            }
+        colL[tid] = stage_phys(l);
     }
     if (tid == 0) {
-        for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < NSTAGE; s++) {
             mbar_init(&full[s], PROD_THREADS);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], EPI_THREADS);
             mbar_init(&accfull[s], 1);
-            mbar_init(&accempty[s], EPI_WARPS * 32);
+            mbar_init(&accempty[s], EPI_THREADS);
         }
         mbar_init_fence();
     }
@@ -187,12 +216,14 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
 
     if (warp >= EPI_WARPS && warp < MMA_WARP) {
         // ------------------------------------------------------ producers
+        // tile element L = ptid (slots 0..7) | j << 8 (slots 8..11), j < 16
         const int ptid = tid - EPI_WARPS * 32;
         uint64_t g_t = 0;
         uint32_t l_t = 0, n_t = 0;
+        int pl0 = 0;
         {
             int pl = 0, cl = 0;
-            for (int s = 0; s < 13; s++) {
+            for (int s = 0; s < 12; s++) {
                 const bool part = (L.slot_part >> s) & 1;
                 if (s < 8 && ((ptid >> s) & 1)) {
                     g_t |= 1ull << L.slot_q[s];
@@ -201,89 +232,92 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
                 }
                 if (part) pl++;
                 else cl++;
+                if (s == 7) pl0 = pl;
             }
         }
-        uint64_t g_hi[5];
+        uint64_t g_hi[4];
 #pragma unroll
-        for (int b = 0; b < 5; b++) g_hi[b] = 1ull << L.slot_q[8 + b];
+        for (int b = 0; b < 4; b++) g_hi[b] = 1ull << L.slot_q[8 + b];
         uint32_t i = 0;
         for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
-            const uint32_t s = i & 1;
-            if (i >= 2 && !mbar_wait(&empty[s], ((i >> 1) - 1) & 1, WAIT_LIMIT)) {
+            const uint32_t s = i & (NSTAGE - 1);
+            if (i >= NSTAGE && !mbar_wait(&empty[s], ((i >> 2) - 1) & 1, WAIT_LIMIT)) {
                 atomicExch(err, 1);
                 break;
             }
-            uint64_t tbase = 0;
-            {
-                uint64_t m = L.outer_mask, v = tile;
-                while (m) {
-                    const uint64_t low = m & (~m + 1);
-                    if (v & 1) tbase |= low;
-                    v >>= 1;
-                    m ^= low;
-                }
-            }
-            uint8_t *const sB = sB0 + s * 65536;
-            const int pl0 = __popc(L.slot_part & 0xFF);
-#pragma unroll
-            for (int half = 0; half < 2; half++) {
             float2 x[16];
+            {
+                const uint64_t tb = deposit_tile(tile, L.outer_mask) | g_t;
 #pragma unroll
-            for (int jj = 0; jj < 16; jj++) {
-                const int j = 16 * half + jj;
-                uint64_t g = tbase | g_t;
+                for (int j = 0; j < 16; j++) {
+                    uint64_t g = tb;
 #pragma unroll
-                for (int b = 0; b < 5; b++)
-                    if ((j >> b) & 1) g |= g_hi[b];
-                x[jj] = __ldcs(sv + g);
-            }
-#pragma unroll
-            for (int jj = 0; jj < 16; jj++) {
-                const int j = 16 * half + jj;
-                uint32_t l = l_t, nn = n_t;
-                {
-                    int pl = pl0, cl = 8 - pl0;
-#pragma unroll
-                    for (int b = 0; b < 5; b++) {
-                        const bool part = (L.slot_part >> (8 + b)) & 1;
-                        if ((j >> b) & 1) {
-                            if (part) l |= 1u << pl;
-                            else nn |= 1u << cl;
-                        }
-                        if (part) pl++;
-                        else cl++;
-                    }
+                    for (int b = 0; b < 4; b++)
+                        if ((j >> b) & 1) g |= g_hi[b];
+                    x[j] = __ldcs(sv + g);
                 }
-                const __nv_bfloat16 hr = __float2bfloat16_rn(x[jj].x), hi = __float2bfloat16_rn(x[jj].y);
-                const __nv_bfloat16 lr = __float2bfloat16_rn(x[jj].x - __bfloat162float(hr));
-                const __nv_bfloat16 li = __float2bfloat16_rn(x[jj].y - __bfloat162float(hi));
-                const uint32_t kb = l >> 5, kin = (2 * l) & 63;
-                const uint32_t off = sw128_off(nn, kin);
-                __nv_bfloat162 ph, plo;
-                ph.x = hr; ph.y = hi;
-                plo.x = lr; plo.y = li;
-                *reinterpret_cast<__nv_bfloat162 *>(sB + kb * 16384 + off) = ph;
-                *reinterpret_cast<__nv_bfloat162 *>(sB + (2 + kb) * 16384 + off) = plo;
             }
+            // warm L2 with the tile two steps ahead (no registers held)
+            if (tile + 2ull * gridDim.x < n_tiles) {
+                const uint64_t tb = deposit_tile(tile + 2ull * gridDim.x, L.outer_mask) | g_t;
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    uint64_t g = tb;
+#pragma unroll
+                    for (int b = 0; b < 4; b++)
+                        if ((j >> b) & 1) g |= g_hi[b];
+                    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(sv + g));
+                }
             }
-            proxy_fence_smem();
-            mbar_arrive(&full[s]);
+            {
+                uint8_t *const sB = sB0 + s * STAGE_BYTES;
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    uint32_t l = l_t, nn = n_t;
+                    {
+                        int pl = pl0, cl = 8 - pl0;
+#pragma unroll
+                        for (int b = 0; b < 4; b++) {
+                            const bool part = (L.slot_part >> (8 + b)) & 1;
+                            if ((j >> b) & 1) {
+                                if (part) l |= 1u << pl;
+                                else nn |= 1u << cl;
+                            }
+                            if (part) pl++;
+                            else cl++;
+                        }
+                    }
+                    const float2 v = x[j];
+                    const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi = __float2bfloat16_rn(v.y);
+                    const __nv_bfloat16 lr = __float2bfloat16_rn(v.x - __bfloat162float(hr));
+                    const __nv_bfloat16 li = __float2bfloat16_rn(v.y - __bfloat162float(hi));
+                    const uint32_t kb = l >> 5, kin = (2 * l) & 63;
+                    const uint32_t off = sw128_off(nn, kin);
+                    __nv_bfloat162 ph, plo;
+                    ph.x = hr; ph.y = hi;
+                    plo.x = lr; plo.y = li;
+                    *reinterpret_cast<__nv_bfloat162 *>(sB + kb * KBLK_BYTES + off) = ph;
+                    *reinterpret_cast<__nv_bfloat162 *>(sB + (2 + kb) * KBLK_BYTES + off) = plo;
+                }
+                proxy_fence_smem();
+                mbar_arrive(&full[s]);
+            }
         }
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(128, 128);
+            const uint32_t idesc = idesc_bf16_f32(128, 64);
             uint32_t i = 0;
             for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
-                const uint32_t s = i & 1, u = i >> 1;
+                const uint32_t s = i & (NSTAGE - 1), u = i >> 2;
                 if (!mbar_wait(&full[s], u & 1, WAIT_LIMIT) ||
-                    (i >= 2 && !mbar_wait(&accempty[s], (u - 1) & 1, WAIT_LIMIT))) {
+                    (i >= NSTAGE && !mbar_wait(&accempty[s], (u - 1) & 1, WAIT_LIMIT))) {
                     atomicExch(err, 1);
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = smem_u32(sA), sb = smem_u32(sB0 + s * 65536);
-                const uint32_t d = tmem + s * 128;
+                const uint32_t sa = smem_u32(sA), sb = smem_u32(sB0 + s * STAGE_BYTES);
+                const uint32_t d = tmem + s * 64;
                 uint32_t acc = 0;
 #pragma unroll
                 for (int p = 0; p < 3; p++) {
@@ -291,52 +325,62 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
 #pragma unroll
                     for (int ks = 0; ks < 8; ks++) {
                         const uint32_t aa = sa + (asel * 2 + (ks >> 2)) * 16384 + (ks & 3) * 32;
-                        const uint32_t ba = sb + (bsel * 2 + (ks >> 2)) * 16384 + (ks & 3) * 32;
+                        const uint32_t ba = sb + (bsel * 2 + (ks >> 2)) * KBLK_BYTES + (ks & 3) * 32;
                         umma_bf16(d, sw128_desc(aa), sw128_desc(ba), idesc, acc);
                         acc = 1;
                     }
                 }
-                umma_commit(&empty[s]);     // the stage's shared memory is free again
-                umma_commit(&accfull[s]);   // the accumulator holds the tile
+                umma_commit(&accfull[s]);   // accumulator ready; the stage's B operand is consumed
             }
         }
     } else {
         // ------------------------------------------------------ epilogue
-        const uint32_t r_out = tid;                 // output real index 2m + c (TMEM lane)
+        const int q = warp & 3, half = warp >> 2;   // TMEM lane quarter, column half
+        const uint32_t r_out = 32 * q + lane;       // output real index 2m + c (TMEM lane)
         const uint32_t m_out = r_out >> 1, c_out = r_out & 1;
-        uint64_t g_m = 0;
+        uint32_t Lm = 0;                             // tile element of amplitude m_out, column 0
+        for (int s = 0, pb = 0; s < 12; s++)
+            if ((L.slot_part >> s) & 1) {
+                if ((m_out >> pb) & 1) Lm |= 1u << s;
+                pb++;
+            }
+        const uint32_t pm = stage_phys(Lm);
+        // copy-out layout: tile element L = tid (slots 0..7) | j << 8 (slots 8..11)
+        uint64_t g_t = 0;
+        for (int s = 0; s < 8; s++)
+            if ((tid >> s) & 1) g_t |= 1ull << L.slot_q[s];
+        uint64_t g_hi[4];
 #pragma unroll
-        for (int j = 0; j < DENSE_K; j++)
-            if ((m_out >> j) & 1) g_m |= 1ull << L.part_q[j];
-        float *const svf = reinterpret_cast<float *>(sv);
+        for (int b = 0; b < 4; b++) g_hi[b] = 1ull << L.slot_q[8 + b];
         uint32_t i = 0;
         for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
-            const uint32_t a = i & 1, u = i >> 1;
-            if (!mbar_wait(&accfull[a], u & 1, WAIT_LIMIT)) {
+            const uint32_t s = i & (NSTAGE - 1), u = i >> 2;
+            if (!mbar_wait(&accfull[s], u & 1, WAIT_LIMIT)) {
                 atomicExch(err, 1);
                 break;
             }
             tc_fence_after();
-            uint64_t tbase = 0;
-            {
-                uint64_t m = L.outer_mask, v = tile;
-                while (m) {
-                    const uint64_t low = m & (~m + 1);
-                    if (v & 1) tbase |= low;
-                    v >>= 1;
-                    m ^= low;
-                }
-            }
-            const uint64_t rowg = tbase | g_m;
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + a * 128 + c * 32, v);
-#pragma unroll
-                for (int k = 0; k < 32; k++) __stcs(svf + 2 * (rowg | colg[c * 32 + k]) + c_out, v[k]);
-            }
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + s * 64 + 32 * half, v);
             tc_fence_before();
-            mbar_arrive(&accempty[a]);
+            mbar_arrive(&accempty[s]);
+            // FP32 tile into the freed stage, swizzled address order
+            proxy_fence_smem();
+            float *const st = reinterpret_cast<float *>(sB0 + s * STAGE_BYTES);
+#pragma unroll
+            for (int k = 0; k < 32; k++) st[2 * (pm ^ colL[32 * half + k]) + c_out] = v[k];
+            asm volatile("bar.sync 1, %0;\n" ::"n"(EPI_THREADS) : "memory");
+            const uint64_t tb = deposit_tile(tile, L.outer_mask) | g_t;
+            const float2 *const st2 = reinterpret_cast<const float2 *>(st);
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                uint64_t g = tb;
+#pragma unroll
+                for (int b = 0; b < 4; b++)
+                    if ((j >> b) & 1) g |= g_hi[b];
+                __stcs(sv + g, st2[stage_phys((uint32_t)tid | ((uint32_t)j << 8))]);
+            }
+            mbar_arrive(&empty[s]);
         }
     }
     __syncthreads();

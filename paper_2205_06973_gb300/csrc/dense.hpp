@@ -11,7 +11,7 @@
 namespace hisv {
 
 constexpr int DENSE_K = 6;                    // qubits of a dense part
-constexpr int DENSE_COLS = 7;                 // column qubits of one tile (128 columns)
+constexpr int DENSE_COLS = 6;                 // column qubits of one tile (64 columns)
 constexpr int DENSE_A_BYTES = 64 * 1024;      // A image: [hi, lo] x [k-block 0, 1] x 128 rows x 128 B
 
 // Launch record of one dense part (by value).

@@ -246,6 +246,8 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
         L.n = n;
         L.t = t;
         L.phase_begin = (uint32_t)prog.phases.size();
+        L.op_begin = (uint32_t)prog.ops.size();
+        L.coef_begin = (uint32_t)prog.coefs.size();
         for (int p = 0; p < t; p++) L.tile_q[p] = (uint8_t)q_at[p];
         // part factor: 1/sqrt2 per (unnormalised) H and e^{-i theta/2} per RZ
         double fr = 1.0, fi = 0.0;
@@ -401,6 +403,8 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
             first = false;
         }
         L.n_phases = (uint32_t)prog.phases.size() - L.phase_begin;
+        L.op_end = (uint32_t)prog.ops.size();
+        L.coef_end = (uint32_t)prog.coefs.size();
         L.gr = fr;
         L.gi = fi;
         L.flags = (last_tphase || fr != 1.0 || fi != 0.0) ? PL_STORE_FACTOR : 0u;

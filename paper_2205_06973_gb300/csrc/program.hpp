@@ -68,6 +68,8 @@ struct PartLaunch {
     int32_t t;
     uint32_t flags;          // PL_STORE_FACTOR: multiply by (gr, gi) x per-thread phase at the store
     uint32_t pad;
+    uint32_t op_begin, op_end;      // this part's ops and coefficients (contiguous ranges); the
+    uint32_t coef_begin, coef_end;  // kernel stages them in shared memory when they fit
     double gr, gi;           // part factor: 2^{-h/2} for h unnormalised H gates times RZ global phases
     uint8_t tile_q[32];      // global qubit of tile slot p (p < t); the gather/copy layout
     uint8_t store_reg_q[8];  // global qubit of register bit b in the last phase (after SWAP relabels)
@@ -75,5 +77,6 @@ struct PartLaunch {
 };
 
 constexpr uint32_t PL_STORE_FACTOR = 1u;
+constexpr uint32_t PROG_SMEM_BYTES = 8192;   // per-CTA shared-memory copy of one part's program
 
 }  // namespace hisv
