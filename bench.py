@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--method", default="dagp", choices=["nat", "dfs", "dagp"])
     ap.add_argument("--k", type=int, default=0, help="part qubit limit (0: autotuned default)")
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--tc", type=int, default=0, help="with --k: run parts of <= 6 qubits on the tensor cores")
     ap.add_argument("--n", type=int, default=28)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
@@ -207,16 +208,23 @@ def run_ours(a):
     from paper_2205_06973_gb300 import api
 
     n, gates = synth.layered_28q(n=a.n)
-    k = choose_k(a.method, a.k)
-    plan = api.Plan(gates, n, a.method, k)
     st = api.State(n, "c64", tile=a.tile)
-    stats = plan.stats("c64", a.tile)
+    if a.k:
+        choice = {"method": a.method, "k": a.k, "tc": bool(a.tc), "tile": a.tile, "trials": []}
+    else:
+        from paper_2205_06973_gb300 import autotune
+        choice = autotune.tune_state(f"layered{n}", n, gates, "c64", state=st, use_cache=False)
+    k, tc, method = choice["k"], bool(choice["tc"]), choice["method"]
+    if choice.get("tile"):
+        st = api.State(n, "c64", tile=choice["tile"])
+    plan = api.Plan(gates, n, method, k)
+    stats = plan.stats("c64", choice.get("tile", 0), tc=tc)
     passes = stats["passes"]
     bytes_per_pass = 2 * st.nbytes
     bytes_per_step = passes * bytes_per_pass
 
     for _ in range(max(a.warmup, 3)):
-        st.apply(plan)
+        st.apply(plan, tc=tc)
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
@@ -226,7 +234,7 @@ def run_ours(a):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st.stream)
     for _ in range(a.steps):
-        st.apply(plan)
+        st.apply(plan, tc=tc)
     e1.record(st.stream)
     torch.cuda.synchronize()
     barrier(ws)
@@ -240,10 +248,11 @@ def run_ours(a):
     launch_ms = ms / passes
     peak, peak_kind = peaks()
     achieved = bytes_per_pass / (launch_ms / 1e3) / 1e9
-    wkey = f"layered{n}_{a.method}_k{k}_c64_t{a.tile or 'auto'}"
+    kernel = "k_dense6" if (tc and stats["dense"] * 2 >= passes) else "k_part"
+    wkey = f"layered{n}_{method}_k{k}_c64_{'tc' if tc else 't' + str(choice.get('tile') or 'auto')}"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                "traffic": traffic_from_profile(wkey), "kernel": "k_part",
+                "traffic": traffic_from_profile(wkey), "kernel": kernel,
                 "algorithmic_bytes_per_launch": bytes_per_pass, "launch_ms": round(launch_ms, 4)}
 
     e2e = None
@@ -253,13 +262,13 @@ def run_ours(a):
         host_out = torch.empty(1 << n, dtype=torch.complex64).pin_memory()
         reps = 3
         st.upload(host_in)
-        st.apply(plan)
+        st.apply(plan, tc=tc)
         st.copy_to_host(host_out)
         barrier(ws)
         t0 = time.perf_counter()
         for _ in range(reps):
             st.upload(host_in)
-            st.apply(plan)
+            st.apply(plan, tc=tc)
             st.copy_to_host(host_out)       # synchronises the stream
         dt = (time.perf_counter() - t0) / reps
         dt = max_over_ranks(ws, dt, dev)
@@ -287,13 +296,16 @@ def run_ours(a):
     if rank == 0 and ws == 1 and not a.no_cpu:
         pog, P = plan.export()
         cpu = cpu_baseline_oracle(n, gates, pog, P, max_parts=64, budget_s=20.0)
+        cpu["sample"] += f" ({method} k={k} plan)"
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
                 "warmup": max(a.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 arithmetic)", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_qubits": n, "gates": len(gates), "method": a.method,
-                           "k": k, "passes": passes, "phases": stats["phases"], "ops": stats["ops"],
+                "config": {"workload": WORKLOAD, "n_qubits": n, "gates": len(gates), "method": method,
+                           "k": k, "tensor_core_dense_parts": stats["dense"], "passes": passes,
+                           "phases": stats["phases"], "ops": stats["ops"],
+                           "autotune_trials": choice.get("trials", []),
                            "state_bytes": st.nbytes, "parallelism": f"replicas x{ws}",
                            "l2": "state (2 GiB) larger than L2 (129 MB); no flush needed"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

@@ -37,7 +37,7 @@ typedef enum {
     SV_ERR_OOM = 2,        /* device or host allocation failed */
     SV_ERR_CUDA = 3,       /* a CUDA call failed (launch, copy, fault surfaced at a sync) */
     SV_ERR_PARTITION = 4,  /* a gate has more qubits than the part limit k (Sec. IV-A, L <= L_m) */
-    SV_ERR_TIMEOUT = 5,    /* a bounded device wait gave up (batched persistent kernel) */
+    SV_ERR_TIMEOUT = 5,    /* a bounded device wait gave up (batched / tensor-core kernels) */
     SV_ERR_BUSY = 6,       /* the handle has work that must complete first */
     SV_ERR_INTERNAL = 7
 } sv_status;
@@ -151,6 +151,53 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags);
  * and the norm sum_x |a_x|^2 accumulated in FP64 into *norm_out (host, may be
  * NULL). Synchronises the stream when norm_out is not NULL. */
 sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *norm_out);
+
+/* ---------------------------------------------------------------- batch ---
+ * Many small, independent circuits run in ONE persistent kernel launch that a
+ * CUDA graph captures once and replays (the batched workload: thousands of
+ * uneven circuits of 10..30 qubits). States are complex64, contiguous in one
+ * device buffer in circuit order (circuit i starts after the 2^n_j amplitudes
+ * of every j < i). Each plan's parts run on 2^10-amplitude tiles, one warp
+ * per tile; parts of one circuit run in order (a device work list in wave
+ * order with per-circuit tile counters and bounded waits), parts of different
+ * circuits overlap. Parts are limited to 10 qubits (plans with k <= 10).
+ *
+ * sv_batch_create  n_qubits[n_circuits] in [10, 30]; states start in |0...0>;
+ *                  stream NULL = a stream the library creates (graph capture
+ *                  needs a non-legacy stream). Allocates the states.
+ * sv_batch_set_plan  plan for circuit i (qubit count must match); the plan
+ *                  must stay alive until the next sv_batch_run has returned.
+ * sv_batch_config  warps per CTA (1..8) and tiles per work item (1..4096);
+ *                  0 keeps the default (8, 16). Changing plans or the
+ *                  configuration rebuilds the work list and the graph.
+ * sv_batch_run     apply every circuit once to its current state; the first
+ *                  run builds the work list, uploads it and captures the
+ *                  graph (host work), later runs replay it. Stream-ordered;
+ *                  SV_FLAG_SYNC waits and reports SV_ERR_TIMEOUT if a bounded
+ *                  device wait gave up.
+ * sv_batch_reset   every state back to |0...0> (stream-ordered).
+ * sv_batch_probs   p[x] = |a_x|^2 of all states into dev_out (floats,
+ *                  concatenated like the states; may be NULL) and each
+ *                  state's norm (FP64 accumulation) into norms_host[n] (may
+ *                  be NULL; synchronises when not NULL).
+ * sv_batch_state   device address and byte size of circuit i's state.
+ * sv_batch_copy_state  copy circuit i's state (bytes = its size) to host
+ *                  memory; synchronises.
+ * sv_batch_info    total amplitudes, work items and parts of the built program.
+ * sv_batch_sync    synchronise and report device errors.
+ * sv_batch_destroy free everything the batch allocated. */
+typedef struct sv_batch sv_batch;
+sv_status sv_batch_create(uint32_t n_circuits, const int *n_qubits, void *stream, sv_batch **out);
+sv_status sv_batch_set_plan(sv_batch *b, uint32_t i, sv_plan *p);
+sv_status sv_batch_config(sv_batch *b, int warps_per_cta, int tiles_per_item);
+sv_status sv_batch_run(sv_batch *b, uint32_t flags);
+sv_status sv_batch_reset(sv_batch *b);
+sv_status sv_batch_probs(sv_batch *b, void *dev_out, double *norms_host);
+sv_status sv_batch_state(sv_batch *b, uint32_t i, void **dev_ptr, size_t *bytes);
+sv_status sv_batch_copy_state(sv_batch *b, uint32_t i, void *host_dst, size_t bytes);
+sv_status sv_batch_info(sv_batch *b, uint64_t *total_amplitudes, uint32_t *n_items, uint32_t *n_parts);
+sv_status sv_batch_sync(sv_batch *b);
+sv_status sv_batch_destroy(sv_batch *b);
 
 /* ------------------------------------------------- allocation-free probs ---
  * sv_probs_noalloc: the same probabilities and FP64-accumulated norm as

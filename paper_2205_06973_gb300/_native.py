@@ -65,6 +65,17 @@ _SIGS = {
     "sv_apply_parts": ([_vp, _vp, ctypes.c_uint32], ctypes.c_int),
     "sv_measure_probs": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "sv_probs_noalloc": ([_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "sv_batch_create": ([ctypes.c_uint32, _vp, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+    "sv_batch_set_plan": ([_vp, ctypes.c_uint32, _vp], ctypes.c_int),
+    "sv_batch_config": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "sv_batch_run": ([_vp, ctypes.c_uint32], ctypes.c_int),
+    "sv_batch_reset": ([_vp], ctypes.c_int),
+    "sv_batch_probs": ([_vp, _vp, _vp], ctypes.c_int),
+    "sv_batch_state": ([_vp, ctypes.c_uint32, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "sv_batch_copy_state": ([_vp, ctypes.c_uint32, _vp, ctypes.c_size_t], ctypes.c_int),
+    "sv_batch_info": ([_vp, ctypes.POINTER(ctypes.c_uint64), _u32p, _u32p], ctypes.c_int),
+    "sv_batch_sync": ([_vp], ctypes.c_int),
+    "sv_batch_destroy": ([_vp], ctypes.c_int),
     "sv_last_error": ([], ctypes.c_char_p),
     "sv_version": ([], ctypes.c_char_p),
 }

@@ -1,0 +1,160 @@
+"""Autotuner: picks the part limit k and the launch shape by measuring them.
+
+* ``tune_state`` times candidate (method, k, tensor-core dense path, tile)
+  configurations of one circuit on one state with CUDA events and returns
+  the fastest.
+* ``tune_batch`` times candidate (k, warps per CTA, tiles per work item)
+  configurations of the batched persistent launch on a sample of the
+  circuits.
+
+Results are cached in a JSON file (``$HISVSIM_TUNE_CACHE``, default
+``~/.cache/hisvsim/autotune.json``) keyed by a workload key and the
+precision, so a later run reuses the choice without measuring.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import torch
+
+CACHE = os.environ.get("HISVSIM_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "hisvsim",
+                                                            "autotune.json"))
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key, value):
+    d = _load()
+    d[key] = value
+    try:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + f".{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE)
+    except OSError:
+        pass
+
+
+def cached(key):
+    return _load().get(key)
+
+
+def cached_k(workload, method, precision):
+    v = cached(f"state:{workload}:{precision}")
+    if v and v.get("method") == method:
+        return v.get("k")
+    return None
+
+
+def _time_apply(st, plan, tc, reps):
+    st.apply(plan, sync=True, tc=tc)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st.stream)
+    for _ in range(reps):
+        st.apply(plan, tc=tc)
+    e1.record(st.stream)
+    e1.synchronize()
+    st.sync()
+    return e0.elapsed_time(e1) / reps
+
+
+STATE_CANDIDATES = (
+    ("dagp", 6, True, 0), ("dagp", 5, True, 0), ("dfs", 6, True, 0), ("dagp", 8, True, 0),
+    ("dagp", 10, False, 0), ("dagp", 12, False, 0), ("dagp", 8, False, 0),
+)
+
+
+def tune_state(workload, n, gates, precision="c64", candidates=STATE_CANDIDATES, reps=1, state=None,
+               use_cache=True, log=None):
+    """Fastest (method, k, tc, tile) for this circuit; tc is ignored for
+    complex128. Returns a dict with the choice and every measurement."""
+    from . import api
+    key = f"state:{workload}:{precision}"
+    if use_cache and cached(key):
+        return cached(key)
+    own = state is None
+    st = state if state is not None else api.State(n, precision)
+    trials = []
+    for method, k, tc, tile in candidates:
+        if precision == "c128" and tc:
+            continue
+        if k > n:
+            continue
+        t0 = time.perf_counter()
+        plan = api.Plan(gates, n, method, k)
+        plan_s = time.perf_counter() - t0
+        try:
+            if tile:
+                from . import _native as N
+                N.check(N.lib.sv_set_tile(st.h, tile))
+            ms = _time_apply(st, plan, tc, reps)
+            stats = plan.stats(precision, tile, tc=tc)
+        except Exception as e:   # a configuration the library rejects (tile too small)
+            if log:
+                log(f"tune: skip {method} k={k} tc={tc} tile={tile}: {e}")
+            plan.close()
+            continue
+        finally:
+            if tile:
+                from . import _native as N
+                N.lib.sv_set_tile(st.h, 0)
+        trials.append({"method": method, "k": k, "tc": tc, "tile": tile, "ms": round(ms, 3),
+                       "passes": stats["passes"], "plan_s": round(plan_s, 3)})
+        plan.close()
+    if own:
+        st.close()
+    if not trials:
+        raise RuntimeError("no candidate configuration ran")
+    best = min(trials, key=lambda r: r["ms"])
+    out = dict(best)
+    out["trials"] = trials
+    _store(key, out)
+    return out
+
+
+BATCH_CANDIDATES = tuple((k, w, c) for k in (9, 10) for w in (4, 8) for c in (2, 4, 8))
+
+
+def tune_batch(workload, circuits, method="dfs", candidates=BATCH_CANDIDATES, sample=512, use_cache=True):
+    """Fastest (k, warps per CTA, tiles per item) of the batched launch on the
+    first ``sample`` circuits."""
+    from .batch import Batch
+    key = f"batch:{workload}:c64"
+    if use_cache and cached(key):
+        return cached(key)
+    sub = circuits[:sample]
+    trials = []
+    by_k = {}
+    for k, w, c in candidates:
+        if k not in by_k:
+            by_k[k] = Batch(sub, method=method, k=k)
+        b = by_k[k]
+        b.configure(w, c)
+        b.run(sync=True)   # builds and captures
+        b.reset()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        b.run()
+        e1.record(b.stream)
+        e1.synchronize()
+        b.sync()
+        trials.append({"k": k, "warps": w, "chunk": c, "ms": round(e0.elapsed_time(e1), 3)})
+    for b in by_k.values():
+        b.close()
+    best = min(trials, key=lambda r: r["ms"])
+    out = dict(best)
+    out["method"] = method
+    out["trials"] = trials
+    _store(key, out)
+    return out

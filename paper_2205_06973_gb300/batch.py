@@ -1,0 +1,90 @@
+"""Batched persistent launch over many small circuits (sv_batch_* of the C ABI).
+
+All states live in one device buffer that the library allocates; ``Batch``
+wraps the handle, keeps the plans alive and returns per-circuit
+probabilities as views of one concatenated device tensor.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as N
+from .api import Plan
+
+
+class Batch:
+    def __init__(self, circuits, method="dfs", k=10, warps_per_cta=0, tiles_per_item=0, stream=None,
+                 plans=None):
+        """circuits: list of (n_qubits, gates); or plans: list of built Plan
+        objects (the batch then owns them)."""
+        if plans is not None:
+            circuits = [(p.n, None) for p in plans]
+        self.n = len(circuits)
+        self.nq = np.array([c[0] for c in circuits], dtype=np.int32)
+        self.offsets = np.concatenate([[0], np.cumsum(1 << self.nq.astype(np.int64))])
+        self.total = int(self.offsets[-1])
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = ctypes.c_void_p()
+        N.check(N.lib.sv_batch_create(self.n, self.nq.ctypes.data, ctypes.c_void_p(self.stream.cuda_stream),
+                                      ctypes.byref(h)))
+        self.h = h
+        self.plans = plans if plans is not None else [Plan(g, n, method, min(k, n)) for n, g in circuits]
+        for i, p in enumerate(self.plans):
+            N.check(N.lib.sv_batch_set_plan(self.h, i, p.h))
+        if warps_per_cta or tiles_per_item:
+            N.check(N.lib.sv_batch_config(self.h, warps_per_cta, tiles_per_item))
+
+    @classmethod
+    def from_plans(cls, items, stream=None, warps_per_cta=0, tiles_per_item=0):
+        """items: list of (n_qubits, Plan)."""
+        return cls(None, plans=[p for _, p in items], stream=stream, warps_per_cta=warps_per_cta,
+                   tiles_per_item=tiles_per_item)
+
+    def configure(self, warps_per_cta=0, tiles_per_item=0):
+        N.check(N.lib.sv_batch_config(self.h, warps_per_cta, tiles_per_item))
+
+    def run(self, sync=False):
+        N.check(N.lib.sv_batch_run(self.h, N.SV_FLAG_SYNC if sync else 0))
+
+    def reset(self):
+        N.check(N.lib.sv_batch_reset(self.h))
+
+    def sync(self):
+        N.check(N.lib.sv_batch_sync(self.h))
+
+    def probs(self, out=None, norms=True):
+        """Probabilities of all states (one float32 device tensor, concatenated)
+        and the per-circuit norms (numpy, FP64 accumulation) if requested."""
+        if out is None:
+            out = torch.empty(self.total, dtype=torch.float32, device="cuda")
+        nrm = np.zeros(self.n, dtype=np.float64) if norms else None
+        N.check(N.lib.sv_batch_probs(self.h, ctypes.c_void_p(out.data_ptr()),
+                                     nrm.ctypes.data if norms else None))
+        return out, nrm
+
+    def state_host(self, i):
+        """Circuit i's amplitudes copied to host memory (synchronises)."""
+        host = torch.empty(1 << int(self.nq[i]), dtype=torch.complex64)
+        N.check(N.lib.sv_batch_copy_state(self.h, i, ctypes.c_void_p(host.data_ptr()), host.numel() * 8))
+        return host
+
+    def info(self):
+        t, it, pa = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
+        N.check(N.lib.sv_batch_info(self.h, ctypes.byref(t), ctypes.byref(it), ctypes.byref(pa)))
+        return {"amplitudes": t.value, "items": it.value, "parts": pa.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            N.lib.sv_batch_destroy(self.h)
+            self.h = None
+        for p in getattr(self, "plans", []):
+            p.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/hisvsim.h"
+#include "abi_internal.hpp"
 #include "dense.hpp"
 #include "kernels.hpp"
 #include "partition.hpp"
@@ -38,41 +39,6 @@ constexpr int kProbBlocks = 152 * 8;
 namespace hisv {
 void set_last_error(const std::string &msg) { g_err = msg; }
 }
-
-struct DevProgram {
-    int dev = -1;
-    Phase *d_phases = nullptr;
-    Op *d_ops = nullptr;
-    void *d_coefs = nullptr;
-    uint8_t *d_aimg = nullptr;      // A images of the dense parts
-};
-
-struct sv_state {
-    int n = 0;
-    sv_precision prec = SV_C64;
-    void *buf = nullptr;
-    size_t bytes = 0;
-    bool owns = false;
-    cudaStream_t stream = nullptr;
-    int tile = 0;
-    int dev = 0;
-    double *d_partials = nullptr;   // kProbBlocks + 1 doubles; the last holds the norm
-    double *h_norm = nullptr;       // pinned
-    int *d_err = nullptr;           // device error word of bounded waits (0 = none)
-};
-
-struct sv_plan {
-    int n = 0;
-    sv_method method = SV_PART_NONE;
-    int k = 0;
-    std::vector<GateRef> gates;
-    std::vector<uint32_t> pog;
-    uint32_t n_parts = 0;
-    int max_part = 0;                                                      // qubits of the largest part
-    std::map<std::tuple<bool, int, int>, std::unique_ptr<Program>> host_progs;   // (fp64, t, dense)
-    std::map<std::tuple<int, bool, int, int>, DevProgram> dev_progs;             // (dev, fp64, t, dense)
-    std::vector<std::vector<double>> mats;                                 // gatewise matrices
-};
 
 static size_t amp_bytes(sv_precision p) { return p == SV_C128 ? 16 : 8; }
 static bool is_fp64(const sv_state *s) { return s->prec == SV_C128; }
@@ -310,6 +276,7 @@ sv_status sv_plan_destroy(sv_plan *p) {
         cudaFree(kv.second.d_ops);
         cudaFree(kv.second.d_coefs);
         cudaFree(kv.second.d_aimg);
+        cudaFree(kv.second.d_dnorm);
     }
     cudaSetDevice(cur);
     delete p;
@@ -321,6 +288,7 @@ static void free_dev(DevProgram &d) {
     cudaFree(d.d_ops);
     cudaFree(d.d_coefs);
     cudaFree(d.d_aimg);
+    cudaFree(d.d_dnorm);
 }
 
 static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, int dense, const Program **hp,
@@ -341,6 +309,7 @@ static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, int dense, cons
         if (e == cudaSuccess) e = cudaMalloc(&d.d_ops, sizeof(Op) * nop);
         if (e == cudaSuccess) e = cudaMalloc(&d.d_coefs, rsz * ncf);
         if (e == cudaSuccess) e = cudaMalloc(&d.d_aimg, nim);
+        if (e == cudaSuccess) e = cudaMalloc(&d.d_dnorm, sizeof(double) * (prog.dense.size() + 1));
         if (e != cudaSuccess) {
             cudaGetLastError();
             free_dev(d);
@@ -404,6 +373,8 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
         const DevProgram *dp = nullptr;
         st = get_dev_program(s, p, t, dense_mode(flags, fp64), &hp, &dp);
         if (st != SV_OK) return st;
+        if (!hp->dense.empty())
+            CUDA_TRY(cudaMemsetAsync(dp->d_dnorm, 0, sizeof(double) * (hp->dense.size() + 1), s->stream));
         for (size_t i = 0; i < hp->kind.size(); i++) {
             const uint32_t j = hp->index[i];
             cudaError_t e;
@@ -412,7 +383,7 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
                                 hp->n_tiles[j], s->stream);
             else
                 e = launch_dense6(s->buf, hp->dense[j], dp->d_aimg + (size_t)j * DENSE_A_BYTES, hp->dense_tiles[j],
-                                  s->d_err, s->stream);
+                                  s->d_err, dp->d_dnorm, j, s->stream);
             if (e != cudaSuccess) return fail(SV_ERR_CUDA, std::string("part launch: ") + cudaGetErrorString(e));
         }
     }

@@ -1,0 +1,59 @@
+// Internal definitions of the C-ABI handles, shared by abi.cpp and batch_abi.cpp.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/hisvsim.h"
+#include "partition.hpp"
+#include "planner.hpp"
+
+using hisv::GateRef;
+using hisv::Op;
+using hisv::Phase;
+using hisv::Program;
+
+namespace hisv {
+void set_last_error(const std::string &msg);
+}
+
+struct DevProgram {
+    int dev = -1;
+    Phase *d_phases = nullptr;
+    Op *d_ops = nullptr;
+    void *d_coefs = nullptr;
+    uint8_t *d_aimg = nullptr;      // A images of the dense parts
+    double *d_dnorm = nullptr;      // norm accumulators of the dense passes (1 + dense parts)
+};
+
+struct sv_state {
+    int n = 0;
+    sv_precision prec = SV_C64;
+    void *buf = nullptr;
+    size_t bytes = 0;
+    bool owns = false;
+    cudaStream_t stream = nullptr;
+    int tile = 0;
+    int dev = 0;
+    double *d_partials = nullptr;   // kProbBlocks + 1 doubles; the last holds the norm
+    double *h_norm = nullptr;       // pinned
+    int *d_err = nullptr;           // device error word of bounded waits (0 = none)
+};
+
+struct sv_plan {
+    int n = 0;
+    sv_method method = SV_PART_NONE;
+    int k = 0;
+    std::vector<GateRef> gates;
+    std::vector<uint32_t> pog;
+    uint32_t n_parts = 0;
+    int max_part = 0;                                                      // qubits of the largest part
+    std::map<std::tuple<bool, int, int>, std::unique_ptr<Program>> host_progs;   // (fp64, t, dense)
+    std::map<std::tuple<int, bool, int, int>, DevProgram> dev_progs;             // (dev, fp64, t, dense)
+    std::vector<std::vector<double>> mats;                                 // gatewise matrices
+};
+

@@ -1,0 +1,321 @@
+// C ABI of the batched persistent launch (sv_batch_*; declared in include/hisvsim.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "abi_internal.hpp"
+#include "batch.hpp"
+
+using namespace hisv;
+
+namespace {
+sv_status bfail(sv_status st, const std::string &msg) {
+    set_last_error(msg);
+    return st;
+}
+#define BCUDA(call)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return bfail(SV_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+}  // namespace
+
+struct sv_batch {
+    uint32_t n = 0;                      // circuits
+    std::vector<int> nq;                 // qubits per circuit
+    std::vector<uint64_t> off;           // first amplitude per circuit
+    uint64_t total = 0;                  // amplitudes in all states
+    std::vector<sv_plan *> plans;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int warps = 8;                       // warps per CTA
+    int chunk = 16;                      // tiles per queue item
+    // device
+    float2 *sv = nullptr;
+    uint64_t *d_off = nullptr;
+    uint32_t *d_nq = nullptr;
+    uint32_t *d_done = nullptr;          // n counters + 1 queue ticket
+    int *d_err = nullptr;
+    double *d_norms = nullptr;
+    std::vector<double> h_norms;
+    // compiled program (rebuilt when plans or the configuration change)
+    bool built = false;
+    BatchLaunch launch{};
+    void *d_prog = nullptr;              // one allocation: items, parts, phases, ops, coefs
+    uint32_t n_items = 0, n_parts = 0;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+};
+
+static void drop_program(sv_batch *b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    cudaFree(b->d_prog);
+    b->d_prog = nullptr;
+    b->built = false;
+}
+
+extern "C" {
+
+sv_status sv_batch_create(uint32_t n_circuits, const int *n_qubits, void *stream, sv_batch **out) {
+    if (!out) return bfail(SV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_circuits == 0 || !n_qubits) return bfail(SV_ERR_ARG, "need at least one circuit");
+    std::unique_ptr<sv_batch> b(new sv_batch());
+    b->n = n_circuits;
+    b->nq.assign(n_qubits, n_qubits + n_circuits);
+    b->off.resize(n_circuits);
+    for (uint32_t i = 0; i < n_circuits; i++) {
+        if (b->nq[i] < BATCH_TILE_QUBITS || b->nq[i] > 30)
+            return bfail(SV_ERR_ARG, "batched circuits need 10..30 qubits (circuit " + std::to_string(i) + ")");
+        b->off[i] = b->total;
+        b->total += 1ull << b->nq[i];
+    }
+    b->plans.assign(n_circuits, nullptr);
+    b->h_norms.assign(n_circuits, 0.0);
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    if (!b->stream) {   // graph capture needs a non-legacy stream
+        BCUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
+    }
+    cudaError_t e = cudaMalloc(&b->sv, sizeof(float2) * b->total);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_off, sizeof(uint64_t) * n_circuits);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_nq, sizeof(uint32_t) * n_circuits);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_done, sizeof(uint32_t) * (n_circuits + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_norms, sizeof(double) * n_circuits);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b->sv); cudaFree(b->d_off); cudaFree(b->d_nq); cudaFree(b->d_done); cudaFree(b->d_err);
+        cudaFree(b->d_norms);
+        if (b->own_stream) cudaStreamDestroy(b->stream);
+        return bfail(SV_ERR_OOM, std::string("batch allocation: ") + cudaGetErrorString(e));
+    }
+    std::vector<uint32_t> nq32(b->nq.begin(), b->nq.end());
+    BCUDA(cudaMemcpyAsync(b->d_off, b->off.data(), sizeof(uint64_t) * n_circuits, cudaMemcpyHostToDevice, b->stream));
+    BCUDA(cudaMemcpyAsync(b->d_nq, nq32.data(), sizeof(uint32_t) * n_circuits, cudaMemcpyHostToDevice, b->stream));
+    BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+    BCUDA(launch_batch_reset(b->sv, b->d_off, n_circuits, b->total, b->stream));
+    BCUDA(cudaStreamSynchronize(b->stream));   // the host vectors above go out of scope
+    *out = b.release();
+    return SV_OK;
+}
+
+sv_status sv_batch_set_plan(sv_batch *b, uint32_t i, sv_plan *p) {
+    if (!b || !p) return bfail(SV_ERR_ARG, "NULL argument");
+    if (i >= b->n) return bfail(SV_ERR_ARG, "circuit index out of range");
+    if (p->n != b->nq[i]) return bfail(SV_ERR_ARG, "plan qubit count differs from circuit " + std::to_string(i));
+    if (p->method == SV_PART_NONE) return bfail(SV_ERR_ARG, "batched circuits need a partitioned plan");
+    if (p->max_part > BATCH_TILE_QUBITS) return bfail(SV_ERR_PARTITION, "batched parts are limited to 10 qubits (k <= 10)");
+    b->plans[i] = p;
+    drop_program(b);
+    return SV_OK;
+}
+
+sv_status sv_batch_config(sv_batch *b, int warps_per_cta, int tiles_per_item) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    if (warps_per_cta < 0 || warps_per_cta > 8 || tiles_per_item < 0 || tiles_per_item > 4096)
+        return bfail(SV_ERR_ARG, "warps_per_cta in [1, 8], tiles_per_item in [1, 4096] (0 = default)");
+    b->warps = warps_per_cta ? warps_per_cta : 8;
+    b->chunk = tiles_per_item ? tiles_per_item : 16;
+    drop_program(b);
+    return SV_OK;
+}
+
+static sv_status build_program(sv_batch *b) {
+    std::vector<PartLaunch> parts;
+    std::vector<Phase> phases;
+    std::vector<Op> ops;
+    std::vector<float> coefs;
+    std::vector<uint32_t> part_base(b->n), n_parts(b->n);
+    uint32_t maxP = 0;
+    for (uint32_t c = 0; c < b->n; c++) {
+        sv_plan *p = b->plans[c];
+        if (!p) return bfail(SV_ERR_ARG, "circuit " + std::to_string(c) + " has no plan");
+        Program prog;
+        std::string err;
+        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, false, BATCH_TILE_QUBITS, 5, 0, prog, err))
+            return bfail(SV_ERR_PARTITION, err);
+        const uint32_t ph0 = (uint32_t)phases.size(), op0 = (uint32_t)ops.size(), cf0 = (uint32_t)coefs.size();
+        part_base[c] = (uint32_t)parts.size();
+        n_parts[c] = (uint32_t)prog.parts.size();
+        maxP = std::max(maxP, n_parts[c]);
+        for (PartLaunch L : prog.parts) {
+            L.phase_begin += ph0;
+            L.op_begin += op0;
+            L.op_end += op0;
+            L.coef_begin += cf0;
+            L.coef_end += cf0;
+            parts.push_back(L);
+        }
+        for (Phase ph : prog.phases) {
+            ph.op_begin += op0;
+            phases.push_back(ph);
+        }
+        for (Op op : prog.ops) {
+            op.coef += cf0;
+            ops.push_back(op);
+        }
+        for (double v : prog.coefs) coefs.push_back((float)v);
+    }
+    std::vector<BatchItem> items;
+    for (uint32_t w = 0; w < maxP; w++)
+        for (uint32_t c = 0; c < b->n; c++) {
+            if (w >= n_parts[c]) continue;
+            const uint32_t nt = 1u << (b->nq[c] - BATCH_TILE_QUBITS);
+            for (uint32_t t0 = 0; t0 < nt; t0 += (uint32_t)b->chunk) {
+                BatchItem it;
+                it.circuit = c;
+                it.part = part_base[c] + w;
+                it.tile_begin = t0;
+                it.tile_count = std::min<uint32_t>((uint32_t)b->chunk, nt - t0);
+                it.wait = w * nt;
+                items.push_back(it);
+            }
+        }
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t s_items = al(items.size() * sizeof(BatchItem)), s_parts = al(parts.size() * sizeof(PartLaunch));
+    const size_t s_ph = al(phases.size() * sizeof(Phase)), s_op = al(ops.size() * sizeof(Op));
+    const size_t s_cf = al(std::max<size_t>(1, coefs.size()) * sizeof(float));
+    char *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, s_items + s_parts + s_ph + s_op + s_cf);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(SV_ERR_OOM, std::string("batch program: ") + cudaGetErrorString(e));
+    }
+    b->d_prog = d;
+    std::vector<char> host(s_items + s_parts + s_ph + s_op + s_cf, 0);
+    std::memcpy(host.data(), items.data(), items.size() * sizeof(BatchItem));
+    std::memcpy(host.data() + s_items, parts.data(), parts.size() * sizeof(PartLaunch));
+    std::memcpy(host.data() + s_items + s_parts, phases.data(), phases.size() * sizeof(Phase));
+    std::memcpy(host.data() + s_items + s_parts + s_ph, ops.data(), ops.size() * sizeof(Op));
+    std::memcpy(host.data() + s_items + s_parts + s_ph + s_op, coefs.data(), coefs.size() * sizeof(float));
+    BCUDA(cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice));
+    BatchLaunch &B = b->launch;
+    B.svbase = b->sv;
+    B.items = reinterpret_cast<const BatchItem *>(d);
+    B.n_items = (uint32_t)items.size();
+    B.circ_off = b->d_off;
+    B.parts = reinterpret_cast<const PartLaunch *>(d + s_items);
+    B.phases = reinterpret_cast<const Phase *>(d + s_items + s_parts);
+    B.ops = reinterpret_cast<const Op *>(d + s_items + s_parts + s_ph);
+    B.coefs = reinterpret_cast<const float *>(d + s_items + s_parts + s_ph + s_op);
+    B.done = b->d_done;
+    B.head = b->d_done + b->n;
+    B.err = b->d_err;
+    b->n_items = B.n_items;
+    b->n_parts = (uint32_t)parts.size();
+    int n_ctas = 0;
+    BCUDA(batch_prepare(b->warps, &n_ctas));
+    // one graph: zero the tile counters and the ticket, then the persistent launch
+    BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaMemsetAsync(b->d_done, 0, sizeof(uint32_t) * (b->n + 1), b->stream);
+    if (ce == cudaSuccess) ce = launch_batch(B, b->warps, n_ctas, b->stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(SV_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    b->graph = g;
+    BCUDA(cudaGraphInstantiate(&b->gexec, g, 0));
+    b->built = true;
+    return SV_OK;
+}
+
+static sv_status batch_check(sv_batch *b) {
+    int h = 0;
+    BCUDA(cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BCUDA(cudaStreamSynchronize(b->stream));
+    if (h) {
+        BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+        return bfail(SV_ERR_TIMEOUT, "a bounded wait of the batched kernel gave up");
+    }
+    return SV_OK;
+}
+
+sv_status sv_batch_run(sv_batch *b, uint32_t flags) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    if (!b->built) {
+        sv_status st = build_program(b);
+        if (st != SV_OK) {
+            drop_program(b);
+            return st;
+        }
+    }
+    BCUDA(cudaGraphLaunch(b->gexec, b->stream));
+    if (flags & SV_FLAG_SYNC) return batch_check(b);
+    return SV_OK;
+}
+
+sv_status sv_batch_sync(sv_batch *b) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    return batch_check(b);
+}
+
+sv_status sv_batch_reset(sv_batch *b) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    BCUDA(launch_batch_reset(b->sv, b->d_off, b->n, b->total, b->stream));
+    return SV_OK;
+}
+
+sv_status sv_batch_probs(sv_batch *b, void *dev_out, double *norms_host) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    BCUDA(launch_batch_probs(b->sv, b->d_off, b->d_nq, b->n, reinterpret_cast<float *>(dev_out), b->d_norms,
+                             b->stream));
+    if (norms_host) {
+        BCUDA(cudaMemcpyAsync(b->h_norms.data(), b->d_norms, sizeof(double) * b->n, cudaMemcpyDeviceToHost,
+                              b->stream));
+        BCUDA(cudaStreamSynchronize(b->stream));
+        std::memcpy(norms_host, b->h_norms.data(), sizeof(double) * b->n);
+    }
+    return SV_OK;
+}
+
+sv_status sv_batch_state(sv_batch *b, uint32_t i, void **dev_ptr, size_t *bytes) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    if (i >= b->n) return bfail(SV_ERR_ARG, "circuit index out of range");
+    if (dev_ptr) *dev_ptr = b->sv + b->off[i];
+    if (bytes) *bytes = sizeof(float2) << b->nq[i];
+    return SV_OK;
+}
+
+sv_status sv_batch_copy_state(sv_batch *b, uint32_t i, void *host_dst, size_t bytes) {
+    if (!b || !host_dst) return bfail(SV_ERR_ARG, "NULL argument");
+    if (i >= b->n) return bfail(SV_ERR_ARG, "circuit index out of range");
+    if (bytes != (sizeof(float2) << b->nq[i])) return bfail(SV_ERR_ARG, "bytes must equal the state size");
+    BCUDA(cudaMemcpyAsync(host_dst, b->sv + b->off[i], bytes, cudaMemcpyDeviceToHost, b->stream));
+    return batch_check(b);
+}
+
+sv_status sv_batch_info(sv_batch *b, uint64_t *total_amplitudes, uint32_t *n_items, uint32_t *n_parts) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    if (total_amplitudes) *total_amplitudes = b->total;
+    if (n_items) *n_items = b->n_items;
+    if (n_parts) *n_parts = b->n_parts;
+    return SV_OK;
+}
+
+sv_status sv_batch_destroy(sv_batch *b) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    drop_program(b);
+    cudaFree(b->sv);
+    cudaFree(b->d_off);
+    cudaFree(b->d_nq);
+    cudaFree(b->d_done);
+    cudaFree(b->d_err);
+    cudaFree(b->d_norms);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    if (e != cudaSuccess) return bfail(SV_ERR_CUDA, std::string("pending batch work failed: ") + cudaGetErrorString(e));
+    return SV_OK;
+}
+
+}  // extern "C"

@@ -172,7 +172,7 @@ __device__ __forceinline__ uint64_t deposit_tile(uint64_t v, uint64_t mask) {
 
 __global__ void __launch_bounds__(DENSE_THREADS, 1)
 k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const uint8_t *__restrict__ a_img,
-         uint64_t n_tiles, int *__restrict__ err) {
+         uint64_t n_tiles, int *__restrict__ err, double *__restrict__ dn, uint32_t dense_idx) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *const base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *const sA = base;
@@ -239,6 +239,7 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
 #pragma unroll
         for (int b = 0; b < 4; b++) g_hi[b] = 1ull << L.slot_q[8 + b];
         uint32_t i = 0;
+        double in_norm = 0.0;     // sum of |a|^2 of the input (first dense pass of an apply)
         for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
             const uint32_t s = i & (NSTAGE - 1);
             if (i >= NSTAGE && !mbar_wait(&empty[s], ((i >> 2) - 1) & 1, WAIT_LIMIT)) {
@@ -269,6 +270,7 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
                     asm volatile("prefetch.global.L2 [%0];\n" ::"l"(sv + g));
                 }
             }
+            float tile_in = 0.0f;   // FP32 partial of this tile, folded into the FP64 sum below
             {
                 uint8_t *const sB = sB0 + s * STAGE_BYTES;
 #pragma unroll
@@ -288,6 +290,7 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
                         }
                     }
                     const float2 v = x[j];
+                    tile_in = fmaf(v.x, v.x, fmaf(v.y, v.y, tile_in));
                     const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi = __float2bfloat16_rn(v.y);
                     const __nv_bfloat16 lr = __float2bfloat16_rn(v.x - __bfloat162float(hr));
                     const __nv_bfloat16 li = __float2bfloat16_rn(v.y - __bfloat162float(hi));
@@ -302,6 +305,12 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
                 proxy_fence_smem();
                 mbar_arrive(&full[s]);
             }
+            if (dense_idx == 0) in_norm += (double)tile_in;
+        }
+        if (dense_idx == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) in_norm += __shfl_xor_sync(0xffffffffu, in_norm, o);
+            if (lane == 0) atomicAdd(dn, in_norm);
         }
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------ MMA issuer
@@ -345,6 +354,14 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
                 pb++;
             }
         const uint32_t pm = stage_phys(Lm);
+        // unitarity: rescale to the input norm N0 measured by the first dense
+        // pass, correcting the drift measured on the previous dense pass
+        float scale = 1.0f;
+        if (dense_idx > 0) {
+            const double n0 = dn[0], prev = dn[dense_idx];
+            if (n0 > 0.0 && prev > 0.0) scale = (float)sqrt(n0 / prev);
+        }
+        double out_norm = 0.0;
         // copy-out layout: tile element L = tid (slots 0..7) | j << 8 (slots 8..11)
         uint64_t g_t = 0;
         for (int s = 0; s < 8; s++)
@@ -368,7 +385,13 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
             proxy_fence_smem();
             float *const st = reinterpret_cast<float *>(sB0 + s * STAGE_BYTES);
 #pragma unroll
-            for (int k = 0; k < 32; k++) st[2 * (pm ^ colL[32 * half + k]) + c_out] = v[k];
+            float tile_out = 0.0f;
+            for (int k = 0; k < 32; k++) {
+                const float y = v[k] * scale;
+                tile_out = fmaf(y, y, tile_out);
+                st[2 * (pm ^ colL[32 * half + k]) + c_out] = y;
+            }
+            out_norm += (double)tile_out;
             asm volatile("bar.sync 1, %0;\n" ::"n"(EPI_THREADS) : "memory");
             const uint64_t tb = deposit_tile(tile, L.outer_mask) | g_t;
             const float2 *const st2 = reinterpret_cast<const float2 *>(st);
@@ -382,6 +405,9 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
             }
             mbar_arrive(&empty[s]);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) out_norm += __shfl_xor_sync(0xffffffffu, out_norm, o);
+        if (lane == 0) atomicAdd(dn + 1 + dense_idx, out_norm);
     }
     __syncthreads();
     if (warp == MMA_WARP) {
@@ -424,7 +450,7 @@ void dense_a_image(const double *U, std::vector<uint8_t> &img) {
 }
 
 cudaError_t launch_dense6(void *sv, const DenseLaunch &L, const void *a_img, uint64_t n_tiles, int *d_err,
-                          cudaStream_t st) {
+                          double *d_norms, uint32_t dense_idx, cudaStream_t st) {
     static uint64_t attr_set = 0;
     static int sms[64];
     int dev = 0;
@@ -443,7 +469,7 @@ cudaError_t launch_dense6(void *sv, const DenseLaunch &L, const void *a_img, uin
     if (grid < 1) grid = 1;
     k_dense6<<<(unsigned)grid, DENSE_THREADS, DENSE_SMEM, st>>>(reinterpret_cast<float2 *>(sv), L,
                                                                  reinterpret_cast<const uint8_t *>(a_img), n_tiles,
-                                                                 d_err);
+                                                                 d_err, d_norms, dense_idx);
     return cudaGetLastError();
 }
 

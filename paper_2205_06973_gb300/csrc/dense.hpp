@@ -30,8 +30,12 @@ struct DenseLaunch {
 // K-major with the 128-byte swizzle the tensor-core descriptors expect.
 void dense_a_image(const double *U, std::vector<uint8_t> &img);
 
-// Whether the tensor-core kernel can run: compute capability 10.3 device.
-cudaError_t launch_dense6(void *sv, const DenseLaunch &L, const void *a_img, uint64_t n_tiles,
-                          int *d_err, cudaStream_t st);
+// One dense pass. d_norms: FP64 accumulators of one apply, zeroed before its
+// first dense pass: [0] = input sum |a|^2 (summed by dense pass 0), [1 + j] =
+// output sum of dense pass j. Pass j > 0 rescales its output by
+// sqrt([0] / [j]) (the exact evolution is unitary), which removes the norm
+// drift of the split-BF16 tensor-core arithmetic.
+cudaError_t launch_dense6(void *sv, const DenseLaunch &L, const void *a_img, uint64_t n_tiles, int *d_err,
+                          double *d_norms, uint32_t dense_idx, cudaStream_t st);
 
 }  // namespace hisv

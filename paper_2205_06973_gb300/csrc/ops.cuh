@@ -1,0 +1,287 @@
+// Register-level operations of the part interpreter (shared by the part
+// kernel and the batched warp-level kernel).
+//
+// A thread holds 2^R amplitudes a[0..2^R) of its tile; register bit b of the
+// index i is one tile slot (qubit). Every op acts on compile-time register
+// bits (with_bit turns a runtime bit into a template argument), so the
+// amplitudes stay in registers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "program.hpp"
+
+namespace hisv {
+
+template <typename Real> struct CT;
+template <> struct CT<float> { typedef float2 T; };
+template <> struct CT<double> { typedef double2 T; };
+
+// ------------------------------------------------------------------------
+// register-bit operations; B, A are compile-time register bits
+// ------------------------------------------------------------------------
+// Hadamard without its 1/sqrt2: the planner folds the factor into the part's
+// store factor, so each H costs one add and one subtract per amplitude pair.
+template <int NR, int B, typename C>
+__device__ __forceinline__ void op_h(C (&a)[NR]) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        a[i].x = x.x + y.x; a[i].y = x.y + y.y;
+        a[j].x = x.x - y.x; a[j].y = x.y - y.y;
+    }
+}
+
+template <int NR, int B, typename C, typename Real>
+__device__ __forceinline__ void op_u2(C (&a)[NR], const Real *m) {
+    const Real m00r = m[0], m00i = m[1], m01r = m[2], m01i = m[3];
+    const Real m10r = m[4], m10i = m[5], m11r = m[6], m11i = m[7];
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        a[i].x = m00r * x.x - m00i * x.y + m01r * y.x - m01i * y.y;
+        a[i].y = m00r * x.y + m00i * x.x + m01r * y.y + m01i * y.x;
+        a[j].x = m10r * x.x - m10i * x.y + m11r * y.x - m11i * y.y;
+        a[j].y = m10r * x.y + m10i * x.x + m11r * y.y + m11i * y.x;
+    }
+}
+
+template <int NR, int B, typename C, typename Real>
+__device__ __forceinline__ void op_rx(C (&a)[NR], Real c, Real s) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        a[i].x = c * x.x + s * y.y; a[i].y = c * x.y - s * y.x;
+        a[j].x = s * x.y + c * y.x; a[j].y = c * y.y - s * x.x;
+    }
+}
+
+template <int NR, int B, typename C, typename Real>
+__device__ __forceinline__ void op_ry(C (&a)[NR], Real c, Real s) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        a[i].x = c * x.x - s * y.x; a[i].y = c * x.y - s * y.y;
+        a[j].x = s * x.x + c * y.x; a[j].y = s * x.y + c * y.y;
+    }
+}
+
+template <int NR, int B, typename C>
+__device__ __forceinline__ void op_x(C (&a)[NR]) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i];
+        a[i] = a[j];
+        a[j] = x;
+    }
+}
+
+template <int NR, int B, typename C>
+__device__ __forceinline__ void op_y(C (&a)[NR]) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        a[i].x = y.y; a[i].y = -y.x;
+        a[j].x = -x.y; a[j].y = x.x;
+    }
+}
+
+template <typename C, typename Real>
+__device__ __forceinline__ void cmul_in(C &v, Real dr, Real di) {
+    const Real x = v.x, y = v.y;
+    v.x = x * dr - y * di;
+    v.y = x * di + y * dr;
+}
+
+template <int NR, int B, typename C, typename Real>
+__device__ __forceinline__ void op_d(C (&a)[NR], Real d0r, Real d0i, Real d1r, Real d1i) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) cmul_in(a[i], d1r, d1i);
+        else cmul_in(a[i], d0r, d0i);
+    }
+}
+
+template <int NR, int B, typename C, typename Real>
+__device__ __forceinline__ void op_p(C (&a)[NR], Real dr, Real di) {
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+        if (i & (1 << B)) cmul_in(a[i], dr, di);
+}
+
+template <int NR, int B, typename C>
+__device__ __forceinline__ void op_z(C (&a)[NR]) {
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+        if (i & (1 << B)) { a[i].x = -a[i].x; a[i].y = -a[i].y; }
+}
+
+template <int NR, int A, int B, typename C>
+__device__ __forceinline__ void op_cx(C (&a)[NR]) {   // A control, B target
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (!(i & (1 << A)) || (i & (1 << B))) continue;
+        const int j = i | (1 << B);
+        const C x = a[i];
+        a[i] = a[j];
+        a[j] = x;
+    }
+}
+
+template <int NR, int A, int B, typename C, typename Real>
+__device__ __forceinline__ void op_cp(C (&a)[NR], Real dr, Real di) {
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+        if ((i & (1 << A)) && (i & (1 << B))) cmul_in(a[i], dr, di);
+}
+
+template <int NR, int A, int B, typename C>
+__device__ __forceinline__ void op_cz(C (&a)[NR]) {
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+        if ((i & (1 << A)) && (i & (1 << B))) { a[i].x = -a[i].x; a[i].y = -a[i].y; }
+}
+
+// Call f(integral_constant<int, b>) for a runtime register bit b < R.
+template <int R, int B = 0, typename F>
+__device__ __forceinline__ void with_bit(int b, F &&f) {
+    if constexpr (B < R) {
+        if (b == B) f(std::integral_constant<int, B>());
+        else with_bit<R, B + 1>(b, static_cast<F &&>(f));
+    }
+}
+
+// Swizzled shared-memory index contribution of tile slot p. The swizzle XORs
+// the slot bits above the bank group into the low bits (linear over GF(2)),
+// so a warp whose lane bits sit on slots of distinct residues touches
+// distinct banks: 8-byte elements use 4-bit groups, 16-byte elements 3-bit.
+template <typename Real>
+__device__ __forceinline__ uint32_t swz(int p) {
+    if constexpr (sizeof(Real) == 4) return p < 4 ? (1u << p) : ((1u << p) | (1u << (p & 3)));
+    else return p < 3 ? (1u << p) : ((1u << p) | (1u << (p % 3)));
+}
+
+
+// Run a phase's ops on the thread's amplitudes. ops/cf_base: the op records
+// and the coefficient array their coef indices refer to; (tpr, tpi): the
+// per-thread phase of diagonal gates on thread bits.
+template <typename Real, int R>
+__device__ __forceinline__ void run_ops(typename CT<Real>::T (&a)[1 << R], const Op *__restrict__ opsp, uint32_t count,
+                                        const Real *__restrict__ coefs, int tid, Real &tpr, Real &tpi) {
+    constexpr int NR = 1 << R;
+    for (uint32_t o = 0; o < count; o++) {
+        const Op op = opsp[o];
+        const Real *cf = coefs + op.coef;
+        switch (op.kind) {
+        case OP_H:
+            with_bit<R>(op.a, [&](auto bc) { op_h<NR, decltype(bc)::value>(a); });
+            break;
+        case OP_U2:
+            with_bit<R>(op.a, [&](auto bc) { op_u2<NR, decltype(bc)::value>(a, cf); });
+            break;
+        case OP_RX: {
+            const Real c = cf[0], s = cf[1];
+            with_bit<R>(op.a, [&](auto bc) { op_rx<NR, decltype(bc)::value>(a, c, s); });
+        } break;
+        case OP_RY: {
+            const Real c = cf[0], s = cf[1];
+            with_bit<R>(op.a, [&](auto bc) { op_ry<NR, decltype(bc)::value>(a, c, s); });
+        } break;
+        case OP_X:
+            with_bit<R>(op.a, [&](auto bc) { op_x<NR, decltype(bc)::value>(a); });
+            break;
+        case OP_Y:
+            with_bit<R>(op.a, [&](auto bc) { op_y<NR, decltype(bc)::value>(a); });
+            break;
+        case OP_D: {
+            const Real d0r = cf[0], d0i = cf[1], d1r = cf[2], d1i = cf[3];
+            with_bit<R>(op.a, [&](auto bc) { op_d<NR, decltype(bc)::value>(a, d0r, d0i, d1r, d1i); });
+        } break;
+        case OP_P: {
+            const Real dr = cf[0], di = cf[1];
+            with_bit<R>(op.a, [&](auto bc) { op_p<NR, decltype(bc)::value>(a, dr, di); });
+        } break;
+        case OP_Z:
+            with_bit<R>(op.a, [&](auto bc) { op_z<NR, decltype(bc)::value>(a); });
+            break;
+        case OP_CX:
+            with_bit<R>(op.a, [&](auto ac) {
+                with_bit<R>(op.b, [&](auto bc) {
+                    constexpr int A = decltype(ac)::value, B = decltype(bc)::value;
+                    if constexpr (A != B) op_cx<NR, A, B>(a);
+                });
+            });
+            break;
+        case OP_CP: {
+            const Real dr = cf[0], di = cf[1];
+            with_bit<R>(op.a, [&](auto ac) {
+                with_bit<R>(op.b, [&](auto bc) {
+                    constexpr int A = decltype(ac)::value, B = decltype(bc)::value;
+                    if constexpr (A != B) op_cp<NR, A, B>(a, dr, di);
+                });
+            });
+        } break;
+        case OP_CZ:
+            with_bit<R>(op.a, [&](auto ac) {
+                with_bit<R>(op.b, [&](auto bc) {
+                    constexpr int A = decltype(ac)::value, B = decltype(bc)::value;
+                    if constexpr (A != B) op_cz<NR, A, B>(a);
+                });
+            });
+            break;
+        case OP_CXT:
+            if ((tid >> op.tb) & 1)
+                with_bit<R>(op.b, [&](auto bc) { op_x<NR, decltype(bc)::value>(a); });
+            break;
+        case OP_CPT:
+            if ((tid >> op.tb) & 1) {
+                const Real dr = cf[0], di = cf[1];
+                with_bit<R>(op.a, [&](auto bc) { op_p<NR, decltype(bc)::value>(a, dr, di); });
+            }
+            break;
+        case OP_CZT:
+            if ((tid >> op.tb) & 1)
+                with_bit<R>(op.a, [&](auto bc) { op_z<NR, decltype(bc)::value>(a); });
+            break;
+        case OP_TD: {
+            const int bit = (tid >> op.tb) & 1;
+            const Real dr = bit ? cf[2] : cf[0], di = bit ? cf[3] : cf[1];
+            const Real x = tpr, y = tpi;
+            tpr = x * dr - y * di;
+            tpi = x * di + y * dr;
+        } break;
+        case OP_TP2:
+            if (((tid >> op.tb) & 1) && ((tid >> op.b) & 1)) {
+                const Real dr = cf[0], di = cf[1];
+                const Real x = tpr, y = tpi;
+                tpr = x * dr - y * di;
+                tpi = x * di + y * dr;
+            }
+            break;
+        case OP_TAPPLY:
+#pragma unroll
+            for (int i = 0; i < NR; i++) cmul_in(a[i], tpr, tpi);
+            tpr = Real(1);
+            tpi = Real(0);
+            break;
+        default:
+            break;
+        }
+    }
+}
+
+}  // namespace hisv

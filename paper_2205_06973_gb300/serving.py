@@ -1,0 +1,199 @@
+"""Serving loop with continuous batching over the C ABI.
+
+Requests (a circuit on n qubits and an arrival time) are admitted in arrival
+order once their state fits: 8 * 2^n bytes against a device byte budget and
+a free slot. Admitted states stay on the device until their result is taken.
+
+* Small circuits (n <= small_n) are collected into micro-batches: whenever
+  the batched kernel is idle, every admitted small request that has not
+  started runs in one batched persistent launch (sv_batch_*), so requests
+  that arrived while the previous batch was on the GPU join the next one.
+* Large circuits get their own state and CUDA stream and run their part
+  passes (sv_apply_parts) concurrently with the batch and with each other.
+
+A request's result is its probability vector summary: the norm (FP64
+accumulation on the device), the probability of |0...0> and the most likely
+basis state with its probability; the full state can be kept for checks.
+Latency = completion time - arrival time. ``mode="gatewise"`` serves the same
+stream with one plain pass per gate for every request (no batching), the
+comparison the paper's per-gate simulators correspond to.
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import dataclasses
+import time
+
+import numpy as np
+import torch
+
+from . import _native as N
+from .api import Plan, State
+from .batch import Batch
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    n: int
+    gates: list
+    arrival: float
+    family: str = ""
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    n: int
+    arrival: float
+    start: float
+    done: float
+    norm: float
+    p0: float
+    argmax: int
+    pmax: float
+    state: object = None
+
+    @property
+    def latency(self):
+        return self.done - self.arrival
+
+
+def _summary(probs: torch.Tensor):
+    p0 = float(probs[0].item())
+    am = int(torch.argmax(probs).item())
+    return p0, am, float(probs[am].item())
+
+
+class Server:
+    def __init__(self, budget_bytes=170e9, max_slots=4096, small_n=20, batch_max=512, k_small=10,
+                 k_large=6, tc=True, method_small="dfs", method_large="dagp", mode="parts",
+                 keep_states=False, planners=8):
+        self.budget = float(budget_bytes)
+        self.max_slots = max_slots
+        self.small_n = small_n
+        self.batch_max = batch_max
+        self.k_small = k_small
+        self.k_large = k_large
+        self.tc = tc
+        self.method_small = method_small
+        self.method_large = method_large
+        self.mode = mode
+        self.keep = keep_states
+        self.pool = cf.ThreadPoolExecutor(max_workers=planners)
+        self.streams = [torch.cuda.Stream() for _ in range(8)]
+        self.batch_stream = torch.cuda.Stream()
+
+    @staticmethod
+    def state_bytes(n):
+        return 8 * (1 << n)
+
+    def run(self, requests, time_scale=1.0, log=None):
+        """Serve the requests (sorted by arrival); arrival times are replayed
+        on the wall clock scaled by time_scale. Returns (results, stats)."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        pending = collections.deque()
+        small_wait = []                    # admitted small requests not started
+        running_large = []                 # (req, state, plan, event, start)
+        batch_run = None                   # (reqs, batch, event, start)
+        used = 0.0
+        slots = 0
+        results = []
+        i = 0
+        t0 = time.perf_counter()
+        s_i = 0
+        planned = {}
+
+        def now():
+            return (time.perf_counter() - t0) / time_scale
+
+        def plan_future(r, method, k):
+            return self.pool.submit(Plan, r.gates, r.n, method if self.mode == "parts" else "none", min(k, r.n))
+
+        while i < len(reqs) or pending or small_wait or running_large or batch_run:
+            t = now()
+            while i < len(reqs) and reqs[i].arrival <= t:
+                r = reqs[i]
+                pending.append(r)
+                small = r.n <= self.small_n and self.mode == "parts"
+                planned[r.rid] = plan_future(r, self.method_small if small else self.method_large,
+                                             self.k_small if small else self.k_large)
+                i += 1
+            # admission in arrival order
+            while pending:
+                r = pending[0]
+                b = self.state_bytes(r.n)
+                if slots >= self.max_slots or used + b > self.budget:
+                    break
+                pending.popleft()
+                used += b
+                slots += 1
+                if r.n <= self.small_n and self.mode == "parts":
+                    small_wait.append(r)
+                else:
+                    st = State(r.n, "c64", stream=self.streams[s_i % len(self.streams)])
+                    s_i += 1
+                    plan = planned.pop(r.rid).result()
+                    start = now()
+                    st.apply(plan, gatewise=self.mode != "parts", tc=self.tc and self.mode == "parts")
+                    ev = torch.cuda.Event()
+                    ev.record(st.stream)
+                    running_large.append((r, st, plan, ev, start))
+            # the batched kernel takes every waiting small request when idle
+            if batch_run is None and small_wait:
+                take, small_wait = small_wait[: self.batch_max], small_wait[self.batch_max:]
+                plans = [planned.pop(r.rid).result() for r in take]
+                start = now()
+                b = Batch.from_plans([(r.n, p) for r, p in zip(take, plans)], stream=self.batch_stream)
+                b.run()
+                ev = torch.cuda.Event()
+                ev.record(b.stream)
+                batch_run = (take, b, ev, start)
+            # completions
+            still = []
+            for r, st, plan, ev, start in running_large:
+                if ev.query():
+                    st.sync()
+                    probs = torch.empty(1 << r.n, dtype=torch.float32, device="cuda")
+                    with torch.cuda.stream(st.stream):
+                        norm = st.probs(probs)
+                        p0, am, pm = _summary(probs)
+                    res = Result(r.rid, r.n, r.arrival, start, now(), norm, p0, am, pm,
+                                 st.copy_to_host() if self.keep else None)
+                    results.append(res)
+                    st.close()
+                    plan.close()
+                    used -= self.state_bytes(r.n)
+                    slots -= 1
+                else:
+                    still.append((r, st, plan, ev, start))
+            running_large = still
+            if batch_run is not None and batch_run[2].query():
+                take, b, ev, start = batch_run
+                b.sync()
+                probs, norms = b.probs()
+                torch.cuda.current_stream().wait_stream(b.stream)
+                done_t = now()
+                for j, r in enumerate(take):
+                    p = probs[int(b.offsets[j]):int(b.offsets[j + 1])]
+                    p0, am, pm = _summary(p)
+                    results.append(Result(r.rid, r.n, r.arrival, start, done_t, float(norms[j]), p0, am, pm,
+                                          b.state_host(j) if self.keep else None))
+                    used -= self.state_bytes(r.n)
+                    slots -= 1
+                b.close()
+                batch_run = None
+            if not (running_large or batch_run) and i < len(reqs) and not pending and not small_wait:
+                wait = reqs[i].arrival - now()
+                if wait > 0:
+                    time.sleep(min(wait * time_scale, 0.01))
+            elif running_large or batch_run:
+                time.sleep(0.0002)
+        wall = now()
+        lat = np.array([r.latency for r in results]) if results else np.zeros(1)
+        stats = {"requests": len(results), "wall_s": wall, "circuits_per_s": len(results) / max(wall, 1e-9),
+                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                 "mean_s": float(lat.mean()), "mode": self.mode}
+        results.sort(key=lambda r: r.rid)
+        return results, stats

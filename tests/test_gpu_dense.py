@@ -73,3 +73,21 @@ def test_dense_stats_and_mixed_plan():
     ref = sim.run(n, g)
     out = run_gpu(n, g, method="dagp", k=8, tc=True)
     assert max_abs(out, ref) <= 1e-5
+
+
+def test_dense_norm_and_fidelity_deep_circuit():
+    """Many dense passes: the norm stays at its input value (the passes rescale
+    to it, the exact evolution being unitary) and the fidelity against the
+    FP64 oracle stays >= 0.99999."""
+    _, api = native()
+    n = 16
+    _, g = synth.layered_28q(n=n, depth=60)
+    plan = api.Plan(g, n, "dagp", 6)
+    assert plan.stats("c64", tc=True)["dense"] >= 60
+    plan.close()
+    psi = random_state(n, 31)
+    ref = sim.run(n, g, psi)
+    out = run_gpu(n, g, method="dagp", k=6, psi=psi, tc=True)
+    assert abs(float(np.vdot(out, out).real) - 1.0) <= 5e-6
+    assert abs(np.vdot(ref, out)) ** 2 >= 0.99999
+    assert max_abs(out, ref) <= 1e-5

@@ -1,0 +1,72 @@
+"""Serving loop: continuous batching with admission by state bytes. Each
+request's result is the same alone and in the mix (complex64 tolerance), the
+gate-by-gate serving mode gives the same states, and the byte budget bounds
+what is resident."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import sim
+from tests.gpu_util import native
+
+pytestmark = pytest.mark.gpu
+
+
+def _stream(count, seed=5, max_n=22):
+    out = []
+    arr = synth.serving_arrivals(count, duration_s=0.5, seed=seed)
+    i = 0
+    while len(out) < count:
+        n, fam, g = synth.serving_request(i, seed=seed)
+        i += 1
+        if n > max_n:
+            continue
+        out.append((n, fam, g, arr[len(out)]))
+    return out
+
+
+def test_alone_equals_in_the_mix_and_oracle():
+    native()
+    from paper_2205_06973_gb300.serving import Request, Server
+    stream = _stream(24)
+    reqs = [Request(i, n, g, t, fam) for i, (n, fam, g, t) in enumerate(stream)]
+    srv = Server(budget_bytes=64e6, small_n=18, keep_states=True, k_large=6)
+    mix, stats = srv.run(reqs)
+    assert stats["requests"] == len(reqs)
+    for r in mix:
+        assert abs(r.norm - 1.0) < 1e-4
+    for j in (0, 5, 11, 17, 23):
+        r = reqs[j]
+        alone, _ = Server(budget_bytes=64e6, small_n=18, keep_states=True, k_large=6).run(
+            [Request(0, r.n, r.gates, 0.0)])
+        a = alone[0].state.numpy()
+        m = mix[j].state.numpy()
+        assert np.abs(a - m).max() <= 1e-6, j
+        if r.n <= 16:
+            ref = sim.run(r.n, r.gates)
+            assert np.abs(m - ref).max() <= 1e-5, j
+
+
+def test_gatewise_serving_matches():
+    native()
+    from paper_2205_06973_gb300.serving import Request, Server
+    stream = _stream(8, seed=7, max_n=16)
+    reqs = [Request(i, n, g, t) for i, (n, fam, g, t) in enumerate(stream)]
+    a, _ = Server(small_n=18, keep_states=True).run(reqs)
+    b, _ = Server(small_n=18, keep_states=True, mode="gatewise").run(reqs)
+    for x, y in zip(a, b):
+        assert np.abs(x.state.numpy() - y.state.numpy()).max() <= 1e-5
+
+
+def test_budget_limits_residency():
+    native()
+    from paper_2205_06973_gb300.serving import Request, Server
+    # four 20-qubit states of 8 MiB each with a 17 MiB budget: at most two resident
+    g = synth.layered(20, 4, seed=1, two_q=("CX", "CZ"))
+    reqs = [Request(i, 20, g, 0.0) for i in range(4)]
+    res, stats = Server(budget_bytes=17 * 2 ** 20, small_n=18, k_large=6).run(reqs)
+    starts = sorted(r.start for r in res)
+    dones = sorted(r.done for r in res)
+    # the third request can only start after one of the first two finished
+    assert starts[2] >= dones[0] - 1e-6
+    assert stats["requests"] == 4
