@@ -3,27 +3,40 @@
 // A part on 6 qubits is the 64x64 complex matrix U (the product of its
 // gates). With amplitudes stored as interleaved (re, im) floats, the part
 // maps every column x (64 amplitudes that share the other n - 6 bits) to
-// R x, R the 128x128 real block form R[2i+c][2j+d] of U. One CTA tile is
-// 64 columns (the lowest 6 non-part qubits) and the GEMM
-//     D[128 x 64] = R[128 x 128] . X^T      (M = 128, N = 64, K = 128)
-// runs as split BF16: R = R_hi + R_lo, X = X_hi + X_lo, and
-// D = R_hi X_hi + R_hi X_lo + R_lo X_hi with FP32 accumulation in tensor
-// memory (the dropped R_lo X_lo term is below 2^-16 relative).
+// R x, R the 128x128 real block form R[2i+c][2j+d] of U. A CTA tile is 128
+// columns (the lowest 7 non-part qubits); with the tile as the MMA's A
+// operand and R as its B operand the GEMM is
+//     D[128 x 128] = X^T[128 x 128] . R^T      (M = 128 columns, N = 128, K = 128)
+// so D row n (TMEM lane n) holds the 64 output amplitudes of column n. It
+// runs as split BF16: R = R_hi + R_lo, X = X_hi + X_lo and
+// D = X_hi R_hi + X_lo R_hi + X_hi R_lo with FP32 accumulation in tensor
+// memory (the dropped X_lo R_lo term is below 2^-16 relative).
 //
-// Warp-specialised persistent CTA (13 warps), four pipeline stages:
-//  * 8 producer warps gather tiles from HBM (warming L2 two tiles ahead with
-//    prefetches), split them to BF16 and write them K-major with the 128-byte
-//    swizzle into shared stage i%4;
-//  * one thread of the MMA warp issues the 24 MMAs of tile i into TMEM
-//    accumulator i%4 and commits them;
-//  * 8 epilogue warps drain the accumulator (tcgen05.ld; two warps per TMEM
-//    lane quarter, 32 columns each), stage the FP32 tile in the freed shared
-//    stage in address order (XOR-swizzled), and write it back with coalesced
-//    8-byte stores.
-// Stages and accumulators are handed over with mbarriers (full / empty per
-// stage, full / empty per accumulator). Every mbarrier wait is bounded; on
-// expiry the role records an error code and leaves its loop, and the TMEM
-// the CTA holds is freed on exit.
+// Data path: HBM -> registers -> tensor memory -> registers -> HBM. Only the
+// 64 KiB image of R (resident for the whole launch) is read from shared
+// memory, by the MMAs, so the tile crosses the SM's shared-memory datapath
+// only as global loads and stores.
+//
+// Warp-specialised persistent CTA (13 warps, one CTA per SM):
+//  * 8 converter warps (two per TMEM lane quarter): thread (lane n, half h)
+//    loads amplitudes 32h..32h+31 of column n (for a fixed amplitude the
+//    warp's 32 columns are consecutive in memory when the column qubits are
+//    the lowest ones), splits them to BF16 hi/lo, and writes them with
+//    tcgen05.st into the TMEM A buffer of the tile (two buffers). They warm
+//    L2 with the tile two steps ahead (one 128-byte line per lane).
+//  * one thread of the MMA warp issues the 24 MMAs (K = 16 each) of a tile
+//    into one of two TMEM accumulators and commits them to the accumulator's
+//    full barrier (which also frees the tile's A buffer);
+//  * 4 epilogue warps (one per lane quarter) read the accumulator
+//    (tcgen05.ld; lane n = column n, 16 amplitudes at a time), apply the
+//    norm correction and store complete (re, im) amplitudes, coalesced like
+//    the loads.
+// TMEM: accumulators at columns 0 and 128, A buffers at 256 and 384 (hi in
+// the first 64 columns, lo in the next 64): all 512 columns, so the launch
+// asks for enough shared memory to keep a second CTA off the SM. Every
+// mbarrier wait is bounded; on expiry the role records an error code and
+// leaves its loop, the MMA thread waits (bounded) for its last commit, and
+// the TMEM is freed on exit.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -56,9 +69,6 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 }
-__device__ __forceinline__ void proxy_fence_smem() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -73,22 +83,22 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
                  : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
     return ok != 0;
 }
-// D[tmem] (+)= A[smem desc] . B[smem desc]^T, BF16 in, FP32 accumulate.
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                          uint32_t accumulate) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                 ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
-}
-// Plain arrive of this thread on an mbarrier.
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
-}
 // Bounded wait for the phase of the given parity; false if it gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
     for (uint32_t i = 0; i < limit; i++)
         if (mbar_try(bar, parity)) return true;
     return false;
+}
+// Plain arrive of this thread on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+// D[tmem] (+)= A[tmem] . B[smem desc]^T, BF16 in, FP32 accumulate.
+__device__ __forceinline__ void umma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                             uint32_t accumulate) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+                 ::"r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
 }
 // Arrive on the mbarrier once all previously issued MMAs of this thread complete.
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
@@ -96,8 +106,7 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                  ::"r"(smem_u32(bar)) : "memory");
 }
 // 32 consecutive TMEM columns of this thread's lane (32x32b shape).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                  "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                  "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
@@ -107,10 +116,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
                    "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
                    "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                  : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+// 16 consecutive TMEM columns of this thread's lane from registers (32x32b shape).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+                 "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+                   "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+                   "r"(r[15])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
 // Shared-memory matrix descriptor, K-major, 128-byte swizzle: start address,
 // leading byte offset (unused for this layout, 1), stride byte offset 1024
@@ -132,34 +149,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Byte offset of element k (0..63 within a 64-element k-block) of row r in a
-// K-major 128-byte-swizzled block: 16-byte chunk index XOR (row mod 8).
-__device__ __forceinline__ uint32_t sw128_off(uint32_t r, uint32_t k) {
-    return r * 128u + ((((k >> 3) ^ (r & 7u)) & 7u) << 4) + ((k & 7u) << 1);
-}
-
-}  // namespace
-
-
-
-constexpr int EPI_WARPS = 8;     // two per TMEM lane quarter (warp w: quarter w % 4, column half w / 4)
-constexpr int PROD_WARPS = 8;
-constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
-constexpr int DENSE_THREADS = (MMA_WARP + 1) * 32;
-constexpr int PROD_THREADS = PROD_WARPS * 32;
-constexpr int EPI_THREADS = EPI_WARPS * 32;
-constexpr int NSTAGE = 4;
-constexpr int STAGE_BYTES = 32768;    // B_hi, B_lo x 2 k-blocks x 64 rows x 128 B; or the FP32 output tile
-constexpr int KBLK_BYTES = 8192;      // 64 rows x 128 B
-constexpr uint32_t DENSE_SMEM = 65536 + NSTAGE * STAGE_BYTES + 1024 + 512 + 256;
-constexpr uint32_t DENSE_TMEM_COLS = 256;                         // four 64-column FP32 accumulators
-constexpr uint32_t WAIT_LIMIT = 1u << 24;                         // bounded mbarrier polls
-
-// swizzled word index of tile element L (12 bits, address order over the
-// tile's slots): the high nibbles are folded into the low one
-__device__ __forceinline__ uint32_t stage_phys(uint32_t L) { return L ^ (((L >> 4) ^ (L >> 8)) & 15u); }
-
-__device__ __forceinline__ uint64_t deposit_tile(uint64_t v, uint64_t mask) {
+// v deposited into the set bits of mask (v's bit j -> mask's j-th set bit).
+__device__ __forceinline__ uint64_t deposit_bits(uint64_t v, uint64_t mask) {
     uint64_t out = 0;
     while (mask) {
         const uint64_t low = mask & (~mask + 1);
@@ -169,143 +160,134 @@ __device__ __forceinline__ uint64_t deposit_tile(uint64_t v, uint64_t mask) {
     }
     return out;
 }
+// x + y over the bit positions of mask (x, y with bits only inside mask): the
+// carries run through the positions outside mask, which are set to one.
+__device__ __forceinline__ uint64_t masked_add(uint64_t x, uint64_t y, uint64_t mask) {
+    return ((x | ~mask) + y) & mask;
+}
+
+}  // namespace
+
+constexpr int EPI_WARPS = 4;      // one per TMEM lane quarter (warp w: quarter w)
+constexpr int CONV_WARPS = 8;     // two per TMEM lane quarter (warp 4 + w: quarter w % 4, half w / 4)
+constexpr int MMA_WARP = EPI_WARPS + CONV_WARPS;
+constexpr int DENSE_THREADS = (MMA_WARP + 1) * 32;
+constexpr int CONV_THREADS = CONV_WARPS * 32;
+constexpr int EPI_THREADS = EPI_WARPS * 32;
+constexpr uint32_t TMEM_COLS = 512;                  // D0, D1, A0, A1 at 0, 128, 256, 384
+// R image + barriers; sized above half of the SM's shared memory so that a
+// second CTA (which would wait for the TMEM this one holds) cannot share the SM
+constexpr uint32_t DENSE_SMEM = 120 * 1024;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;            // bounded mbarrier polls
+static_assert(DENSE_A_BYTES + 1024 + 16 * CONV_THREADS + 1024 <= (int)DENSE_SMEM, "shared memory layout");
 
 __global__ void __launch_bounds__(DENSE_THREADS, 1)
 k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const uint8_t *__restrict__ a_img,
          uint64_t n_tiles, int *__restrict__ err, double *__restrict__ dn, uint32_t dense_idx) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *const base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *const sA = base;
-    uint8_t *const sB0 = base + 65536;
-    uint32_t *const colL = reinterpret_cast<uint32_t *>(base + 65536 + NSTAGE * STAGE_BYTES);   // 64 entries
-    uint64_t *const bars = reinterpret_cast<uint64_t *>(base + 65536 + NSTAGE * STAGE_BYTES + 256);
-    uint32_t *const tslot = reinterpret_cast<uint32_t *>(base + 65536 + NSTAGE * STAGE_BYTES + 256 + 16 * 8);
-    uint64_t *const full = bars, *const empty = bars + NSTAGE, *const accfull = bars + 2 * NSTAGE,
-                    *const accempty = bars + 3 * NSTAGE;
+    uint8_t *const sR = base;                                               // R image (B operand)
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(base + DENSE_A_BYTES);
+    uint64_t *const afull = bars, *const dfull = bars + 2, *const dempty = bars + 4;
+    uint32_t *const tslot = reinterpret_cast<uint32_t *>(base + DENSE_A_BYTES + 128);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (int i = tid; i < DENSE_A_BYTES / 16; i += DENSE_THREADS)
-        reinterpret_cast<uint4 *>(sA)[i] = reinterpret_cast<const uint4 *>(a_img)[i];
-    if (tid < 64) {   // swizzled staging index of column n (its bits deposited into the column slots)
-        uint32_t l = 0;
-        for (int s = 0, cb = 0; s < 12; s++)
-            if (!((L.slot_part >> s) & 1)) {
-                if ((tid >> cb) & 1) l |= 1u << s;
-                cb++;
-            }
-        colL[tid] = stage_phys(l);
-    }
+        reinterpret_cast<uint4 *>(sR)[i] = reinterpret_cast<const uint4 *>(a_img)[i];
     if (tid == 0) {
-        for (int s = 0; s < NSTAGE; s++) {
-            mbar_init(&full[s], PROD_THREADS);
-            mbar_init(&empty[s], EPI_THREADS);
-            mbar_init(&accfull[s], 1);
-            mbar_init(&accempty[s], EPI_THREADS);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&afull[b], CONV_THREADS);
+            mbar_init(&dfull[b], 1);
+            mbar_init(&dempty[b], EPI_THREADS);
         }
         mbar_init_fence();
     }
     if (warp == MMA_WARP) {
-        tmem_alloc(tslot, DENSE_TMEM_COLS);
+        tmem_alloc(tslot, TMEM_COLS);
         tmem_relinquish();
     }
-    proxy_fence_smem();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // R image visible to the MMAs
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (warp >= EPI_WARPS && warp < MMA_WARP) {
-        // ------------------------------------------------------ producers
-        // tile element L = ptid (slots 0..7) | j << 8 (slots 8..11), j < 16
-        const int ptid = tid - EPI_WARPS * 32;
-        uint64_t g_t = 0;
-        uint32_t l_t = 0, n_t = 0;
-        int pl0 = 0;
-        {
-            int pl = 0, cl = 0;
-            for (int s = 0; s < 12; s++) {
-                const bool part = (L.slot_part >> s) & 1;
-                if (s < 8 && ((ptid >> s) & 1)) {
-                    g_t |= 1ull << L.slot_q[s];
-                    if (part) l_t |= 1u << pl;
-                    else n_t |= 1u << cl;
-                }
-                if (part) pl++;
-                else cl++;
-                if (s == 7) pl0 = pl;
-            }
-        }
-        uint64_t g_hi[4];
+    // per-thread geometry shared by converters and epilogue: TMEM lane
+    // quarter q and amplitude half h of the warp; column n = 32 q + lane
+    const int q = warp & 3, h = warp >= EPI_WARPS ? ((warp - EPI_WARPS) >> 2) & 1 : 0;
+    const uint32_t n_col = 32 * q + lane;
+    uint64_t coff = 0;                                   // column n's bits on the column qubits
 #pragma unroll
-        for (int b = 0; b < 4; b++) g_hi[b] = 1ull << L.slot_q[8 + b];
+    for (int b = 0; b < DENSE_COLS; b++)
+        if ((n_col >> b) & 1) coff |= 1ull << L.col_q[b];
+    uint64_t pbit[DENSE_K];
+#pragma unroll
+    for (int b = 0; b < DENSE_K; b++) pbit[b] = 1ull << L.part_q[b];
+    const uint64_t hoff = h ? pbit[DENSE_K - 1] : 0ull;  // amplitude bit 5 = the half
+    const uint64_t dgrid = deposit_bits(gridDim.x, L.outer_mask);
+
+    if (warp >= EPI_WARPS && warp < MMA_WARP) {
+        // ------------------------------------------------------ converters
+        // L2 warm-up lines of a tile: qubits 0..3 are tile qubits, so a tile
+        // is 512 lines of 128 bytes, line lam at the deposit of lam into the
+        // tile's qubits above 3
+        const int ctid = tid - EPI_THREADS;
+        const uint64_t all = L.n >= 64 ? ~0ull : ((1ull << L.n) - 1);
+        const uint64_t tile_q = all & ~L.outer_mask & ~0xFull;
+        uint64_t *const lineoff = reinterpret_cast<uint64_t *>(base + DENSE_A_BYTES + 1024) + 2 * ctid;
+#pragma unroll
+        for (int u = 0; u < 2; u++) lineoff[u] = deposit_bits((uint64_t)(ctid + 256 * u), tile_q);
+        double in_norm = 0.0;   // sum of |a|^2 of the input (first dense pass of an apply)
+        uint64_t tb = deposit_bits(blockIdx.x, L.outer_mask);
+        uint64_t tpf = masked_add(tb, masked_add(dgrid, dgrid, L.outer_mask), L.outer_mask);
         uint32_t i = 0;
-        double in_norm = 0.0;     // sum of |a|^2 of the input (first dense pass of an apply)
         for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
-            const uint32_t s = i & (NSTAGE - 1);
-            if (i >= NSTAGE && !mbar_wait(&empty[s], ((i >> 2) - 1) & 1, WAIT_LIMIT)) {
+            const uint32_t b = i & 1;
+            // the MMAs of tile i - 2 (same A buffer) have completed
+            if (i >= 2 && !mbar_wait(&dfull[b], ((i >> 1) - 1) & 1, WAIT_LIMIT)) {
                 atomicExch(err, 1);
                 break;
             }
-            float2 x[16];
-            {
-                const uint64_t tb = deposit_tile(tile, L.outer_mask) | g_t;
-#pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    uint64_t g = tb;
-#pragma unroll
-                    for (int b = 0; b < 4; b++)
-                        if ((j >> b) & 1) g |= g_hi[b];
-                    x[j] = __ldcs(sv + g);
-                }
-            }
-            // warm L2 with the tile two steps ahead (no registers held)
+            tc_fence_after();
             if (tile + 2ull * gridDim.x < n_tiles) {
-                const uint64_t tb = deposit_tile(tile + 2ull * gridDim.x, L.outer_mask) | g_t;
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    uint64_t g = tb;
-#pragma unroll
-                    for (int b = 0; b < 4; b++)
-                        if ((j >> b) & 1) g |= g_hi[b];
-                    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(sv + g));
-                }
+                for (int u = 0; u < 2; u++) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(sv + (tpf | lineoff[u])));
             }
-            float tile_in = 0.0f;   // FP32 partial of this tile, folded into the FP64 sum below
-            {
-                uint8_t *const sB = sB0 + s * STAGE_BYTES;
+            const float2 *const src = sv + (tb | coff | hoff);
+            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + 256 + 128 * b + 32 * h;
+            float tile_in = 0.0f;   // FP32 partial of this tile, folded into the FP64 sum
+#pragma unroll
+            for (int g = 0; g < 2; g++) {   // two rounds of 16 loads (the lines are in L2 by now)
+                float2 x[16];
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
-                    uint32_t l = l_t, nn = n_t;
-                    {
-                        int pl = pl0, cl = 8 - pl0;
+                    const int m = 16 * g + j;
+                    uint64_t o = 0;
 #pragma unroll
-                        for (int b = 0; b < 4; b++) {
-                            const bool part = (L.slot_part >> (8 + b)) & 1;
-                            if ((j >> b) & 1) {
-                                if (part) l |= 1u << pl;
-                                else nn |= 1u << cl;
-                            }
-                            if (part) pl++;
-                            else cl++;
-                        }
-                    }
+                    for (int bb = 0; bb < 5; bb++)
+                        if ((m >> bb) & 1) o |= pbit[bb];
+                    x[j] = __ldcs(src + o);
+                }
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
                     const float2 v = x[j];
                     tile_in = fmaf(v.x, v.x, fmaf(v.y, v.y, tile_in));
-                    const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi = __float2bfloat16_rn(v.y);
-                    const __nv_bfloat16 lr = __float2bfloat16_rn(v.x - __bfloat162float(hr));
-                    const __nv_bfloat16 li = __float2bfloat16_rn(v.y - __bfloat162float(hi));
-                    const uint32_t kb = l >> 5, kin = (2 * l) & 63;
-                    const uint32_t off = sw128_off(nn, kin);
-                    __nv_bfloat162 ph, plo;
-                    ph.x = hr; ph.y = hi;
-                    plo.x = lr; plo.y = li;
-                    *reinterpret_cast<__nv_bfloat162 *>(sB + kb * KBLK_BYTES + off) = ph;
-                    *reinterpret_cast<__nv_bfloat162 *>(sB + (2 + kb) * KBLK_BYTES + off) = plo;
+                    const __nv_bfloat162 bh = __floats2bfloat162_rn(v.x, v.y);
+                    const float2 hf = __bfloat1622float2(bh);
+                    const __nv_bfloat162 bl = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+                    hi[j] = *reinterpret_cast<const uint32_t *>(&bh);
+                    lo[j] = *reinterpret_cast<const uint32_t *>(&bl);
                 }
-                proxy_fence_smem();
-                mbar_arrive(&full[s]);
+                tmem_st16(ta + 16 * g, hi);
+                tmem_st16(ta + 64 + 16 * g, lo);
             }
+            tmem_st_wait();
+            tc_fence_before();
+            mbar_arrive(&afull[b]);
             if (dense_idx == 0) in_norm += (double)tile_in;
+            tb = masked_add(tb, dgrid, L.outer_mask);
+            tpf = masked_add(tpf, dgrid, L.outer_mask);
         }
         if (dense_idx == 0) {
 #pragma unroll
@@ -315,45 +297,37 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(128, 64);
+            const uint32_t idesc = idesc_bf16_f32(128, 128);
+            const uint32_t sb = smem_u32(sR);
             uint32_t i = 0;
             for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
-                const uint32_t s = i & (NSTAGE - 1), u = i >> 2;
-                if (!mbar_wait(&full[s], u & 1, WAIT_LIMIT) ||
-                    (i >= NSTAGE && !mbar_wait(&accempty[s], (u - 1) & 1, WAIT_LIMIT))) {
+                const uint32_t b = i & 1, u = i >> 1;
+                if (!mbar_wait(&afull[b], u & 1, WAIT_LIMIT) ||
+                    (i >= 2 && !mbar_wait(&dempty[b], (u - 1) & 1, WAIT_LIMIT))) {
                     atomicExch(err, 1);
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = smem_u32(sA), sb = smem_u32(sB0 + s * STAGE_BYTES);
-                const uint32_t d = tmem + s * 64;
+                const uint32_t d = tmem + 128 * b, a = tmem + 256 + 128 * b;
                 uint32_t acc = 0;
 #pragma unroll
                 for (int p = 0; p < 3; p++) {
-                    const uint32_t asel = p == 2 ? 1 : 0, bsel = p == 1 ? 1 : 0;
+                    // p = 0: X_hi R_hi, 1: X_lo R_hi, 2: X_hi R_lo
+                    const uint32_t xsel = p == 1 ? 64u : 0u, rsel = p == 2 ? 1u : 0u;
 #pragma unroll
                     for (int ks = 0; ks < 8; ks++) {
-                        const uint32_t aa = sa + (asel * 2 + (ks >> 2)) * 16384 + (ks & 3) * 32;
-                        const uint32_t ba = sb + (bsel * 2 + (ks >> 2)) * KBLK_BYTES + (ks & 3) * 32;
-                        umma_bf16(d, sw128_desc(aa), sw128_desc(ba), idesc, acc);
+                        const uint32_t ra = sb + (rsel * 2 + (ks >> 2)) * 16384 + (ks & 3) * 32;
+                        umma_bf16_ts(d, a + xsel + 8 * ks, sw128_desc(ra), idesc, acc);
                         acc = 1;
                     }
                 }
-                umma_commit(&accfull[s]);   // accumulator ready; the stage's B operand is consumed
+                umma_commit(&dfull[b]);    // accumulator ready, A buffer consumed
             }
+            // the MMAs of the last tile complete before the TMEM is freed
+            if (i > 0 && !mbar_wait(&dfull[(i - 1) & 1], ((i - 1) >> 1) & 1, WAIT_LIMIT)) atomicExch(err, 1);
         }
     } else {
         // ------------------------------------------------------ epilogue
-        const int q = warp & 3, half = warp >> 2;   // TMEM lane quarter, column half
-        const uint32_t r_out = 32 * q + lane;       // output real index 2m + c (TMEM lane)
-        const uint32_t m_out = r_out >> 1, c_out = r_out & 1;
-        uint32_t Lm = 0;                             // tile element of amplitude m_out, column 0
-        for (int s = 0, pb = 0; s < 12; s++)
-            if ((L.slot_part >> s) & 1) {
-                if ((m_out >> pb) & 1) Lm |= 1u << s;
-                pb++;
-            }
-        const uint32_t pm = stage_phys(Lm);
         // unitarity: rescale to the input norm N0 measured by the first dense
         // pass, correcting the drift measured on the previous dense pass
         float scale = 1.0f;
@@ -362,48 +336,41 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
             if (n0 > 0.0 && prev > 0.0) scale = (float)sqrt(n0 / prev);
         }
         double out_norm = 0.0;
-        // copy-out layout: tile element L = tid (slots 0..7) | j << 8 (slots 8..11)
-        uint64_t g_t = 0;
-        for (int s = 0; s < 8; s++)
-            if ((tid >> s) & 1) g_t |= 1ull << L.slot_q[s];
-        uint64_t g_hi[4];
-#pragma unroll
-        for (int b = 0; b < 4; b++) g_hi[b] = 1ull << L.slot_q[8 + b];
+        uint64_t tb = deposit_bits(blockIdx.x, L.outer_mask);
         uint32_t i = 0;
         for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
-            const uint32_t s = i & (NSTAGE - 1), u = i >> 2;
-            if (!mbar_wait(&accfull[s], u & 1, WAIT_LIMIT)) {
+            const uint32_t b = i & 1, u = i >> 1;
+            if (!mbar_wait(&dfull[b], u & 1, WAIT_LIMIT)) {
                 atomicExch(err, 1);
                 break;
             }
             tc_fence_after();
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + s * 64 + 32 * half, v);
-            tc_fence_before();
-            mbar_arrive(&accempty[s]);
-            // FP32 tile into the freed stage, swizzled address order
-            proxy_fence_smem();
-            float *const st = reinterpret_cast<float *>(sB0 + s * STAGE_BYTES);
-#pragma unroll
+            const uint32_t td = tmem + ((uint32_t)(32 * q) << 16) + 128 * b;
+            float2 *const dst = sv + (tb | coff);
             float tile_out = 0.0f;
-            for (int k = 0; k < 32; k++) {
-                const float y = v[k] * scale;
-                tile_out = fmaf(y, y, tile_out);
-                st[2 * (pm ^ colL[32 * half + k]) + c_out] = y;
+#pragma unroll
+            for (int g = 0; g < 4; g++) {   // 16 amplitudes (32 columns) at a time
+                uint32_t r[32];
+                tmem_ld32(td + 32 * g, r);
+                tmem_ld_wait();
+                if (g == 3) {
+                    tc_fence_before();
+                    mbar_arrive(&dempty[b]);
+                }
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int m = 16 * g + j;
+                    uint64_t o = 0;
+#pragma unroll
+                    for (int bb = 0; bb < 6; bb++)
+                        if ((m >> bb) & 1) o |= pbit[bb];
+                    const float2 y = make_float2(__uint_as_float(r[2 * j]) * scale, __uint_as_float(r[2 * j + 1]) * scale);
+                    tile_out = fmaf(y.x, y.x, fmaf(y.y, y.y, tile_out));
+                    __stcs(dst + o, y);
+                }
             }
             out_norm += (double)tile_out;
-            asm volatile("bar.sync 1, %0;\n" ::"n"(EPI_THREADS) : "memory");
-            const uint64_t tb = deposit_tile(tile, L.outer_mask) | g_t;
-            const float2 *const st2 = reinterpret_cast<const float2 *>(st);
-#pragma unroll
-            for (int j = 0; j < 16; j++) {
-                uint64_t g = tb;
-#pragma unroll
-                for (int b = 0; b < 4; b++)
-                    if ((j >> b) & 1) g |= g_hi[b];
-                __stcs(sv + g, st2[stage_phys((uint32_t)tid | ((uint32_t)j << 8))]);
-            }
-            mbar_arrive(&empty[s]);
+            tb = masked_add(tb, dgrid, L.outer_mask);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) out_norm += __shfl_xor_sync(0xffffffffu, out_norm, o);
@@ -412,7 +379,7 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
     __syncthreads();
     if (warp == MMA_WARP) {
         tc_fence_after();
-        tmem_dealloc(tmem, DENSE_TMEM_COLS);
+        tmem_dealloc(tmem, TMEM_COLS);
     }
 }
 

@@ -1,7 +1,7 @@
 // Dense fused-part path: a part acting on 6 qubits is applied as one 64x64
 // complex matrix, i.e. a 128x128 real GEMM on interleaved (re, im) data, on
-// the tcgen05 tensor cores in split BF16 (A_hi B_hi + A_hi B_lo + A_lo B_hi,
-// FP32 accumulation in tensor memory).
+// the tcgen05 tensor cores in split BF16 (X_hi R_hi + X_lo R_hi + X_hi R_lo,
+// FP32 accumulation in tensor memory), 128 state columns per tile.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -11,8 +11,8 @@
 namespace hisv {
 
 constexpr int DENSE_K = 6;                    // qubits of a dense part
-constexpr int DENSE_COLS = 6;                 // column qubits of one tile (64 columns)
-constexpr int DENSE_A_BYTES = 64 * 1024;      // A image: [hi, lo] x [k-block 0, 1] x 128 rows x 128 B
+constexpr int DENSE_COLS = 7;                 // column qubits of one tile (128 columns)
+constexpr int DENSE_A_BYTES = 64 * 1024;      // R image: [hi, lo] x [k-block 0, 1] x 128 rows x 128 B
 
 // Launch record of one dense part (by value).
 struct DenseLaunch {

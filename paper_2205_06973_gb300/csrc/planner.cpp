@@ -194,10 +194,12 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
         uint64_t S = 0;
         for (int g : gl) S |= gmask[g];
         if (dense_mode == 1 && !fp64 && popc(S) <= DENSE_K && n >= DENSE_K + DENSE_COLS) {
-            // dense part: the part's qubits padded with the lowest others to 6,
-            // columns on the lowest 7 remaining qubits
+            // dense part: the part's qubits padded to 6 with the highest others
+            // (the unitary is the identity on them), columns on the lowest 7
+            // remaining qubits, so that the 32 lanes of a warp (columns) stay
+            // consecutive amplitudes unless the part itself holds low qubits
             uint64_t P = S, C = 0;
-            for (int q = 0; q < n && popc(P) < DENSE_K; q++) P |= 1ull << q;
+            for (int q = n - 1; q >= 0 && popc(P) < DENSE_K; q--) P |= 1ull << q;
             for (int q = 0; q < n && popc(C) < DENSE_COLS; q++)
                 if (!((P >> q) & 1)) C |= 1ull << q;
             DenseLaunch D;

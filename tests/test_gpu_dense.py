@@ -17,8 +17,8 @@ def rel_l2(a, b):
 
 
 def test_dense_single_tile_identity_like():
-    """12 qubits = one CTA tile; a part of one H then H again is the identity."""
-    n = 12
+    """13 qubits = one CTA tile; a part of one H then H again is the identity."""
+    n = 13
     g = [("H", (0,), 0.0), ("H", (0,), 0.0)]
     psi = random_state(n, 1)
     out = run_gpu(n, g, method="nat", k=6, psi=psi, tc=True)
