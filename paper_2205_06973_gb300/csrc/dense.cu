@@ -129,6 +129,37 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
+// W consecutive complex64 amplitudes (W = 1, 2, 4: 8, 16, 32 bytes, aligned
+// to their size), streaming (evict-first) load and store.
+template <int W>
+__device__ __forceinline__ void ld_amps(const float2 *p, float2 *x) {
+    if constexpr (W == 1) {
+        x[0] = __ldcs(p);
+    } else if constexpr (W == 2) {
+        const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+        x[0] = make_float2(v.x, v.y);
+        x[1] = make_float2(v.z, v.w);
+    } else {
+        asm volatile("ld.global.cs.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                     : "=f"(x[0].x), "=f"(x[0].y), "=f"(x[1].x), "=f"(x[1].y), "=f"(x[2].x), "=f"(x[2].y),
+                       "=f"(x[3].x), "=f"(x[3].y)
+                     : "l"(p));
+    }
+}
+template <int W>
+__device__ __forceinline__ void st_amps(float2 *p, const float2 *y) {
+    if constexpr (W == 1) {
+        __stcs(p, y[0]);
+    } else if constexpr (W == 2) {
+        __stcs(reinterpret_cast<float4 *>(p), make_float4(y[0].x, y[0].y, y[1].x, y[1].y));
+    } else {
+        asm volatile("st.global.cs.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
+                     ::"l"(p), "f"(y[0].x), "f"(y[0].y), "f"(y[1].x), "f"(y[1].y), "f"(y[2].x), "f"(y[2].y),
+                       "f"(y[3].x), "f"(y[3].y)
+                     : "memory");
+    }
+}
+
 // Shared-memory matrix descriptor, K-major, 128-byte swizzle: start address,
 // leading byte offset (unused for this layout, 1), stride byte offset 1024
 // (between 8-row groups), descriptor version 1, layout type 2 (128B swizzle).
@@ -181,6 +212,7 @@ constexpr uint32_t DENSE_SMEM = 120 * 1024;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;            // bounded mbarrier polls
 static_assert(DENSE_A_BYTES + 1024 + 16 * CONV_THREADS + 1024 <= (int)DENSE_SMEM, "shared memory layout");
 
+template <int W>
 __global__ void __launch_bounds__(DENSE_THREADS, 1)
 k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const uint8_t *__restrict__ a_img,
          uint64_t n_tiles, int *__restrict__ err, double *__restrict__ dn, uint32_t dense_idx) {
@@ -260,13 +292,13 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
             for (int g = 0; g < 2; g++) {   // two rounds of 16 loads (the lines are in L2 by now)
                 float2 x[16];
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    const int m = 16 * g + j;
+                for (int j = 0; j < 16; j += W) {
+                    const int m = 16 * g + j;   // its low log2(W) bits are 0: W consecutive amplitudes
                     uint64_t o = 0;
 #pragma unroll
                     for (int bb = 0; bb < 5; bb++)
                         if ((m >> bb) & 1) o |= pbit[bb];
-                    x[j] = __ldcs(src + o);
+                    ld_amps<W>(src + o, x + j);
                 }
                 uint32_t hi[16], lo[16];
 #pragma unroll
@@ -358,15 +390,20 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
                     mbar_arrive(&dempty[b]);
                 }
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
+                for (int j = 0; j < 16; j += W) {
                     const int m = 16 * g + j;
                     uint64_t o = 0;
 #pragma unroll
                     for (int bb = 0; bb < 6; bb++)
                         if ((m >> bb) & 1) o |= pbit[bb];
-                    const float2 y = make_float2(__uint_as_float(r[2 * j]) * scale, __uint_as_float(r[2 * j + 1]) * scale);
-                    tile_out = fmaf(y.x, y.x, fmaf(y.y, y.y, tile_out));
-                    __stcs(dst + o, y);
+                    float2 y[W];
+#pragma unroll
+                    for (int w = 0; w < W; w++) {
+                        y[w] = make_float2(__uint_as_float(r[2 * (j + w)]) * scale,
+                                           __uint_as_float(r[2 * (j + w) + 1]) * scale);
+                        tile_out = fmaf(y[w].x, y[w].x, fmaf(y[w].y, y[w].y, tile_out));
+                    }
+                    st_amps<W>(dst + o, y);
                 }
             }
             out_norm += (double)tile_out;
@@ -425,18 +462,33 @@ cudaError_t launch_dense6(void *sv, const DenseLaunch &L, const void *a_img, uin
     if (e != cudaSuccess) return e;
     if (dev >= 64) return cudaErrorInvalidDevice;
     if (!((attr_set >> dev) & 1)) {
-        e = cudaFuncSetAttribute(k_dense6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM);
+        e = cudaFuncSetAttribute(k_dense6<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_dense6<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_dense6<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         attr_set |= 1ull << dev;
     }
+    if (reinterpret_cast<uintptr_t>(sv) & 15) return cudaErrorMisalignedAddress;
     uint64_t grid = (uint64_t)sms[dev];
     if (grid > n_tiles) grid = n_tiles;
     if (grid < 1) grid = 1;
-    k_dense6<<<(unsigned)grid, DENSE_THREADS, DENSE_SMEM, st>>>(reinterpret_cast<float2 *>(sv), L,
-                                                                 reinterpret_cast<const uint8_t *>(a_img), n_tiles,
-                                                                 d_err, d_norms, dense_idx);
+    // amplitudes per lane access: the part qubits 0, 1, ... in a row make the
+    // amplitudes of a column consecutive (qubit 0 a column qubit: the lanes are)
+    int z = 0;
+    while (z < DENSE_K && L.part_q[z] == z) z++;
+    const bool a32 = (reinterpret_cast<uintptr_t>(sv) & 31) == 0;
+    float2 *const p = reinterpret_cast<float2 *>(sv);
+    const uint8_t *const a = reinterpret_cast<const uint8_t *>(a_img);
+    if (z >= 2 && a32)
+        k_dense6<4><<<(unsigned)grid, DENSE_THREADS, DENSE_SMEM, st>>>(p, L, a, n_tiles, d_err, d_norms, dense_idx);
+    else if (z >= 1)
+        k_dense6<2><<<(unsigned)grid, DENSE_THREADS, DENSE_SMEM, st>>>(p, L, a, n_tiles, d_err, d_norms, dense_idx);
+    else
+        k_dense6<1><<<(unsigned)grid, DENSE_THREADS, DENSE_SMEM, st>>>(p, L, a, n_tiles, d_err, d_norms, dense_idx);
     return cudaGetLastError();
 }
 
