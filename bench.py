@@ -59,25 +59,33 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {
+    "k_dense6": ("dense.cu", "dense.hpp", "planner.cpp"),
+    "k_part": ("kernels.cu", "ops.cuh", "program.hpp", "planner.cpp"),
+}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
-    for f in ("kernels.cu", "program.hpp", "planner.cpp"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2205_06973_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(workload_key):
-    """DRAM bytes per part-kernel launch from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_part_traffic.txt")
+def traffic_from_profile(kernel, workload_key):
+    """DRAM bytes per launch of the kernel from the committed ncu summary
+    (profiles/traffic.txt), if it was taken on the current kernel source
+    (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    cur = kernel_source_hash()
+    cur = kernel_source_hash(kernel)
     with open(path) as f:
         for line in f:
             parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
-            if parts.get("source") == cur and parts.get("workload") == workload_key:
+            if (parts.get("kernel") == kernel and parts.get("source") == cur
+                    and parts.get("workload") == workload_key):
                 try:
                     return float(parts["bytes_per_launch"])
                 except (KeyError, ValueError):
@@ -252,7 +260,7 @@ def run_ours(a):
     wkey = f"layered{n}_{method}_k{k}_c64_{'tc' if tc else 't' + str(choice.get('tile') or 'auto')}"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                "traffic": traffic_from_profile(wkey), "kernel": kernel,
+                "traffic": traffic_from_profile(kernel, wkey), "kernel": kernel,
                 "algorithmic_bytes_per_launch": bytes_per_pass, "launch_ms": round(launch_ms, 4)}
 
     e2e = None

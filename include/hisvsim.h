@@ -74,8 +74,9 @@ typedef struct sv_plan sv_plan;
 /* Flags of sv_apply_parts. */
 #define SV_FLAG_GATEWISE 0x1u   /* ignore the parts: one plain pass per gate (comparator) */
 #define SV_FLAG_SYNC     0x2u   /* synchronise the stream before returning */
-#define SV_FLAG_TC_DENSE 0x4u   /* complex64: parts of at most 6 qubits run as one fused 64x64
-                                   unitary on the tensor cores (split BF16, FP32 accumulation) */
+#define SV_FLAG_TC_DENSE 0x4u   /* complex64, n >= 13: parts of at most 6 qubits run as one fused
+                                   64x64 unitary on the tensor cores (split BF16, FP32
+                                   accumulation); other parts keep the gate-list kernel */
 
 /* ---------------------------------------------------------------- state ---
  * sv_create: make an n-qubit state (1 <= n <= 36) initialised to |0...0>.
