@@ -206,6 +206,7 @@ struct Units {
     std::vector<int> mg;
     std::vector<std::set<int>> succ, pred;
     std::vector<std::vector<uint64_t>> reach;  // units reachable by >= 1 edge
+    std::vector<int> wprev, wnext;             // [unit * n + q]: neighbouring unit on wire q, or -1
     int next_id = 0;
 
     bool bit(const std::vector<uint64_t> &r, int i) const { return (r[i >> 6] >> (i & 63)) & 1; }
@@ -243,6 +244,27 @@ struct Units {
                     pred[b].insert(a);
                 }
             }
+        // wire order: a unit's gates on a wire are contiguous (the part graph
+        // is acyclic), so units follow each other on every wire
+        const int n = d.n;
+        wprev.assign((size_t)cap * n, -1);
+        wnext.assign((size_t)cap * n, -1);
+        for (int q = 0; q < n; q++) {
+            std::vector<std::pair<int, int>> on;   // (first gate on q, unit)
+            for (int i = 0; i < U; i++) {
+                if (!((qm[i] >> q) & 1)) continue;
+                for (int g : gates[i])
+                    if ((d.qmask[g] >> q) & 1) {
+                        on.push_back({g, i});
+                        break;
+                    }
+            }
+            std::sort(on.begin(), on.end());
+            for (size_t j = 1; j < on.size(); j++) {
+                wnext[(size_t)on[j - 1].second * n + q] = on[j].second;
+                wprev[(size_t)on[j].second * n + q] = on[j - 1].second;
+            }
+        }
         std::vector<int> order = topo();
         for (int i = (int)order.size() - 1; i >= 0; i--) {
             int u = order[i];
@@ -312,6 +334,25 @@ struct Units {
         for (int x : pc) { succ[x].erase(a); succ[x].erase(b); succ[x].insert(c); }
         succ[c] = std::move(sc);
         pred[c] = std::move(pc);
+        const int n = dag->n;
+        for (int q = 0; q < n; q++) {
+            const bool ia = (qm[a] >> q) & 1, ib = (qm[b] >> q) & 1;
+            if (!ia && !ib) continue;
+            int p, nx;
+            if (ia && ib) {   // adjacent on q (no unit between them: no long path)
+                const bool ab = wnext[(size_t)a * n + q] == b;
+                p = wprev[(size_t)(ab ? a : b) * n + q];
+                nx = wnext[(size_t)(ab ? b : a) * n + q];
+            } else {
+                const int u = ia ? a : b;
+                p = wprev[(size_t)u * n + q];
+                nx = wnext[(size_t)u * n + q];
+            }
+            wprev[(size_t)c * n + q] = p;
+            wnext[(size_t)c * n + q] = nx;
+            if (p >= 0) wnext[(size_t)p * n + q] = c;
+            if (nx >= 0) wprev[(size_t)nx * n + q] = c;
+        }
         std::vector<uint64_t> rc(words, 0);
         for (int w = 0; w < words; w++) rc[w] = reach[a][w] | reach[b][w];
         rc[a >> 6] &= ~(1ull << (a & 63));
@@ -319,12 +360,17 @@ struct Units {
         for (int x = 0; x < next_id; x++) {
             if (!alive[x] || x == c) continue;
             std::vector<uint64_t> &r = reach[x];
-            if (bit(r, a) || bit(r, b)) {
-                r[a >> 6] &= ~(1ull << (a & 63));
-                r[b >> 6] &= ~(1ull << (b & 63));
-                r[c >> 6] |= 1ull << (c & 63);
-                for (int w = 0; w < words; w++) r[w] |= rc[w];
+            const bool ra = bit(r, a), rb = bit(r, b);
+            if (!ra && !rb) continue;
+            // x already holds the reach of the side it reached; only the
+            // other side's reach can be new to it
+            if (ra != rb) {
+                const std::vector<uint64_t> &o = ra ? reach[b] : reach[a];
+                for (int w = 0; w < words; w++) r[w] |= o[w];
             }
+            r[a >> 6] &= ~(1ull << (a & 63));
+            r[b >> 6] &= ~(1ull << (b & 63));
+            r[c >> 6] |= 1ull << (c & 63);
         }
         reach[a].clear();
         reach[b].clear();
@@ -333,29 +379,35 @@ struct Units {
     }
 
     // Merge rule: smallest key (-shared, min mg, max mg) among valid pairs.
+    // Two units that share a qubit can only be valid when no unit lies
+    // between them on that wire (else a path of length 2 runs through it,
+    // and it stays there while both live), so the candidates that share
+    // qubits are the wire neighbours: the same merges as over all sharing
+    // pairs, with far fewer heap entries.
     void merge_loop(int k, bool zero_shared) {
         typedef std::tuple<int, int, int, int, int> Key;
         std::priority_queue<Key, std::vector<Key>, std::greater<Key>> heap;
         int n = dag->n;
-        std::vector<std::set<int>> byq(n);
-        for (int u : live())
-            for (int q = 0; q < n; q++)
-                if ((qm[u] >> q) & 1) byq[q].insert(u);
         auto push = [&](int a, int b) {
             if (popc(qm[a] | qm[b]) > k) return;
             int m1 = std::min(mg[a], mg[b]), m2 = std::max(mg[a], mg[b]);
             heap.push(Key(-popc(qm[a] & qm[b]), m1, m2, a, b));
         };
-        auto sharing = [&](int u) {
-            std::set<int> out;
+        auto push_neighbours = [&](int u) {
             for (int q = 0; q < n; q++)
-                if ((qm[u] >> q) & 1) out.insert(byq[q].begin(), byq[q].end());
-            out.erase(u);
-            return out;
+                if ((qm[u] >> q) & 1) {
+                    const int p = wprev[(size_t)u * n + q], nx = wnext[(size_t)u * n + q];
+                    if (p >= 0) push(p, u);
+                    if (nx >= 0) push(u, nx);
+                }
         };
-        for (int u : live())
-            for (int v : sharing(u))
-                if (v > u) push(u, v);
+        for (int u : live()) {
+            for (int q = 0; q < n; q++)
+                if ((qm[u] >> q) & 1) {
+                    const int nx = wnext[(size_t)u * n + q];
+                    if (nx >= 0) push(std::min(u, nx), std::max(u, nx));
+                }
+        }
         bool zero_done = false;
         while (true) {
             if (heap.empty()) {
@@ -373,19 +425,12 @@ struct Units {
             int a = std::get<3>(top), b = std::get<4>(top);
             if (!alive[a] || !alive[b]) continue;
             if (long_path(a, b)) continue;
-            uint64_t m = qm[a] | qm[b];
             int c = merge(a, b);
-            for (int q = 0; q < n; q++)
-                if ((m >> q) & 1) {
-                    byq[q].erase(a);
-                    byq[q].erase(b);
-                    byq[q].insert(c);
-                }
             if (zero_done) {
                 for (int v : live())
                     if (v != c) push(v, c);
             } else {
-                for (int v : sharing(c)) push(v, c);
+                push_neighbours(c);
             }
         }
     }

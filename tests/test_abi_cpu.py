@@ -138,3 +138,21 @@ def test_plan_tile_too_small(native):
     p = _plan(native, g, n, "dagp", 12)
     with pytest.raises(native.SvError):
         p.stats("c128", 11)    # a 12-qubit part cannot fit an 11-qubit tile
+
+
+@pytest.mark.parametrize("k", [4, 6, 10])
+def test_partition_bit_exact_serving_requests(native, k):
+    """Large requests of the serving stream (parameterised, layered and QFT
+    families, 21-22 qubits, ~1500 gates) at the part sizes the server uses."""
+    seen = set()
+    i = 0
+    while len(seen) < 3 and i < 400:
+        n, fam, g = synth.serving_request(i, seed=5)
+        i += 1
+        if n > 22 or n < 21 or fam in seen:
+            continue
+        seen.add(fam)
+        pog, _ = _plan(native, g, n, "dagp", k).export()
+        ref = pt.partition(g, n, "dagp", k)
+        assert list(pog) == ref, (i - 1, fam)
+        pt.check_partition(g, n, k, ref)
