@@ -73,30 +73,28 @@ sv_status sv_create(int n, sv_precision prec, void *dev_buf, size_t dev_buf_byte
     if (dev_buf) {
         s->buf = dev_buf;
     } else {
-        cudaError_t e = cudaMalloc(&s->buf, bytes);
+        cudaError_t e = dev_alloc(&s->buf, bytes, s->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            return fail(SV_ERR_OOM, std::string("cudaMalloc state: ") + cudaGetErrorString(e));
+            return fail(SV_ERR_OOM, std::string("state allocation: ") + cudaGetErrorString(e));
         }
         s->owns = true;
     }
-    cudaError_t e = cudaMalloc(&s->d_partials, sizeof(double) * (kProbBlocks + 1));
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_norm, sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_err, sizeof(int));
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&s->d_partials), sizeof(double) * (kProbBlocks + 1), s->stream);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&s->d_err), sizeof(int), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (s->owns) cudaFree(s->buf);
-        if (s->d_partials) cudaFree(s->d_partials);
-        if (s->h_norm) cudaFreeHost(s->h_norm);
-        if (s->d_err) cudaFree(s->d_err);
+        if (s->owns) dev_free(s->buf, s->stream);
+        dev_free(s->d_partials, s->stream);
+        dev_free(s->d_err, s->stream);
         return fail(SV_ERR_OOM, std::string("scratch allocation: ") + cudaGetErrorString(e));
     }
     e = launch_set_basis(is_fp64(s.get()), s->buf, n, 0, s->stream);
     if (e != cudaSuccess) {
-        if (s->owns) cudaFree(s->buf);
-        cudaFree(s->d_partials);
-        cudaFreeHost(s->h_norm);
+        if (s->owns) dev_free(s->buf, s->stream);
+        dev_free(s->d_partials, s->stream);
+        dev_free(s->d_err, s->stream);
         return fail(SV_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e));
     }
     *out = s.release();
@@ -106,10 +104,10 @@ sv_status sv_create(int n, sv_precision prec, void *dev_buf, size_t dev_buf_byte
 sv_status sv_destroy(sv_state *s) {
     if (!s) return fail(SV_ERR_ARG, "state is NULL");
     cudaError_t e = cudaStreamSynchronize(s->stream);
-    if (s->owns) cudaFree(s->buf);
-    cudaFree(s->d_partials);
-    cudaFreeHost(s->h_norm);
-    cudaFree(s->d_err);
+    if (s->owns) dev_free(s->buf, s->stream);
+    dev_free(s->d_partials, s->stream);
+    dev_free(s->d_err, s->stream);
+    dev_free(s->d_dnorm, s->stream);
     delete s;
     if (e != cudaSuccess) return fail(SV_ERR_CUDA, std::string("pending work failed: ") + cudaGetErrorString(e));
     return SV_OK;
@@ -270,25 +268,23 @@ sv_status sv_plan_destroy(sv_plan *p) {
     if (!p) return fail(SV_ERR_ARG, "plan is NULL");
     int cur = 0;
     cudaGetDevice(&cur);
-    for (auto &kv : p->dev_progs) {
+    for (auto &kv : p->dev_progs) {   // no apply of the plan may be in flight
         cudaSetDevice(kv.second.dev);
-        cudaFree(kv.second.d_phases);
-        cudaFree(kv.second.d_ops);
-        cudaFree(kv.second.d_coefs);
-        cudaFree(kv.second.d_aimg);
-        cudaFree(kv.second.d_dnorm);
+        dev_free(kv.second.d_phases, 0);
+        dev_free(kv.second.d_ops, 0);
+        dev_free(kv.second.d_coefs, 0);
+        dev_free(kv.second.d_aimg, 0);
     }
     cudaSetDevice(cur);
     delete p;
     return SV_OK;
 }
 
-static void free_dev(DevProgram &d) {
-    cudaFree(d.d_phases);
-    cudaFree(d.d_ops);
-    cudaFree(d.d_coefs);
-    cudaFree(d.d_aimg);
-    cudaFree(d.d_dnorm);
+static void free_dev(DevProgram &d, cudaStream_t st) {
+    dev_free(d.d_phases, st);
+    dev_free(d.d_ops, st);
+    dev_free(d.d_coefs, st);
+    dev_free(d.d_aimg, st);
 }
 
 static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, int dense, const Program **hp,
@@ -305,14 +301,14 @@ static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, int dense, cons
         const size_t nph = std::max<size_t>(1, prog.phases.size()), nop = std::max<size_t>(1, prog.ops.size());
         const size_t ncf = std::max<size_t>(1, prog.coefs.size()), nim = std::max<size_t>(16, prog.a_img.size());
         const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
-        cudaError_t e = cudaMalloc(&d.d_phases, sizeof(Phase) * nph);
-        if (e == cudaSuccess) e = cudaMalloc(&d.d_ops, sizeof(Op) * nop);
-        if (e == cudaSuccess) e = cudaMalloc(&d.d_coefs, rsz * ncf);
-        if (e == cudaSuccess) e = cudaMalloc(&d.d_aimg, nim);
-        if (e == cudaSuccess) e = cudaMalloc(&d.d_dnorm, sizeof(double) * (prog.dense.size() + 1));
+        cudaStream_t st = s->stream;
+        cudaError_t e = dev_alloc(reinterpret_cast<void **>(&d.d_phases), sizeof(Phase) * nph, st);
+        if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&d.d_ops), sizeof(Op) * nop, st);
+        if (e == cudaSuccess) e = dev_alloc(&d.d_coefs, rsz * ncf, st);
+        if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&d.d_aimg), nim, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            free_dev(d);
+            free_dev(d, st);
             return fail(SV_ERR_OOM, std::string("program upload: ") + cudaGetErrorString(e));
         }
         std::vector<float> cf32;
@@ -321,12 +317,19 @@ static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, int dense, cons
             cf32.assign(prog.coefs.begin(), prog.coefs.end());
             cf = cf32.data();
         }
-        if (!prog.phases.empty()) e = cudaMemcpy(d.d_phases, prog.phases.data(), sizeof(Phase) * prog.phases.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && !prog.ops.empty()) e = cudaMemcpy(d.d_ops, prog.ops.data(), sizeof(Op) * prog.ops.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && !prog.coefs.empty()) e = cudaMemcpy(d.d_coefs, cf, rsz * prog.coefs.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && !prog.a_img.empty()) e = cudaMemcpy(d.d_aimg, prog.a_img.data(), prog.a_img.size(), cudaMemcpyHostToDevice);
+        if (!prog.phases.empty())
+            e = cudaMemcpyAsync(d.d_phases, prog.phases.data(), sizeof(Phase) * prog.phases.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !prog.ops.empty())
+            e = cudaMemcpyAsync(d.d_ops, prog.ops.data(), sizeof(Op) * prog.ops.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !prog.coefs.empty())
+            e = cudaMemcpyAsync(d.d_coefs, cf, rsz * prog.coefs.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !prog.a_img.empty())
+            e = cudaMemcpyAsync(d.d_aimg, prog.a_img.data(), prog.a_img.size(), cudaMemcpyHostToDevice, st);
+        // the program is shared by every state that applies the plan, on any
+        // stream: it is complete before it is published (cf32 also dies here)
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) {
-            free_dev(d);
+            free_dev(d, st);
             return fail(SV_ERR_CUDA, std::string("program upload: ") + cudaGetErrorString(e));
         }
         it = p->dev_progs.emplace(key, d).first;
@@ -373,8 +376,21 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
         const DevProgram *dp = nullptr;
         st = get_dev_program(s, p, t, dense_mode(flags, fp64), &hp, &dp);
         if (st != SV_OK) return st;
-        if (!hp->dense.empty())
-            CUDA_TRY(cudaMemsetAsync(dp->d_dnorm, 0, sizeof(double) * (hp->dense.size() + 1), s->stream));
+        if (!hp->dense.empty()) {
+            const size_t need = hp->dense.size() + 1;
+            if (s->dnorm_cap < need) {
+                dev_free(s->d_dnorm, s->stream);
+                s->d_dnorm = nullptr;
+                s->dnorm_cap = 0;
+                cudaError_t e = dev_alloc(reinterpret_cast<void **>(&s->d_dnorm), sizeof(double) * need, s->stream);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(SV_ERR_OOM, std::string("norm accumulators: ") + cudaGetErrorString(e));
+                }
+                s->dnorm_cap = need;
+            }
+            CUDA_TRY(cudaMemsetAsync(s->d_dnorm, 0, sizeof(double) * need, s->stream));
+        }
         for (size_t i = 0; i < hp->kind.size(); i++) {
             const uint32_t j = hp->index[i];
             cudaError_t e;
@@ -383,7 +399,7 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
                                 hp->n_tiles[j], s->stream);
             else
                 e = launch_dense6(s->buf, hp->dense[j], dp->d_aimg + (size_t)j * DENSE_A_BYTES, hp->dense_tiles[j],
-                                  s->d_err, dp->d_dnorm, j, s->stream);
+                                  s->d_err, s->d_dnorm, j, s->stream);
             if (e != cudaSuccess) return fail(SV_ERR_CUDA, std::string("part launch: ") + cudaGetErrorString(e));
         }
     }
@@ -400,9 +416,9 @@ sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *nor
     double *d_norm = s->d_partials + kProbBlocks;
     CUDA_TRY(launch_probs(is_fp64(s), s->buf, s->n, dev_out, out_fp64, s->d_partials, kProbBlocks, d_norm, s->stream));
     if (norm_out) {
-        CUDA_TRY(cudaMemcpyAsync(s->h_norm, d_norm, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(&s->h_norm, d_norm, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
         CUDA_TRY(cudaStreamSynchronize(s->stream));
-        *norm_out = *s->h_norm;
+        *norm_out = s->h_norm;
     }
     return SV_OK;
 }

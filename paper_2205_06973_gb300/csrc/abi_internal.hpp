@@ -18,6 +18,14 @@ using hisv::Phase;
 using hisv::Program;
 
 namespace hisv {
+
+// Device allocations of the library are stream-ordered (the device memory
+// pool): allocating or freeing never synchronises the whole device, so
+// states and batches on other streams keep running.
+inline cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st) { return cudaMallocAsync(p, bytes, st); }
+inline void dev_free(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
 void set_last_error(const std::string &msg);
 }
 
@@ -26,8 +34,7 @@ struct DevProgram {
     Phase *d_phases = nullptr;
     Op *d_ops = nullptr;
     void *d_coefs = nullptr;
-    uint8_t *d_aimg = nullptr;      // A images of the dense parts
-    double *d_dnorm = nullptr;      // norm accumulators of the dense passes (1 + dense parts)
+    uint8_t *d_aimg = nullptr;      // R images of the dense parts
 };
 
 struct sv_state {
@@ -40,8 +47,10 @@ struct sv_state {
     int tile = 0;
     int dev = 0;
     double *d_partials = nullptr;   // kProbBlocks + 1 doubles; the last holds the norm
-    double *h_norm = nullptr;       // pinned
+    double h_norm = 0.0;            // norm read back from the device
     int *d_err = nullptr;           // device error word of bounded waits (0 = none)
+    double *d_dnorm = nullptr;      // norm accumulators of one apply's dense passes
+    size_t dnorm_cap = 0;           // (1 + dense parts), grown on demand
 };
 
 struct sv_plan {

@@ -56,7 +56,7 @@ static void drop_program(sv_batch *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     b->gexec = nullptr;
     b->graph = nullptr;
-    cudaFree(b->d_prog);
+    dev_free(b->d_prog, b->stream);   // after the launches already queued on the stream
     b->d_prog = nullptr;
     b->built = false;
 }
@@ -84,16 +84,18 @@ sv_status sv_batch_create(uint32_t n_circuits, const int *n_qubits, void *stream
         BCUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
         b->own_stream = true;
     }
-    cudaError_t e = cudaMalloc(&b->sv, sizeof(float2) * b->total);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_off, sizeof(uint64_t) * n_circuits);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_nq, sizeof(uint32_t) * n_circuits);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_done, sizeof(uint32_t) * (n_circuits + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_norms, sizeof(double) * n_circuits);
+    cudaStream_t st = b->stream;
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&b->sv), sizeof(float2) * b->total, st);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_off), sizeof(uint64_t) * n_circuits, st);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_nq), sizeof(uint32_t) * n_circuits, st);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_done), sizeof(uint32_t) * (n_circuits + 1), st);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_err), sizeof(int), st);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_norms), sizeof(double) * n_circuits, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(b->sv); cudaFree(b->d_off); cudaFree(b->d_nq); cudaFree(b->d_done); cudaFree(b->d_err);
-        cudaFree(b->d_norms);
+        dev_free(b->sv, st); dev_free(b->d_off, st); dev_free(b->d_nq, st); dev_free(b->d_done, st);
+        dev_free(b->d_err, st); dev_free(b->d_norms, st);
+        cudaStreamSynchronize(st);
         if (b->own_stream) cudaStreamDestroy(b->stream);
         return bfail(SV_ERR_OOM, std::string("batch allocation: ") + cudaGetErrorString(e));
     }
@@ -184,7 +186,7 @@ static sv_status build_program(sv_batch *b) {
     const size_t s_ph = al(phases.size() * sizeof(Phase)), s_op = al(ops.size() * sizeof(Op));
     const size_t s_cf = al(std::max<size_t>(1, coefs.size()) * sizeof(float));
     char *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, s_items + s_parts + s_ph + s_op + s_cf);
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&d), s_items + s_parts + s_ph + s_op + s_cf, b->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return bfail(SV_ERR_OOM, std::string("batch program: ") + cudaGetErrorString(e));
@@ -196,7 +198,8 @@ static sv_status build_program(sv_batch *b) {
     std::memcpy(host.data() + s_items + s_parts, phases.data(), phases.size() * sizeof(Phase));
     std::memcpy(host.data() + s_items + s_parts + s_ph, ops.data(), ops.size() * sizeof(Op));
     std::memcpy(host.data() + s_items + s_parts + s_ph + s_op, coefs.data(), coefs.size() * sizeof(float));
-    BCUDA(cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice));
+    BCUDA(cudaMemcpyAsync(d, host.data(), host.size(), cudaMemcpyHostToDevice, b->stream));
+    BCUDA(cudaStreamSynchronize(b->stream));   // the host image goes out of scope
     BatchLaunch &B = b->launch;
     B.svbase = b->sv;
     B.items = reinterpret_cast<const BatchItem *>(d);
@@ -306,13 +309,16 @@ sv_status sv_batch_destroy(sv_batch *b) {
     if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
     cudaError_t e = cudaStreamSynchronize(b->stream);
     drop_program(b);
-    cudaFree(b->sv);
-    cudaFree(b->d_off);
-    cudaFree(b->d_nq);
-    cudaFree(b->d_done);
-    cudaFree(b->d_err);
-    cudaFree(b->d_norms);
-    if (b->own_stream) cudaStreamDestroy(b->stream);
+    dev_free(b->sv, b->stream);
+    dev_free(b->d_off, b->stream);
+    dev_free(b->d_nq, b->stream);
+    dev_free(b->d_done, b->stream);
+    dev_free(b->d_err, b->stream);
+    dev_free(b->d_norms, b->stream);
+    if (b->own_stream) {
+        cudaStreamSynchronize(b->stream);   // the frees complete before the stream goes
+        cudaStreamDestroy(b->stream);
+    }
     delete b;
     if (e != cudaSuccess) return bfail(SV_ERR_CUDA, std::string("pending batch work failed: ") + cudaGetErrorString(e));
     return SV_OK;

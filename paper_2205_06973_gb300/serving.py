@@ -104,6 +104,7 @@ class Server:
         t0 = time.perf_counter()
         s_i = 0
         planned = {}
+        host = {"plan_wait_s": 0.0, "batch_build_s": 0.0, "batches": 0, "batched_requests": 0}
 
         def now():
             return (time.perf_counter() - t0) / time_scale
@@ -134,7 +135,9 @@ class Server:
                 else:
                     st = State(r.n, "c64", stream=self.streams[s_i % len(self.streams)])
                     s_i += 1
+                    w0 = time.perf_counter()
                     plan = planned.pop(r.rid).result()
+                    host["plan_wait_s"] += time.perf_counter() - w0
                     start = now()
                     st.apply(plan, gatewise=self.mode != "parts", tc=self.tc and self.mode == "parts")
                     ev = torch.cuda.Event()
@@ -143,10 +146,16 @@ class Server:
             # the batched kernel takes every waiting small request when idle
             if batch_run is None and small_wait:
                 take, small_wait = small_wait[: self.batch_max], small_wait[self.batch_max:]
+                w0 = time.perf_counter()
                 plans = [planned.pop(r.rid).result() for r in take]
+                w1 = time.perf_counter()
+                host["plan_wait_s"] += w1 - w0
                 start = now()
                 b = Batch.from_plans([(r.n, p) for r, p in zip(take, plans)], stream=self.batch_stream)
                 b.run()
+                host["batch_build_s"] += time.perf_counter() - w1
+                host["batches"] += 1
+                host["batched_requests"] += len(take)
                 ev = torch.cuda.Event()
                 ev.record(b.stream)
                 batch_run = (take, b, ev, start)
@@ -194,6 +203,6 @@ class Server:
         lat = np.array([r.latency for r in results]) if results else np.zeros(1)
         stats = {"requests": len(results), "wall_s": wall, "circuits_per_s": len(results) / max(wall, 1e-9),
                  "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                 "mean_s": float(lat.mean()), "mode": self.mode}
+                 "mean_s": float(lat.mean()), "mode": self.mode, **host}
         results.sort(key=lambda r: r.rid)
         return results, stats
