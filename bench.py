@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 4096-circuit batched launch")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving sample")
     return ap.parse_args()
 
 
@@ -204,6 +206,77 @@ def cpu_baseline_oracle(n, gates, pog, n_parts, max_parts, budget_s=20.0):
                       f"(32 B/amplitude per pass), {dt:.1f} s"}
 
 
+def batch_section():
+    """4096 parameterised circuits (10-20 qubits, RY/RZ layers + CX ladder,
+    depth 10-50) in one persistent graph-captured launch; k, warps per CTA and
+    tiles per work item picked by the autotuner on 512 of them."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2205_06973_gb300 import autotune
+    from paper_2205_06973_gb300.batch import Batch
+    circs = synth.batch_circuits(4096)
+    t0 = time.perf_counter()
+    choice = autotune.tune_batch("param4096", circs, method="dfs", use_cache=False)
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = Batch(circs, method=choice["method"], k=choice["k"], warps_per_cta=choice["warps"],
+              tiles_per_item=choice["chunk"])
+    plan_s = time.perf_counter() - t0
+    b.run(sync=True)            # builds the work list and captures the graph
+    b.reset()
+    b.run(sync=True)
+    bytes_all = 0
+    for (n, _), p in zip(circs, b.plans):
+        _, parts = p.export()
+        bytes_all += parts * 2 * 8 * (1 << n)
+    reps = 3
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    for _ in range(reps):
+        b.run()
+    e1.record(b.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    b.reset()
+    b.run(sync=True)
+    _, norms = b.probs()
+    info = b.info()
+    b.close()
+    return {"workload": "4096 parameterised circuits, 10-20 qubits (uniform), RY/RZ layers + CX ladder, "
+                        "depth 10-50, complex64, one persistent graph-captured launch",
+            "circuits_per_s": round(4096 / ms * 1e3, 1), "ms_per_launch": round(ms, 2),
+            "GBs": round(bytes_all / ms / 1e6, 1), "bytes_per_launch": bytes_all,
+            "autotune": {k: choice[k] for k in ("method", "k", "warps", "chunk")}, "tune_s": round(tune_s, 1),
+            "plan_s": round(plan_s, 1), "parts": info.get("parts"), "items": info.get("items"),
+            "norm_min": float(np.min(norms)), "norm_max": float(np.max(norms))}
+
+
+def serving_section():
+    """The serving loop on a bounded sample of the request stream (Poisson,
+    20000 requests / 60 s, 10-33 qubits with 80 % <= 20, three families): its
+    first 300 requests of at most 26 qubits, replayed at their arrival times,
+    part-fused and gate by gate."""
+    import synth
+    from paper_2205_06973_gb300.serving import Request, Server
+    arr = synth.serving_arrivals(20000, 60.0, seed=5)
+    reqs, i = [], 0
+    while len(reqs) < 300:
+        n, fam, g = synth.serving_request(i, seed=5)
+        if n <= 26:
+            reqs.append(Request(len(reqs), n, g, arr[i], fam))
+        i += 1
+    out = {"workload": "first 300 requests with n <= 26 of the 20000-request stream (seed 5), "
+                       "arrival times replayed", "n_large": sum(r.n > 20 for r in reqs)}
+    for mode in ("parts", "gatewise"):
+        _, st = Server(budget_bytes=170e9, mode=mode).run(reqs)
+        out[mode] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items() if k != "mode"}
+    out["throughput_vs_gate_by_gate"] = round(out["parts"]["circuits_per_s"] / out["gatewise"]["circuits_per_s"], 2)
+    out["p99_vs_gate_by_gate"] = round(out["gatewise"]["p99_s"] / out["parts"]["p99_s"], 2)
+    return out
+
+
 def run_ours(a):
     import torch
     ws, rank, local = dist_env()
@@ -306,6 +379,12 @@ def run_ours(a):
         cpu = cpu_baseline_oracle(n, gates, pog, P, max_parts=64, budget_s=20.0)
         cpu["sample"] += f" ({method} k={k} plan)"
 
+    batch = serving = None
+    if rank == 0 and not a.no_batch:
+        batch = batch_section()
+    if rank == 0 and not a.no_serving:
+        serving = serving_section()
+
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
                 "warmup": max(a.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True,
@@ -317,7 +396,8 @@ def run_ours(a):
                            "state_bytes": st.nbytes, "parallelism": f"replicas x{ws}",
                            "l2": "state (2 GiB) larger than L2 (129 MB); no flush needed"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": passes * a.steps, "compare": compare, "norm": norm}
+                "gpu_launches": passes * a.steps, "compare": compare, "norm": norm,
+                "batch": batch, "serving": serving}
         print(json.dumps(line), flush=True)
     st.close()
     plan.close()

@@ -6,7 +6,9 @@ probabilities as views of one concatenated device tensor.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import ctypes
+import os
 
 import numpy as np
 import torch
@@ -31,7 +33,10 @@ class Batch:
         N.check(N.lib.sv_batch_create(self.n, self.nq.ctypes.data, ctypes.c_void_p(self.stream.cuda_stream),
                                       ctypes.byref(h)))
         self.h = h
-        self.plans = plans if plans is not None else [Plan(g, n, method, min(k, n)) for n, g in circuits]
+        if plans is None:   # the partitioners run in C++ with the GIL released: plan in parallel
+            with cf.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+                plans = list(ex.map(lambda c: Plan(c[1], c[0], method, min(k, c[0])), circuits))
+        self.plans = plans
         for i, p in enumerate(self.plans):
             N.check(N.lib.sv_batch_set_plan(self.h, i, p.h))
         if warps_per_cta or tiles_per_item:

@@ -9,7 +9,11 @@ a free slot. Admitted states stay on the device until their result is taken.
   started runs in one batched persistent launch (sv_batch_*), so requests
   that arrived while the previous batch was on the GPU join the next one.
 * Large circuits get their own state and CUDA stream and run their part
-  passes (sv_apply_parts) concurrently with the batch and with each other.
+  passes (sv_apply_parts) beside the batch; at most ``large_running`` of
+  them at a time, in arrival order (each pass fills the GPU, so sharing it
+  among many large requests only stretches all their latencies). The batch
+  stream has the higher priority, so small requests are not queued behind
+  the passes of large ones.
 
 A request's result is its probability vector summary: the norm (FP64
 accumulation on the device), the probability of |0...0> and the most likely
@@ -69,7 +73,7 @@ def _summary(probs: torch.Tensor):
 class Server:
     def __init__(self, budget_bytes=170e9, max_slots=4096, small_n=20, batch_max=512, k_small=10,
                  k_large=6, tc=True, method_small="dfs", method_large="dagp", mode="parts",
-                 keep_states=False, planners=8):
+                 keep_states=False, planners=8, large_running=2):
         self.budget = float(budget_bytes)
         self.max_slots = max_slots
         self.small_n = small_n
@@ -81,9 +85,11 @@ class Server:
         self.method_large = method_large
         self.mode = mode
         self.keep = keep_states
+        self.large_running = large_running
         self.pool = cf.ThreadPoolExecutor(max_workers=planners)
-        self.streams = [torch.cuda.Stream() for _ in range(8)]
-        self.batch_stream = torch.cuda.Stream()
+        self.streams = [torch.cuda.Stream() for _ in range(max(1, large_running))]
+        lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+        self.batch_stream = torch.cuda.Stream(priority=hi)
 
     @staticmethod
     def state_bytes(n):
@@ -95,6 +101,7 @@ class Server:
         reqs = sorted(requests, key=lambda r: r.arrival)
         pending = collections.deque()
         small_wait = []                    # admitted small requests not started
+        large_wait = collections.deque()   # admitted large requests not started
         running_large = []                 # (req, state, plan, event, start)
         batch_run = None                   # (reqs, batch, event, start)
         used = 0.0
@@ -112,7 +119,7 @@ class Server:
         def plan_future(r, method, k):
             return self.pool.submit(Plan, r.gates, r.n, method if self.mode == "parts" else "none", min(k, r.n))
 
-        while i < len(reqs) or pending or small_wait or running_large or batch_run:
+        while i < len(reqs) or pending or small_wait or large_wait or running_large or batch_run:
             t = now()
             while i < len(reqs) and reqs[i].arrival <= t:
                 r = reqs[i]
@@ -133,16 +140,20 @@ class Server:
                 if r.n <= self.small_n and self.mode == "parts":
                     small_wait.append(r)
                 else:
-                    st = State(r.n, "c64", stream=self.streams[s_i % len(self.streams)])
-                    s_i += 1
-                    w0 = time.perf_counter()
-                    plan = planned.pop(r.rid).result()
-                    host["plan_wait_s"] += time.perf_counter() - w0
-                    start = now()
-                    st.apply(plan, gatewise=self.mode != "parts", tc=self.tc and self.mode == "parts")
-                    ev = torch.cuda.Event()
-                    ev.record(st.stream)
-                    running_large.append((r, st, plan, ev, start))
+                    large_wait.append(r)
+            # large requests start in arrival order as running slots free up
+            while large_wait and len(running_large) < max(1, self.large_running):
+                r = large_wait.popleft()
+                st = State(r.n, "c64", stream=self.streams[s_i % len(self.streams)])
+                s_i += 1
+                w0 = time.perf_counter()
+                plan = planned.pop(r.rid).result()
+                host["plan_wait_s"] += time.perf_counter() - w0
+                start = now()
+                st.apply(plan, gatewise=self.mode != "parts", tc=self.tc and self.mode == "parts")
+                ev = torch.cuda.Event()
+                ev.record(st.stream)
+                running_large.append((r, st, plan, ev, start))
             # the batched kernel takes every waiting small request when idle
             if batch_run is None and small_wait:
                 take, small_wait = small_wait[: self.batch_max], small_wait[self.batch_max:]
@@ -193,7 +204,8 @@ class Server:
                     slots -= 1
                 b.close()
                 batch_run = None
-            if not (running_large or batch_run) and i < len(reqs) and not pending and not small_wait:
+            if not (running_large or batch_run) and i < len(reqs) and not pending and not small_wait \
+                    and not large_wait:
                 wait = reqs[i].arrival - now()
                 if wait > 0:
                     time.sleep(min(wait * time_scale, 0.01))
