@@ -85,6 +85,8 @@ def traffic_from_profile(kernel, workload_key):
     cur = kernel_source_hash(kernel)
     with open(path) as f:
         for line in f:
+            if line.lstrip().startswith("#"):
+                continue
             parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
             if (parts.get("kernel") == kernel and parts.get("source") == cur
                     and parts.get("workload") == workload_key):

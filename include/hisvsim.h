@@ -158,10 +158,10 @@ sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *nor
  * CUDA graph captures once and replays (the batched workload: thousands of
  * uneven circuits of 10..30 qubits). States are complex64, contiguous in one
  * device buffer in circuit order (circuit i starts after the 2^n_j amplitudes
- * of every j < i). Each plan's parts run on 2^10-amplitude tiles, one warp
+ * of every j < i). Each plan's parts run on 2^9-amplitude tiles, one warp
  * per tile; parts of one circuit run in order (a device work list in wave
  * order with per-circuit tile counters and bounded waits), parts of different
- * circuits overlap. Parts are limited to 10 qubits (plans with k <= 10).
+ * circuits overlap. Parts are limited to 9 qubits (plans with k <= 9).
  *
  * sv_batch_create  n_qubits[n_circuits] in [10, 30]; states start in |0...0>;
  *                  stream NULL = a stream the library creates (graph capture

@@ -122,7 +122,7 @@ def tune_state(workload, n, gates, precision="c64", candidates=STATE_CANDIDATES,
     return out
 
 
-BATCH_CANDIDATES = tuple((k, w, c) for k in (9, 10) for w in (4, 8) for c in (2, 4, 8))
+BATCH_CANDIDATES = tuple((k, w, c) for k in (8, 9) for w in (4, 8) for c in (2, 4, 8))
 
 
 def tune_batch(workload, circuits, method="dfs", candidates=BATCH_CANDIDATES, sample=512, use_cache=True):

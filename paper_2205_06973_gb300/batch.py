@@ -18,7 +18,7 @@ from .api import Plan
 
 
 class Batch:
-    def __init__(self, circuits, method="dfs", k=10, warps_per_cta=0, tiles_per_item=0, stream=None,
+    def __init__(self, circuits, method="dfs", k=9, warps_per_cta=0, tiles_per_item=0, stream=None,
                  plans=None):
         """circuits: list of (n_qubits, gates); or plans: list of built Plan
         objects (the batch then owns them)."""

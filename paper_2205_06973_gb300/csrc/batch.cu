@@ -1,6 +1,6 @@
 // Batched persistent kernel: thousands of small, uneven circuits in one launch.
 //
-// Every circuit's plan is compiled for 2^10-amplitude tiles (32 lanes x 32
+// Every circuit's plan is compiled for 2^9-amplitude tiles (32 lanes x 16
 // amplitudes), so one warp executes one tile of one part with warp-private
 // shared memory and no CTA-wide barrier. A device work list holds items
 // (circuit, part, range of tiles) in wave order: the first parts of all
@@ -21,8 +21,8 @@ namespace hisv {
 
 namespace {
 
-constexpr int BT = 10;          // tile qubits
-constexpr int BR = 5;           // register bits per lane
+constexpr int BT = BATCH_TILE_QUBITS;   // tile qubits
+constexpr int BR = BATCH_REG_BITS;      // register bits per lane
 constexpr int BNR = 1 << BR;
 constexpr uint32_t BATCH_WAIT_LIMIT = 1u << 22;
 

@@ -24,7 +24,7 @@ struct BatchLaunch {
     const BatchItem *items;
     uint32_t n_items;
     const uint64_t *circ_off;    // first amplitude of each circuit's state
-    const PartLaunch *parts;     // all circuits' parts (tile of 2^10 amplitudes)
+    const PartLaunch *parts;     // all circuits' parts (tile of 2^9 amplitudes)
     const Phase *phases;
     const Op *ops;
     const float *coefs;
@@ -33,7 +33,9 @@ struct BatchLaunch {
     int *err;                    // bounded-wait failure flag
 };
 
-constexpr int BATCH_TILE_QUBITS = 10;
+constexpr int BATCH_TILE_QUBITS = 9;   // one warp's tile: 32 lanes x 16 amplitudes
+constexpr int BATCH_REG_BITS = 4;      // tile qubits held in registers (16 amplitudes per lane)
+constexpr int BATCH_MIN_QUBITS = 10;
 
 // Raise the shared-memory limit and return the persistent grid size (CTAs
 // resident on all SMs) for a CTA of warps_per_cta warps.

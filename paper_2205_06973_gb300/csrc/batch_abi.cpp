@@ -72,7 +72,7 @@ sv_status sv_batch_create(uint32_t n_circuits, const int *n_qubits, void *stream
     b->nq.assign(n_qubits, n_qubits + n_circuits);
     b->off.resize(n_circuits);
     for (uint32_t i = 0; i < n_circuits; i++) {
-        if (b->nq[i] < BATCH_TILE_QUBITS || b->nq[i] > 30)
+        if (b->nq[i] < BATCH_MIN_QUBITS || b->nq[i] > 30)
             return bfail(SV_ERR_ARG, "batched circuits need 10..30 qubits (circuit " + std::to_string(i) + ")");
         b->off[i] = b->total;
         b->total += 1ull << b->nq[i];
@@ -114,7 +114,7 @@ sv_status sv_batch_set_plan(sv_batch *b, uint32_t i, sv_plan *p) {
     if (i >= b->n) return bfail(SV_ERR_ARG, "circuit index out of range");
     if (p->n != b->nq[i]) return bfail(SV_ERR_ARG, "plan qubit count differs from circuit " + std::to_string(i));
     if (p->method == SV_PART_NONE) return bfail(SV_ERR_ARG, "batched circuits need a partitioned plan");
-    if (p->max_part > BATCH_TILE_QUBITS) return bfail(SV_ERR_PARTITION, "batched parts are limited to 10 qubits (k <= 10)");
+    if (p->max_part > BATCH_TILE_QUBITS) return bfail(SV_ERR_PARTITION, "batched parts are limited to 9 qubits (k <= 9)");
     b->plans[i] = p;
     drop_program(b);
     return SV_OK;
@@ -142,7 +142,7 @@ static sv_status build_program(sv_batch *b) {
         if (!p) return bfail(SV_ERR_ARG, "circuit " + std::to_string(c) + " has no plan");
         Program prog;
         std::string err;
-        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, false, BATCH_TILE_QUBITS, 5, 0, prog, err))
+        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, false, BATCH_TILE_QUBITS, BATCH_REG_BITS, 0, prog, err))
             return bfail(SV_ERR_PARTITION, err);
         const uint32_t ph0 = (uint32_t)phases.size(), op0 = (uint32_t)ops.size(), cf0 = (uint32_t)coefs.size();
         part_base[c] = (uint32_t)parts.size();

@@ -71,7 +71,7 @@ def _summary(probs: torch.Tensor):
 
 
 class Server:
-    def __init__(self, budget_bytes=170e9, max_slots=4096, small_n=20, batch_max=512, k_small=10,
+    def __init__(self, budget_bytes=170e9, max_slots=4096, small_n=20, batch_max=512, k_small=9,
                  k_large=6, tc=True, method_small="dfs", method_large="dagp", mode="parts",
                  keep_states=False, planners=8, large_running=2):
         self.budget = float(budget_bytes)

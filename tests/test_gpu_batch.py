@@ -23,7 +23,7 @@ def test_batch_matches_oracle_per_circuit():
     circs = [c for c in _circuits(40) if c[0] <= 15][:16]
     circs.append((10, synth.qft(10)))
     circs.append((12, synth.layered(12, 6, seed=3, two_q=("CX", "CZ"))))
-    b = Batch(circs, method="dagp", k=10)
+    b = Batch(circs, method="dagp", k=9)
     b.run(sync=True)
     probs, norms = b.probs()
     probs = probs.cpu().numpy()
