@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) k_batch(float2 *__restrict__ svbase, cons
                         if (i & (1 << b)) o ^= s_reg[b];
                     a[i] = wsm[o];
                 }
-                run_ops<float, BR>(a, ops + ph.op_begin, ph.op_count, coefs, lane, tpr, tpi);
+                run_ops<float, BR>(a, ops + ph.op_begin, ph.op_count, coefs, lane, tpr, tpi, wsm, s_thr, s_reg);
             }
             if (P.flags & PL_STORE_FACTOR) {
                 const float gr = (float)P.gr, gi = (float)P.gi;

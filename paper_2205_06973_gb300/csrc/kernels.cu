@@ -157,7 +157,7 @@ k_part(typename CT<Real>::T *__restrict__ sv, const __grid_constant__ PartLaunch
                 a[i] = cur[o];
             }
             // Execute: the phase's gates
-            run_ops<Real, R>(a, ops + ph.op_begin, ph.op_count, coefs, tid, tpr, tpi);
+            run_ops<Real, R>(a, ops + ph.op_begin, ph.op_count, coefs, tid, tpr, tpi, cur, s_thr, s_reg);
         }
         // Scatter: the last phase's layout, with SWAP relabels applied; the
         // part factor and the last phase's per-thread phase are applied here

@@ -76,30 +76,6 @@ __device__ __forceinline__ void op_ry(C (&a)[NR], Real c, Real s) {
     }
 }
 
-template <int NR, int B, typename C>
-__device__ __forceinline__ void op_x(C (&a)[NR]) {
-#pragma unroll
-    for (int i = 0; i < NR; i++) {
-        if (i & (1 << B)) continue;
-        const int j = i | (1 << B);
-        const C x = a[i];
-        a[i] = a[j];
-        a[j] = x;
-    }
-}
-
-template <int NR, int B, typename C>
-__device__ __forceinline__ void op_y(C (&a)[NR]) {
-#pragma unroll
-    for (int i = 0; i < NR; i++) {
-        if (i & (1 << B)) continue;
-        const int j = i | (1 << B);
-        const C x = a[i], y = a[j];
-        a[i].x = y.y; a[i].y = -y.x;
-        a[j].x = -x.y; a[j].y = x.x;
-    }
-}
-
 template <typename C, typename Real>
 __device__ __forceinline__ void cmul_in(C &v, Real dr, Real di) {
     const Real x = v.x, y = v.y;
@@ -128,18 +104,6 @@ __device__ __forceinline__ void op_z(C (&a)[NR]) {
 #pragma unroll
     for (int i = 0; i < NR; i++)
         if (i & (1 << B)) { a[i].x = -a[i].x; a[i].y = -a[i].y; }
-}
-
-template <int NR, int A, int B, typename C>
-__device__ __forceinline__ void op_cx(C (&a)[NR]) {   // A control, B target
-#pragma unroll
-    for (int i = 0; i < NR; i++) {
-        if (!(i & (1 << A)) || (i & (1 << B))) continue;
-        const int j = i | (1 << B);
-        const C x = a[i];
-        a[i] = a[j];
-        a[j] = x;
-    }
 }
 
 template <int NR, int A, int B, typename C, typename Real>
@@ -176,17 +140,76 @@ __device__ __forceinline__ uint32_t swz(int p) {
 }
 
 
-// Run a phase's ops on the thread's amplitudes. ops/cf_base: the op records
+// Register permutations (X, Y, CX) go through shared memory: the thread
+// stores its amplitudes into its own slots of the tile buffer (slot of
+// register index i: s_thr ^ XOR of s_reg[b] over the bits b of i, the
+// layout the phase was loaded with) and loads them back permuted. No other
+// thread touches these slots, so no barrier is needed, and no register is
+// renamed inside the op switch: a permutation kept in registers renames them
+// differently on every path, and reconciling those renamings at the loop's
+// back edge costs every op of the interpreter (measured: about a third of
+// its instructions).
+// New a[i] = old a[i ^ (1 << t)] where the control holds (tctl, and bit cbit
+// of i when cbit >= 0), else a[i] stays; Y also multiplies by -i (bit t of i
+// clear) or +i (set).
+template <int NR, int R, typename C>
+__device__ __forceinline__ void perm_smem(C (&a)[NR], C *buf, uint32_t s_thr, const uint32_t (&s_reg)[R], int t,
+                                          int cbit, bool tctl, bool y) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        uint32_t o = s_thr;
+#pragma unroll
+        for (int b = 0; b < R; b++)
+            if (i & (1 << b)) o ^= s_reg[b];
+        buf[o] = a[i];
+    }
+    uint32_t st = 0;   // s_reg[t] without a dynamic register index
+#pragma unroll
+    for (int b = 0; b < R; b++)
+        if (b == t) st = s_reg[b];
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        uint32_t o = s_thr;
+        asm volatile("" : "+r"(o));   // recompute the slots: keeping all of them live would spill
+#pragma unroll
+        for (int b = 0; b < R; b++)
+            if (i & (1 << b)) o ^= s_reg[b];
+        const bool ctl = tctl && (cbit < 0 || ((i >> cbit) & 1));
+        const C v = buf[ctl ? (o ^ st) : o];
+        if (y) {
+            if ((i >> t) & 1) { a[i].x = -v.y; a[i].y = v.x; }
+            else { a[i].x = v.y; a[i].y = -v.x; }
+        } else {
+            a[i] = v;
+        }
+    }
+}
+
+// Run a phase's ops on the thread's amplitudes. ops/coefs: the op records
 // and the coefficient array their coef indices refer to; (tpr, tpi): the
-// per-thread phase of diagonal gates on thread bits.
+// per-thread phase of diagonal gates on thread bits; buf, s_thr, s_reg: the
+// tile buffer and the thread's slot layout of this phase (permutations).
 template <typename Real, int R>
 __device__ __forceinline__ void run_ops(typename CT<Real>::T (&a)[1 << R], const Op *__restrict__ opsp, uint32_t count,
-                                        const Real *__restrict__ coefs, int tid, Real &tpr, Real &tpi) {
+                                        const Real *__restrict__ coefs, int tid, Real &tpr, Real &tpi,
+                                        typename CT<Real>::T *buf, uint32_t s_thr, const uint32_t (&s_reg)[R]) {
     constexpr int NR = 1 << R;
     for (uint32_t o = 0; o < count; o++) {
         const Op op = opsp[o];
         const Real *cf = coefs + op.coef;
         switch (op.kind) {
+        case OP_X:
+            perm_smem<NR, R>(a, buf, s_thr, s_reg, op.a, -1, true, false);
+            break;
+        case OP_Y:
+            perm_smem<NR, R>(a, buf, s_thr, s_reg, op.a, -1, true, true);
+            break;
+        case OP_CX:
+            perm_smem<NR, R>(a, buf, s_thr, s_reg, op.b, op.a, true, false);
+            break;
+        case OP_CXT:
+            perm_smem<NR, R>(a, buf, s_thr, s_reg, op.b, -1, ((tid >> op.tb) & 1) != 0, false);
+            break;
         case OP_H:
             with_bit<R>(op.a, [&](auto bc) { op_h<NR, decltype(bc)::value>(a); });
             break;
@@ -201,12 +224,6 @@ __device__ __forceinline__ void run_ops(typename CT<Real>::T (&a)[1 << R], const
             const Real c = cf[0], s = cf[1];
             with_bit<R>(op.a, [&](auto bc) { op_ry<NR, decltype(bc)::value>(a, c, s); });
         } break;
-        case OP_X:
-            with_bit<R>(op.a, [&](auto bc) { op_x<NR, decltype(bc)::value>(a); });
-            break;
-        case OP_Y:
-            with_bit<R>(op.a, [&](auto bc) { op_y<NR, decltype(bc)::value>(a); });
-            break;
         case OP_D: {
             const Real d0r = cf[0], d0i = cf[1], d1r = cf[2], d1i = cf[3];
             with_bit<R>(op.a, [&](auto bc) { op_d<NR, decltype(bc)::value>(a, d0r, d0i, d1r, d1i); });
@@ -217,14 +234,6 @@ __device__ __forceinline__ void run_ops(typename CT<Real>::T (&a)[1 << R], const
         } break;
         case OP_Z:
             with_bit<R>(op.a, [&](auto bc) { op_z<NR, decltype(bc)::value>(a); });
-            break;
-        case OP_CX:
-            with_bit<R>(op.a, [&](auto ac) {
-                with_bit<R>(op.b, [&](auto bc) {
-                    constexpr int A = decltype(ac)::value, B = decltype(bc)::value;
-                    if constexpr (A != B) op_cx<NR, A, B>(a);
-                });
-            });
             break;
         case OP_CP: {
             const Real dr = cf[0], di = cf[1];
@@ -242,10 +251,6 @@ __device__ __forceinline__ void run_ops(typename CT<Real>::T (&a)[1 << R], const
                     if constexpr (A != B) op_cz<NR, A, B>(a);
                 });
             });
-            break;
-        case OP_CXT:
-            if ((tid >> op.tb) & 1)
-                with_bit<R>(op.b, [&](auto bc) { op_x<NR, decltype(bc)::value>(a); });
             break;
         case OP_CPT:
             if ((tid >> op.tb) & 1) {
