@@ -327,7 +327,8 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
                 op.coef = c;
                 prog.ops.push_back(op);
             };
-            for (int g : sched) {
+            // one gate's ops (the gate alone)
+            auto emit_one = [&](int g) -> bool {
                 const GateRef &gr = gates[g];
                 const double th = gr.theta;
                 const int s0 = slot_of[gr.q[0]];
@@ -391,7 +392,75 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
                     err = "unknown gate kind";
                     return false;
                 }
+                return true;
+            };
+            // Runs of one-qubit gates on one qubit with no multi-qubit gate on it
+            // in between (gates on other qubits commute with them) become one
+            // op: their product, as a phase (diagonal; the entry of |0> joins
+            // the part factor) or a general 2x2 matrix.
+            auto emit_fused = [&](int q, const std::vector<int> &run) -> bool {
+                if (run.size() == 1) return emit_one(run[0]);
+                double M[8] = {1, 0, 0, 0, 0, 0, 1, 0};
+                for (int g : run) {
+                    double U[8], T[8];
+                    gate_matrix_1q(gates[g].kind, gates[g].theta, U);
+                    for (int r = 0; r < 2; r++)
+                        for (int c = 0; c < 2; c++) {
+                            double re = 0, im = 0;
+                            for (int k = 0; k < 2; k++) {
+                                const double ar = U[2 * (2 * r + k)], ai = U[2 * (2 * r + k) + 1];
+                                const double br = M[2 * (2 * k + c)], bi = M[2 * (2 * k + c) + 1];
+                                re += ar * br - ai * bi;
+                                im += ar * bi + ai * br;
+                            }
+                            T[2 * (2 * r + c)] = re;
+                            T[2 * (2 * r + c) + 1] = im;
+                        }
+                    std::memcpy(M, T, sizeof(M));
+                }
+                const int sq = slot_of[q];
+                const double off = std::hypot(M[2], M[3]) + std::hypot(M[4], M[5]);
+                if (off < 1e-14) {
+                    // diag(m00, m11) = m00 diag(1, m11 / m00), |m00| = 1
+                    const double d0r = M[0], d0i = M[1], d1r = M[6], d1i = M[7];
+                    fmul(d0r, d0i);
+                    const double pr = d1r * d0r + d1i * d0i, pi = d1i * d0r - d1r * d0i;
+                    if (std::fabs(pr - 1.0) < 1e-15 && std::fabs(pi) < 1e-15) return true;   // identity
+                    if ((Rset >> sq) & 1) emit(OP_P, rb[sq], 0, 0, coef({pr, pi}));
+                    else {
+                        emit(OP_TD, 0, 0, tbit[sq], coef({1.0, 0.0, pr, pi}));
+                        tphase = true;
+                    }
+                    return true;
+                }
+                if (!((Rset >> sq) & 1)) {
+                    err = "fused non-diagonal gate on a thread slot";
+                    return false;
+                }
+                emit(OP_U2, rb[sq], 0, 0, coef({M[0], M[1], M[2], M[3], M[4], M[5], M[6], M[7]}));
+                return true;
+            };
+            std::vector<std::vector<int>> pend(n);
+            std::vector<int> pend_order;
+            auto flush = [&](int q) -> bool {
+                if (pend[q].empty()) return true;
+                const bool ok = emit_fused(q, pend[q]);
+                pend[q].clear();
+                return ok;
+            };
+            for (int g : sched) {
+                const GateRef &gr = gates[g];
+                if (gr.arity == 1) {
+                    if (pend[gr.q[0]].empty()) pend_order.push_back(gr.q[0]);
+                    pend[gr.q[0]].push_back(g);
+                    continue;
+                }
+                for (int j = 0; j < gr.arity; j++)
+                    if (!flush(gr.q[j])) return false;
+                if (!emit_one(g)) return false;
             }
+            for (int q : pend_order)
+                if (!flush(q)) return false;
             // the last phase's per-thread phase is applied with the part factor at the store
             if (tphase && !last) emit(OP_TAPPLY, 0, 0, 0, 0);
             if (last) last_tphase = tphase;

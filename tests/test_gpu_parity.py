@@ -162,3 +162,35 @@ def test_empty_circuit_and_basis():
     ref = np.zeros(1 << 12)
     ref[37] = 1
     assert max_abs(out, ref) == 0.0
+
+
+def _one_qubit_runs(n, G, seed):
+    """Long runs of one-qubit gates of every kind on few qubits, between
+    sparse two-qubit gates: the planner fuses each run into one op (a phase
+    when the product is diagonal, else a general 2x2 matrix)."""
+    r = synth.SplitMix64(seed)
+    one = [x for x in synth.GATE_NAMES if x not in synth.TWO_QUBIT]
+    gates = []
+    for _ in range(G):
+        if r.randint(8) == 0:
+            a = r.randint(n)
+            b = (a + 1 + r.randint(n - 1)) % n
+            gates.append((synth.TWO_QUBIT[r.randint(len(synth.TWO_QUBIT))], (a, b), r.angle()))
+        else:
+            q = r.randint(4)   # few qubits: long runs on each
+            gates.append((one[r.randint(len(one))], (q,), r.angle()))
+    # runs whose product is diagonal or the identity
+    gates += [("H", (5,), 0.0), ("Z", (5,), 0.0), ("H", (5,), 0.0), ("X", (6,), 0.0), ("X", (6,), 0.0),
+              ("RZ", (7,), 0.3), ("T", (7,), 0.0), ("S", (7,), 0.0)]
+    return gates
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("method", ["nat", "dagp"])
+def test_fused_one_qubit_runs(precision, method):
+    n = 12
+    g = _one_qubit_runs(n, 400, 77)
+    psi = random_state(n, 78)
+    ref = sim.run(n, g, psi)
+    out = run_gpu(n, g, method=method, k=8, psi=psi, precision=precision)
+    assert max_abs(out, ref) <= TOL[precision]
