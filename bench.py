@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-circuit batched launch")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sample")
+    ap.add_argument("--oracle-report", action="store_true",
+                    help="with --impl reference: time the oracle in both modes, 1 thread and all cores, on the "
+                         "configurations' workloads (bounded prefixes, scaled), one JSON line each")
     return ap.parse_args()
 
 
@@ -454,9 +457,73 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def _oracle_timing():
+    """One measurement series of the oracle (complex128, OpenMP threads as
+    set by OMP_NUM_THREADS): gate by gate and Algorithm 1 on the 14-qubit
+    plain layered circuit (whole), the 28-qubit layered circuit (a prefix of
+    gates / parts, scaled to the whole) and a sample of the 4096-circuit batch."""
+    import numpy as np
+    import synth
+    from oracle import partition as pt
+    from oracle import sim
+    threads = sim.num_threads()
+
+    def rec(**kw):
+        kw["threads"] = threads
+        kw["kind"] = "oracle"
+        print(json.dumps(kw), flush=True)
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    n, g = synth.plain_layered_14q()
+    rec(workload="plain layered 14q, 840 gates, complex128", mode="gate by gate",
+        s=round(timed(lambda: sim.run(n, g)), 4), scaled="none")
+    pog = pt.partition(g, n, "dagp", 8)
+    P = max(pog) + 1
+    rec(workload="plain layered 14q, 840 gates, complex128", mode=f"Algorithm 1, dagP k=8 ({P} parts)",
+        s=round(timed(lambda: sim.run_alg1(n, g, pog, P)), 4), scaled="none")
+    n, g = synth.layered_28q()
+    psi = sim.basis(n)
+    G0 = 8
+    dt = timed(lambda: sim.run(n, g[:G0], psi))
+    rec(workload="layered 28q, 2520 gates, complex128", mode="gate by gate", s=round(dt * len(g) / G0, 2),
+        scaled=f"first {G0} gates took {dt:.2f} s, scaled by {len(g)}/{G0}")
+    pog = np.asarray(pt.partition(g, n, "dagp", 10))
+    P = int(pog.max()) + 1
+    P0 = 1
+    sub = [x for x, p in zip(g, pog) if p < P0]
+    dt = timed(lambda: sim.run_alg1(n, sub, [int(p) for p in pog if p < P0], P0, psi))
+    rec(workload="layered 28q, 2520 gates, complex128", mode=f"Algorithm 1, dagP k=10 ({P} parts)",
+        s=round(dt * P / P0, 2), scaled=f"first {P0} parts took {dt:.2f} s, scaled by {P}/{P0}")
+    circs = synth.batch_circuits(16)
+    dt = timed(lambda: [sim.run(c[0], c[1]) for c in circs])
+    rec(workload="4096 parameterised circuits, 10-20 qubits, complex128", mode="gate by gate",
+        circuits_per_s=round(len(circs) / dt, 2), scaled=f"{len(circs)} circuits took {dt:.2f} s")
+    plans = [pt.partition(c[1], c[0], "dfs", 9) for c in circs]
+    dt = timed(lambda: [sim.run_alg1(c[0], c[1], p, max(p) + 1) for c, p in zip(circs, plans)])
+    rec(workload="4096 parameterised circuits, 10-20 qubits, complex128", mode="Algorithm 1, DFS k=9",
+        circuits_per_s=round(len(circs) / dt, 2), scaled=f"{len(circs)} circuits took {dt:.2f} s")
+
+
+def oracle_report():
+    """The oracle timing series single-threaded and on all host cores (each
+    in a child process, since OpenMP reads its thread count at start)."""
+    for threads in ("1", str(os.cpu_count() or 1)):
+        env = dict(os.environ, OMP_NUM_THREADS=threads, HISV_ORACLE_TIMING="1")
+        subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference"], env=env, check=True)
+
+
 def main():
+    if os.environ.get("HISV_ORACLE_TIMING"):
+        _oracle_timing()
+        return
     a = parse()
-    if a.impl == "reference":
+    if a.impl == "reference" and a.oracle_report:
+        oracle_report()
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -1,0 +1,47 @@
+"""Parity at the benchmark's full size, in the launch configuration bench.py
+times: the 28-qubit random layered circuit (depth 60, 2520 gates) from
+|0...0>, complex64 on the tensor-core dense path (dagP, k = 6), against the
+complex128 gate-list path (dagP, k = 10; FP64 arithmetic, pinned to the CPU
+oracle at 1e-12 by the smaller parity tests) and against the complex64
+gate-by-gate kernels. At 2^28 amplitudes the oracle cannot run in a test, so
+the check uses properties that hold at any size: two independent kernel
+paths agree amplitude by amplitude within the complex64 tolerance, the
+fidelity is >= 0.99999 and the norm stays 1."""
+import pytest
+import torch
+
+import synth
+from tests.gpu_util import native
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(api, n, g, precision, method, k, tc=False, gatewise=False):
+    plan = api.Plan(g, n, method, k)
+    st = api.State(n, precision)
+    st.apply(plan, sync=True, tc=tc, gatewise=gatewise)
+    plan.close()
+    return st
+
+
+def test_layered_28q_dense_vs_c128_and_gatewise():
+    _, api = native()
+    n, g = synth.layered_28q()
+    assert n == 28 and len(g) == 2520
+    ref_st = _run(api, n, g, "c128", "dagp", 10)
+    ref = ref_st.amplitudes()
+    dense_st = _run(api, n, g, "c64", "dagp", 6, tc=True)
+    dense = dense_st.amplitudes().to(torch.complex128)
+    assert abs(float(torch.linalg.vector_norm(ref)) - 1.0) <= 1e-12
+    assert abs(float(torch.linalg.vector_norm(dense)) - 1.0) <= 1e-5
+    assert float((dense - ref).abs().max()) <= 1e-5
+    fid = float(torch.vdot(ref, dense).abs() ** 2)
+    assert fid >= 0.99999, fid
+    del dense
+    dense_st.close()
+    gw_st = _run(api, n, g, "c64", "dagp", 6, gatewise=True)
+    gw = gw_st.amplitudes().to(torch.complex128)
+    assert float((gw - ref).abs().max()) <= 1e-5
+    assert float(torch.vdot(ref, gw).abs() ** 2) >= 0.99999
+    gw_st.close()
+    ref_st.close()
