@@ -343,25 +343,40 @@ def run_ours(a):
 
     e2e = None
     if not a.no_e2e:
-        host_in = torch.zeros(1 << n, dtype=torch.complex64).pin_memory()
-        host_in[0] = 1.0
-        host_out = torch.empty(1 << n, dtype=torch.complex64).pin_memory()
-        reps = 3
-        st.upload(host_in)
-        st.apply(plan, tc=tc)
-        st.copy_to_host(host_out)
+        # two states on two streams: a step's upload and download overlap the
+        # other state's passes (every step still copies its input in and its
+        # result out through the C ABI)
+        sts = [st, api.State(n, "c64", stream=torch.cuda.Stream(), tile=choice.get("tile", 0))]
+        host_in = [torch.zeros(1 << n, dtype=torch.complex64).pin_memory() for _ in range(2)]
+        host_out = [torch.empty(1 << n, dtype=torch.complex64).pin_memory() for _ in range(2)]
+        for h in host_in:
+            h[0] = 1.0
+        for i in range(2):
+            sts[i].upload(host_in[i])
+            sts[i].apply(plan, tc=tc)
+            sts[i].download(host_out[i])
+        for x in sts:
+            x.sync()
+        reps = 6
         barrier(ws)
         t0 = time.perf_counter()
-        for _ in range(reps):
-            st.upload(host_in)
-            st.apply(plan, tc=tc)
-            st.copy_to_host(host_out)       # synchronises the stream
+        for i in range(reps):
+            x = sts[i % 2]
+            if i >= 2:
+                x.sync()          # its step i-2 result has reached host memory
+            x.upload(host_in[i % 2])
+            x.apply(plan, tc=tc)
+            x.download(host_out[i % 2])
+        for x in sts:
+            x.sync()
         dt = (time.perf_counter() - t0) / reps
         dt = max_over_ranks(ws, dt, dev)
+        sts[1].close()
         e2e = {"value": round(ws * bytes_per_step / dt / 1e9, 1), "unit": UNIT,
                "h2d_bytes_per_step": st.nbytes, "d2h_bytes_per_step": st.nbytes,
-               "ms_per_step": round(dt * 1e3, 3),
-               "api": "sv_upload + sv_apply_parts + sv_copy_state (pinned host buffers)"}
+               "ms_per_step": round(dt * 1e3, 3), "steps": reps,
+               "api": "sv_upload + sv_apply_parts + sv_download (pinned host buffers), two states on two "
+                      "streams so that one step's copies overlap the other's passes"}
 
     compare = None
     if not a.no_compare:

@@ -99,6 +99,12 @@ sv_status sv_set_basis(sv_state *s, uint64_t index);
 sv_status sv_upload(sv_state *s, const void *host_src, size_t bytes);
 /* Copy the state to host memory; synchronises the stream. bytes = state size. */
 sv_status sv_copy_state(sv_state *s, void *host_dst, size_t bytes);
+/* Stream-ordered copy of the state to host memory (no synchronisation: the
+ * data is in host_dst once the stream has passed the copy, e.g. after
+ * sv_sync). host_dst must stay valid until then; pinned memory makes the
+ * copy asynchronous, so a caller can overlap one state's transfers with
+ * another state's passes. bytes = state size. */
+sv_status sv_download(sv_state *s, void *host_dst, size_t bytes);
 /* Device address of the amplitudes and the number of bytes they occupy. */
 sv_status sv_device_ptr(sv_state *s, void **ptr, size_t *bytes);
 /* Synchronise the state's stream and report any pending device error; a

@@ -54,6 +54,7 @@ _SIGS = {
     "sv_set_basis": ([_vp, ctypes.c_uint64], ctypes.c_int),
     "sv_upload": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "sv_copy_state": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
+    "sv_download": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "sv_device_ptr": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "sv_sync": ([_vp], ctypes.c_int),
     "sv_set_tile": ([_vp, ctypes.c_int], ctypes.c_int),

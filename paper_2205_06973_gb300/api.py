@@ -90,6 +90,12 @@ class State:
         N.check(N.lib.sv_copy_state(self.h, ctypes.c_void_p(out.data_ptr()), self.nbytes))
         return out
 
+    def download(self, out):
+        """Stream-ordered copy into the host tensor ``out`` (pinned for an
+        asynchronous copy); the data is there after ``sync()``."""
+        N.check(N.lib.sv_download(self.h, ctypes.c_void_p(out.data_ptr()), self.nbytes))
+        return out
+
     def apply(self, plan: Plan, gatewise=False, sync=False, tc=False):
         flags = ((N.SV_FLAG_GATEWISE if gatewise else 0) | (N.SV_FLAG_SYNC if sync else 0)
                  | (N.SV_FLAG_TC_DENSE if tc else 0))

@@ -135,6 +135,13 @@ sv_status sv_copy_state(sv_state *s, void *dst, size_t bytes) {
     return SV_OK;
 }
 
+sv_status sv_download(sv_state *s, void *dst, size_t bytes) {
+    if (!s || !dst) return fail(SV_ERR_ARG, "NULL argument");
+    if (bytes != s->bytes) return fail(SV_ERR_ARG, "bytes must equal the state size");
+    CUDA_TRY(cudaMemcpyAsync(dst, s->buf, bytes, cudaMemcpyDeviceToHost, s->stream));
+    return SV_OK;
+}
+
 sv_status sv_device_ptr(sv_state *s, void **ptr, size_t *bytes) {
     if (!s) return fail(SV_ERR_ARG, "state is NULL");
     if (ptr) *ptr = s->buf;

@@ -194,3 +194,23 @@ def test_fused_one_qubit_runs(precision, method):
     ref = sim.run(n, g, psi)
     out = run_gpu(n, g, method=method, k=8, psi=psi, precision=precision)
     assert max_abs(out, ref) <= TOL[precision]
+
+
+def test_download_stream_ordered():
+    """sv_download queues the copy on the state's stream; after sv_sync the
+    host buffer holds the state, also with a part pass queued before it."""
+    _, api = native()
+    n = 14
+    psi = random_state(n, 91)
+    g = synth.plain_layered_14q()[1][:60]
+    ref = sim.run(n, g, psi)
+    plan = api.Plan(g, n, "dagp", 8)
+    st = api.State(n, "c64", stream=torch.cuda.Stream())
+    st.upload(torch.from_numpy(psi).to(torch.complex64).pin_memory())
+    st.apply(plan)
+    out = torch.empty(1 << n, dtype=torch.complex64).pin_memory()
+    st.download(out)
+    st.sync()
+    assert max_abs(out.numpy().astype(np.complex128), ref) <= TOL["c64"]
+    st.close()
+    plan.close()
