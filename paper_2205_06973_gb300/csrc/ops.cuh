@@ -277,6 +277,10 @@ __device__ __forceinline__ void run_ops(typename CT<Real>::T (&a)[1 << R], const
                 tpi = x * di + y * dr;
             }
             break;
+        case OP_DIAG:
+#pragma unroll
+            for (int i = 0; i < NR; i++) cmul_in(a[i], cf[2 * i], cf[2 * i + 1]);
+            break;
         case OP_TAPPLY:
 #pragma unroll
             for (int i = 0; i < NR; i++) cmul_in(a[i], tpr, tpi);

@@ -462,6 +462,78 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
             for (int q : pend_order)
                 if (!flush(q)) return false;
             // the last phase's per-thread phase is applied with the part factor at the store
+            // Diagonal gates on register bits commute with each other and with
+            // every op on other register bits: a run of them (interleaved with
+            // such ops) merges into one OP_DIAG holding the product's phase for
+            // each of the 2^R register indices. The run ends where an op acts
+            // non-diagonally on a register bit the product depends on.
+            {
+                const int NR = 1 << R;
+                std::vector<Op> in(prog.ops.begin() + ph.op_begin, prog.ops.end());
+                prog.ops.resize(ph.op_begin);
+                std::vector<double> D(2 * NR);
+                uint32_t dep = 0;
+                int merged = 0;
+                Op single{};
+                auto reset = [&]() {
+                    for (int i = 0; i < NR; i++) { D[2 * i] = 1.0; D[2 * i + 1] = 0.0; }
+                    dep = 0;
+                    merged = 0;
+                };
+                auto mulphase = [&](int i, double pr, double pi) {
+                    const double x = D[2 * i], y = D[2 * i + 1];
+                    D[2 * i] = x * pr - y * pi;
+                    D[2 * i + 1] = x * pi + y * pr;
+                };
+                auto flush = [&]() {
+                    if (merged == 1) prog.ops.push_back(single);
+                    else if (merged > 1) {
+                        Op op{};
+                        op.kind = OP_DIAG;
+                        op.coef = (uint32_t)prog.coefs.size();
+                        prog.coefs.insert(prog.coefs.end(), D.begin(), D.end());
+                        prog.ops.push_back(op);
+                    }
+                    reset();
+                };
+                reset();
+                for (const Op &op : in) {
+                    const double *c = prog.coefs.data() + op.coef;
+                    bool diag = true;
+                    switch (op.kind) {
+                    case OP_P: for (int i = 0; i < NR; i++) if ((i >> op.a) & 1) mulphase(i, c[0], c[1]); break;
+                    case OP_Z: for (int i = 0; i < NR; i++) if ((i >> op.a) & 1) mulphase(i, -1.0, 0.0); break;
+                    case OP_D:
+                        for (int i = 0; i < NR; i++) mulphase(i, (i >> op.a) & 1 ? c[2] : c[0], (i >> op.a) & 1 ? c[3] : c[1]);
+                        break;
+                    case OP_CZ:
+                        for (int i = 0; i < NR; i++) if (((i >> op.a) & 1) && ((i >> op.b) & 1)) mulphase(i, -1.0, 0.0);
+                        break;
+                    case OP_CP:
+                        for (int i = 0; i < NR; i++) if (((i >> op.a) & 1) && ((i >> op.b) & 1)) mulphase(i, c[0], c[1]);
+                        break;
+                    default: diag = false; break;
+                    }
+                    if (diag) {
+                        dep |= 1u << op.a;
+                        if (op.kind == OP_CZ || op.kind == OP_CP) dep |= 1u << op.b;
+                        merged++;
+                        single = op;
+                        continue;
+                    }
+                    // register bits the op acts on non-diagonally
+                    uint32_t touch = 0;
+                    switch (op.kind) {
+                    case OP_H: case OP_U2: case OP_RX: case OP_RY: case OP_X: case OP_Y: touch = 1u << op.a; break;
+                    case OP_CX: touch = (1u << op.a) | (1u << op.b); break;
+                    case OP_CXT: touch = 1u << op.b; break;
+                    default: touch = 0; break;   // thread-bit phases: diagonal, they commute
+                    }
+                    if (touch & dep) flush();
+                    prog.ops.push_back(op);
+                }
+                flush();
+            }
             if (tphase && !last) emit(OP_TAPPLY, 0, 0, 0, 0);
             if (last) last_tphase = tphase;
             ph.op_count = (uint32_t)prog.ops.size() - ph.op_begin;

@@ -37,6 +37,7 @@ enum OpKind : uint8_t {
     OP_TD,       // tb; coef: d0, d1: per-thread phase *= (bit ? d1 : d0)
     OP_TP2,      // tb, b = second thread bit; coef: d: per-thread phase *= d if both set
     OP_TAPPLY,   // multiply the thread's amplitudes by its phase, reset the phase to 1
+    OP_DIAG,     // coef: 2^R phases (re, im): register amplitude i *= phase i (merged diagonal gates)
     OP_COUNT
 };
 
