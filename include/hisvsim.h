@@ -204,6 +204,12 @@ sv_status sv_batch_state(sv_batch *b, uint32_t i, void **dev_ptr, size_t *bytes)
 sv_status sv_batch_copy_state(sv_batch *b, uint32_t i, void *host_dst, size_t bytes);
 sv_status sv_batch_info(sv_batch *b, uint64_t *total_amplitudes, uint32_t *n_items, uint32_t *n_parts);
 sv_status sv_batch_sync(sv_batch *b);
+/* Testing the failure path (no GPU fault involved): with on != 0 the last
+ * work item waits for a tile count its circuit never reaches, so its bounded
+ * wait gives up (about a second), the kernel records the error and ends, and
+ * the run reports SV_ERR_TIMEOUT at the next synchronising call; the batch
+ * stays usable. on = 0 restores the normal work list. Rebuilds the program. */
+sv_status sv_batch_hold_last_item(sv_batch *b, int on);
 sv_status sv_batch_destroy(sv_batch *b);
 
 /* ------------------------------------------------- allocation-free probs ---

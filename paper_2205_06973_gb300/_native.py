@@ -55,6 +55,7 @@ _SIGS = {
     "sv_upload": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "sv_copy_state": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "sv_download": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
+    "sv_batch_hold_last_item": ([_vp, ctypes.c_int], ctypes.c_int),
     "sv_device_ptr": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "sv_sync": ([_vp], ctypes.c_int),
     "sv_set_tile": ([_vp, ctypes.c_int], ctypes.c_int),

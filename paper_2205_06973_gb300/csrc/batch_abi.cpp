@@ -34,6 +34,7 @@ struct sv_batch {
     bool own_stream = false;
     int warps = 8;                       // warps per CTA
     int chunk = 16;                      // tiles per queue item
+    bool hold_last = false;              // testing: the last item waits for tiles that never complete
     // device
     float2 *sv = nullptr;
     uint64_t *d_off = nullptr;
@@ -181,6 +182,7 @@ static sv_status build_program(sv_batch *b) {
                 items.push_back(it);
             }
         }
+    if (b->hold_last && !items.empty()) items.back().wait = 0xFFFFFFFFu;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t s_items = al(items.size() * sizeof(BatchItem)), s_parts = al(parts.size() * sizeof(PartLaunch));
     const size_t s_ph = al(phases.size() * sizeof(Phase)), s_op = al(ops.size() * sizeof(Op));
@@ -254,6 +256,13 @@ sv_status sv_batch_run(sv_batch *b, uint32_t flags) {
     }
     BCUDA(cudaGraphLaunch(b->gexec, b->stream));
     if (flags & SV_FLAG_SYNC) return batch_check(b);
+    return SV_OK;
+}
+
+sv_status sv_batch_hold_last_item(sv_batch *b, int on) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    b->hold_last = on != 0;
+    drop_program(b);
     return SV_OK;
 }
 

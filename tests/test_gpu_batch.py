@@ -76,3 +76,28 @@ def test_batch_configurations(warps, chunk):
     _, norms = b.probs()
     assert np.abs(norms - 1.0).max() == 0.0
     b.close()
+
+
+def test_batch_bounded_wait_reports_timeout_and_recovers():
+    """The failure path of the batched kernel without a GPU fault: an item
+    whose dependency never completes (planted with sv_batch_hold_last_item)
+    gives up its bounded wait, the run reports SV_ERR_TIMEOUT, and the same
+    batch then runs correctly once the hold is lifted."""
+    import time
+    N, _ = native()
+    from paper_2205_06973_gb300.batch import Batch
+    circs = _circuits(4, start=200)
+    b = Batch(circs, method="dfs", k=9)
+    N.check(N.lib.sv_batch_hold_last_item(b.h, 1))
+    t0 = time.perf_counter()
+    with pytest.raises(N.SvError) as e:
+        b.run(sync=True)
+    assert e.value.status == N.SV_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    N.check(N.lib.sv_batch_hold_last_item(b.h, 0))
+    b.reset()
+    b.run(sync=True)
+    for i, (n, g) in enumerate(circs):
+        out = b.state_host(i).numpy().astype(np.complex128)
+        assert np.abs(out - sim.run(n, g)).max() <= 1e-5, i
+    b.close()
