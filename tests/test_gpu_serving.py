@@ -70,3 +70,35 @@ def test_budget_limits_residency():
     # the third request can only start after one of the first two finished
     assert starts[2] >= dones[0] - 1e-6
     assert stats["requests"] == 4
+
+
+def test_served_mix_fidelity():
+    """Every result of a served mix (10-24 qubits, the three families) has
+    fidelity >= 0.99999 against an FP64 reference: the CPU oracle for
+    n <= 20, the closed form for the QFT family of any size (QFT of |0...0>),
+    else the complex128 gate-list path (FP64, pinned to the oracle by the
+    parity tests)."""
+    import torch
+    from oracle import closed_form as cf
+    _, api = native()
+    from paper_2205_06973_gb300.serving import Request, Server
+    stream = _stream(32, seed=13, max_n=24)
+    reqs = [Request(i, n, g, t, fam) for i, (n, fam, g, t) in enumerate(stream)]
+    assert any(r.n > 20 for r in reqs) and any(r.family == "qft" and r.n > 20 for r in reqs)
+    res, _ = Server(keep_states=True).run(reqs)
+    for r, out in zip(reqs, res):
+        psi = out.state.numpy().astype(np.complex128)
+        if r.family == "qft":
+            ref = cf.qft_state(sim.basis(r.n))
+        elif r.n <= 20:
+            ref = sim.run(r.n, r.gates)
+        else:
+            plan = api.Plan(r.gates, r.n, "dagp", 10)
+            st = api.State(r.n, "c128")
+            st.apply(plan, sync=True)
+            ref = st.copy_to_host().numpy()
+            st.close()
+            plan.close()
+        fid = abs(np.vdot(ref, psi)) ** 2
+        assert fid >= 0.99999, (r.rid, r.n, r.family, fid)
+        assert np.abs(psi - ref).max() <= 1e-5, (r.rid, r.n, r.family)
