@@ -246,6 +246,21 @@ const char *sv_last_error(void);
 /* Library version string. */
 const char *sv_version(void);
 
+/* ----------------------------------------------------------- OpenQASM 2 ---
+ * The paper's circuits are OpenQASM 2.0 files (Sec. V); this front-end turns
+ * a program text into the gate list sv_plan_build takes.
+ * sv_qasm_parse: text = the program (NUL-terminated). Registers are laid out
+ *   one after another in declaration order (qubit index = register offset +
+ *   index). Gates outside the library's set are decomposed exactly (u2, u3,
+ *   sdg, tdg, cy, crz, crx, cry, ch, cu3, ccx, cswap, rzz; u1 = p); user gate
+ *   definitions are expanded; barrier and a final measure are ignored.
+ *   reset, if, opaque gates and gates after a measure are rejected with
+ *   SV_ERR_ARG (the message names the line). On success *out_gates is a
+ *   library-allocated array of *out_n_gates gates (free it with
+ *   sv_free_gates) and *out_n_qubits the number of qubits. Host only. */
+sv_status sv_qasm_parse(const char *text, sv_gate **out_gates, size_t *out_n_gates, int *out_n_qubits);
+void sv_free_gates(sv_gate *gates);
+
 #ifdef __cplusplus
 }
 #endif

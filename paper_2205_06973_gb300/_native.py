@@ -56,6 +56,8 @@ _SIGS = {
     "sv_copy_state": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "sv_download": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "sv_batch_hold_last_item": ([_vp, ctypes.c_int], ctypes.c_int),
+    "sv_qasm_parse": ([ctypes.c_char_p, _vp, _vp, _vp], ctypes.c_int),
+    "sv_free_gates": ([_vp], None),
     "sv_device_ptr": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "sv_sync": ([_vp], ctypes.c_int),
     "sv_set_tile": ([_vp, ctypes.c_int], ctypes.c_int),

@@ -214,3 +214,30 @@ def test_download_stream_ordered():
     assert max_abs(out.numpy().astype(np.complex128), ref) <= TOL["c64"]
     st.close()
     plan.close()
+
+
+def test_qasm_program_on_gpu():
+    """A program through the OpenQASM front-end and the CUDA path equals the
+    oracle on the same parsed gates (a QFT written with cu1, Toffolis and a
+    user gate, 12 qubits)."""
+    from paper_2205_06973_gb300 import qasm
+    n = 12
+    lines = ["OPENQASM 2.0;", 'include "qelib1.inc";', f"qreg q[{n}];", f"creg c[{n}];",
+             "gate mix(a) x, y { ry(a) x; cx x, y; u3(a/2, -a, pi/3) y; }"]
+    for j in range(n):
+        lines.append(f"h q[{j}];")
+        for m in range(1, n - j):
+            lines.append(f"cu1(pi/2^{m}) q[{j + m}], q[{j}];")
+    for j in range(0, n - 2, 3):
+        lines.append(f"ccx q[{j}], q[{j + 1}], q[{j + 2}];")
+        lines.append(f"mix({0.1 * (j + 1)}) q[{j + 2}], q[{(j + 5) % n}];")
+    lines.append("measure q -> c;")
+    nq, g = qasm.loads("\n".join(lines))
+    assert nq == n
+    psi = random_state(n, 7)
+    ref = sim.run(n, g, psi)
+    for prec in ("c64", "c128"):
+        out = run_gpu(n, g, method="dagp", k=8, psi=psi, precision=prec)
+        assert max_abs(out, ref) <= TOL[prec], prec
+    out = run_gpu(n, g, method="dagp", k=6, psi=psi, tc=True)
+    assert max_abs(out, ref) <= TOL["c64"]
