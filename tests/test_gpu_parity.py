@@ -219,9 +219,9 @@ def test_download_stream_ordered():
 def test_qasm_program_on_gpu():
     """A program through the OpenQASM front-end and the CUDA path equals the
     oracle on the same parsed gates (a QFT written with cu1, Toffolis and a
-    user gate, 12 qubits)."""
+    user gate, 13 qubits: the dense path's smallest state)."""
     from paper_2205_06973_gb300 import qasm
-    n = 12
+    n = 13
     lines = ["OPENQASM 2.0;", 'include "qelib1.inc";', f"qreg q[{n}];", f"creg c[{n}];",
              "gate mix(a) x, y { ry(a) x; cx x, y; u3(a/2, -a, pi/3) y; }"]
     for j in range(n):
