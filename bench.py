@@ -357,7 +357,7 @@ def run_ours(a):
             sts[i].download(host_out[i])
         for x in sts:
             x.sync()
-        reps = 6
+        reps = 10
         barrier(ws)
         t0 = time.perf_counter()
         for i in range(reps):
