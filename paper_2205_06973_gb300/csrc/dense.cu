@@ -40,8 +40,10 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "dense.hpp"
 
@@ -455,22 +457,28 @@ void dense_a_image(const double *U, std::vector<uint8_t> &img) {
 
 cudaError_t launch_dense6(void *sv, const DenseLaunch &L, const void *a_img, uint64_t n_tiles, int *d_err,
                           double *d_norms, uint32_t dense_idx, cudaStream_t st) {
-    static uint64_t attr_set = 0;
+    // per device: shared-memory limit raised and SM count cached, once
+    // (double-checked: a thread that sees the bit sees the count)
+    static std::atomic<uint64_t> attr_set{0};
+    static std::mutex mu;
     static int sms[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 64) return cudaErrorInvalidDevice;
-    if (!((attr_set >> dev) & 1)) {
-        e = cudaFuncSetAttribute(k_dense6<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_dense6<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_dense6<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        attr_set |= 1ull << dev;
+    if (!((attr_set.load(std::memory_order_acquire) >> dev) & 1)) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!((attr_set.load(std::memory_order_relaxed) >> dev) & 1)) {
+            e = cudaFuncSetAttribute(k_dense6<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_dense6<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_dense6<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DENSE_SMEM);
+            if (e != cudaSuccess) return e;
+            e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            attr_set.fetch_or(1ull << dev, std::memory_order_release);
+        }
     }
     if (reinterpret_cast<uintptr_t>(sv) & 15) return cudaErrorMisalignedAddress;
     uint64_t grid = (uint64_t)sms[dev];

@@ -11,7 +11,9 @@
 //  k_probs / k_sum   : |a_x|^2 and the norm with FP64 accumulation.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
 
 #include "kernels.hpp"
@@ -199,23 +201,28 @@ static cudaError_t launch_part_t(void *sv, const PartLaunch &L, const Phase *pha
     const size_t smem = 2 * (sizeof(C) << T);
     // per instantiation: devices on which the shared-memory limit was raised,
     // and the resident CTAs per SM found there
-    static uint64_t attr_set = 0;
+    // (set once under a lock; a thread that sees the device's bit sees its counts)
+    static std::atomic<uint64_t> attr_set{0};
+    static std::mutex mu;
     static int resident[64];
     static int sms[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 64) return cudaErrorInvalidDevice;
-    if (!((attr_set >> dev) & 1)) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, Cfg::NT, smem);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        resident[dev] = nb < 1 ? 1 : nb;
-        attr_set |= 1ull << dev;
+    if (!((attr_set.load(std::memory_order_acquire) >> dev) & 1)) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!((attr_set.load(std::memory_order_relaxed) >> dev) & 1)) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, Cfg::NT, smem);
+            if (e != cudaSuccess) return e;
+            e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            resident[dev] = nb < 1 ? 1 : nb;
+            attr_set.fetch_or(1ull << dev, std::memory_order_release);
+        }
     }
     uint64_t grid = (uint64_t)sms[dev] * resident[dev];
     if (grid > n_tiles) grid = n_tiles;
