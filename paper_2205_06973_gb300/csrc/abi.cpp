@@ -233,6 +233,7 @@ sv_status sv_plan_export(const sv_plan *p, uint32_t *pog, size_t n_gates, uint32
 }
 
 static sv_status get_host_program(sv_plan *p, bool fp64, int t, int dense, const Program **out) {
+    std::lock_guard<std::recursive_mutex> lk(p->mu);
     auto key = std::make_tuple(fp64, t, dense);
     auto it = p->host_progs.find(key);
     if (it == p->host_progs.end()) {
@@ -296,6 +297,7 @@ static void free_dev(DevProgram &d, cudaStream_t st) {
 
 static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, int dense, const Program **hp,
                                  const DevProgram **dp) {
+    std::lock_guard<std::recursive_mutex> lk(p->mu);
     const bool fp64 = is_fp64(s);
     sv_status st = get_host_program(p, fp64, t, dense, hp);
     if (st != SV_OK) return st;
@@ -347,6 +349,7 @@ static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, int dense, cons
 
 static sv_status apply_gatewise(sv_state *s, sv_plan *p) {
     const bool fp64 = is_fp64(s);
+    std::unique_lock<std::recursive_mutex> lk(p->mu);
     if (p->mats.size() != p->gates.size()) {
         p->mats.assign(p->gates.size(), {});
         for (size_t i = 0; i < p->gates.size(); i++) {
@@ -360,6 +363,7 @@ static sv_status apply_gatewise(sv_state *s, sv_plan *p) {
             }
         }
     }
+    lk.unlock();   // the matrices are complete and only read from here
     for (size_t i = 0; i < p->gates.size(); i++) {
         const GateRef &g = p->gates[i];
         cudaError_t e;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <mutex>
 #include <memory>
 #include <string>
 #include <tuple>
@@ -64,5 +65,8 @@ struct sv_plan {
     std::map<std::tuple<bool, int, int>, std::unique_ptr<Program>> host_progs;   // (fp64, t, dense)
     std::map<std::tuple<int, bool, int, int>, DevProgram> dev_progs;             // (dev, fp64, t, dense)
     std::vector<std::vector<double>> mats;                                 // gatewise matrices
+    // the caches above are filled on first use; several host threads may
+    // apply one plan (map nodes never move, so returned pointers stay valid)
+    std::recursive_mutex mu;
 };
 

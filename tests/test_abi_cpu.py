@@ -157,3 +157,16 @@ def test_partition_bit_exact_serving_requests(native, k):
         ref = pt.partition(g, n, "dagp", k)
         assert list(pog) == ref, (i - 1, fam)
         pt.check_partition(g, n, k, ref)
+
+
+def test_plan_stats_from_many_threads(native):
+    """The plan's program caches fill on first use; concurrent callers of one
+    plan get the same answer."""
+    import concurrent.futures as cf
+    n, g = synth.layered_28q(n=16, depth=10)
+    p = _plan(native, g, n, "dagp", 8)
+    with cf.ThreadPoolExecutor(8) as ex:
+        res = list(ex.map(lambda i: p.stats("c64" if i % 2 else "c128", 12, tc=bool(i % 3 == 0)), range(64)))
+    ref = {(i % 2, i % 3 == 0): r for i, r in enumerate(res)}
+    for i, r in enumerate(res):
+        assert r == ref[(i % 2, i % 3 == 0)]
