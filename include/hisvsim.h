@@ -127,7 +127,11 @@ sv_status sv_set_tile(sv_state *s, int tile_qubits);
  * Parts are numbered in execution order: Kahn order of the part graph, ties to
  * the part holding the smallest gate index; gates of a part keep their order.
  * Returns SV_ERR_PARTITION if a gate has more than k qubits, SV_ERR_ARG for a
- * bad kind, arity, repeated or out-of-range qubit. */
+ * bad kind, arity, repeated or out-of-range qubit.
+ * Threads: a plan may be applied to several states, from several host
+ * threads at once (its compiled programs are built once, under a lock); a
+ * state is used from one host thread at a time; sv_plan_destroy needs every
+ * apply of the plan to have completed on the device. */
 sv_status sv_plan_build(const sv_gate *gates, size_t n_gates, int n_qubits, sv_method m, int k,
                         uint64_t seed, int dfs_trials, sv_plan **out);
 /* Copy the partition out: part_of_gate[n_gates] (may be NULL) and the number
