@@ -175,17 +175,6 @@ def max_over_ranks(ws, x, device):
     return float(t.item())
 
 
-def choose_k(method, k):
-    """Part limit: explicit, else the value the tuner cache holds, else 10."""
-    if k:
-        return k
-    try:
-        from paper_2205_06973_gb300 import autotune
-        return autotune.cached_k("layered28", method, "c64") or 10
-    except Exception:
-        return 10
-
-
 def cpu_baseline_oracle(n, gates, pog, n_parts, max_parts, budget_s=20.0):
     """The oracle's Algorithm 1 mode (complex128, OpenMP on the host cores) on
     the first parts of the same plan, until about budget_s of CPU time."""
