@@ -158,3 +158,39 @@ def tune_batch(workload, circuits, method="dfs", candidates=BATCH_CANDIDATES, sa
     out["trials"] = trials
     _store(key, out)
     return out
+
+
+# Cost model of one apply, from measurements on GB300 (complex64): a part
+# pass moves 2 x 8 x 2^n bytes at ~6.3 TB/s on either kernel; the gate-list
+# kernel adds ~2.6e-13 s per interpreter op and amplitude (28-qubit layered
+# circuit at k = 10: 245 ms for 91 passes and 2420 ops; 33-qubit QFT: 1656 ms
+# for 31 passes and 475 ops).
+PASS_BYTES_PER_S = 6.3e12
+OP_S_PER_AMP = 2.6e-13
+
+
+def estimate_s(n, stats, tc):
+    """Estimated seconds of one apply of a plan with these statistics."""
+    t = stats["passes"] * 2 * 8 * (1 << n) / PASS_BYTES_PER_S
+    if not tc or stats["dense"] < stats["passes"]:
+        t += stats["ops"] * (1 << n) * OP_S_PER_AMP
+    return t
+
+
+def choose_plan(gates, n, candidates=(("dagp", 6, True), ("dagp", 10, False))):
+    """Build each candidate plan and keep the one the cost model rates
+    fastest; returns (plan, tc, estimates). The other plans are closed."""
+    from . import api
+    best = None
+    est = []
+    for method, k, tc in candidates:
+        plan = api.Plan(gates, n, method, min(k, n))
+        e = estimate_s(n, plan.stats("c64", 0, tc=tc), tc)
+        est.append({"method": method, "k": k, "tc": tc, "est_s": e})
+        if best is None or e < best[2]:
+            if best is not None:
+                best[0].close()
+            best = (plan, tc, e)
+        else:
+            plan.close()
+    return best[0], best[1], est

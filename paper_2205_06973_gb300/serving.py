@@ -13,7 +13,11 @@ a free slot. Admitted states stay on the device until their result is taken.
   them at a time, in arrival order (each pass fills the GPU, so sharing it
   among many large requests only stretches all their latencies). The batch
   stream has the higher priority, so small requests are not queued behind
-  the passes of large ones.
+  the passes of large ones. Each large request runs the plan the cost model
+  of ``autotune.choose_plan`` rates fastest: the tensor-core dense plan
+  (dagP, k = 6) or the gate-list plan (dagP, k = 10; faster for circuits made
+  mostly of diagonal gates such as the QFT). With ``tc=False`` large requests
+  use ``method_large`` / ``k_large`` on the gate-list kernel.
 
 A request's result is its probability vector summary: the norm (FP64
 accumulation on the device), the probability of |0...0> and the most likely
@@ -33,6 +37,7 @@ import numpy as np
 import torch
 
 from . import _native as N
+from . import autotune
 from .api import Plan, State
 from .batch import Batch
 
@@ -111,13 +116,17 @@ class Server:
         t0 = time.perf_counter()
         s_i = 0
         planned = {}
-        host = {"plan_wait_s": 0.0, "batch_build_s": 0.0, "batches": 0, "batched_requests": 0}
+        host = {"plan_wait_s": 0.0, "batch_build_s": 0.0, "batches": 0, "batched_requests": 0, "large_tc": 0}
 
         def now():
             return (time.perf_counter() - t0) / time_scale
 
-        def plan_future(r, method, k):
-            return self.pool.submit(Plan, r.gates, r.n, method if self.mode == "parts" else "none", min(k, r.n))
+        def plan_future(r, method, k, small):
+            if self.mode != "parts":
+                return self.pool.submit(lambda: (Plan(r.gates, r.n, "none", min(k, r.n)), False))
+            if small or not self.tc:
+                return self.pool.submit(lambda: (Plan(r.gates, r.n, method, min(k, r.n)), False))
+            return self.pool.submit(lambda: autotune.choose_plan(r.gates, r.n)[:2])
 
         while i < len(reqs) or pending or small_wait or large_wait or running_large or batch_run:
             t = now()
@@ -126,7 +135,7 @@ class Server:
                 pending.append(r)
                 small = r.n <= self.small_n and self.mode == "parts"
                 planned[r.rid] = plan_future(r, self.method_small if small else self.method_large,
-                                             self.k_small if small else self.k_large)
+                                             self.k_small if small else self.k_large, small)
                 i += 1
             # admission in arrival order
             while pending:
@@ -147,10 +156,11 @@ class Server:
                 st = State(r.n, "c64", stream=self.streams[s_i % len(self.streams)])
                 s_i += 1
                 w0 = time.perf_counter()
-                plan = planned.pop(r.rid).result()
+                plan, tc = planned.pop(r.rid).result()
                 host["plan_wait_s"] += time.perf_counter() - w0
+                host["large_tc"] += int(tc)
                 start = now()
-                st.apply(plan, gatewise=self.mode != "parts", tc=self.tc and self.mode == "parts")
+                st.apply(plan, gatewise=self.mode != "parts", tc=tc)
                 ev = torch.cuda.Event()
                 ev.record(st.stream)
                 running_large.append((r, st, plan, ev, start))
@@ -158,7 +168,7 @@ class Server:
             if batch_run is None and small_wait:
                 take, small_wait = small_wait[: self.batch_max], small_wait[self.batch_max:]
                 w0 = time.perf_counter()
-                plans = [planned.pop(r.rid).result() for r in take]
+                plans = [planned.pop(r.rid).result()[0] for r in take]
                 w1 = time.perf_counter()
                 host["plan_wait_s"] += w1 - w0
                 start = now()

@@ -170,3 +170,18 @@ def test_plan_stats_from_many_threads(native):
     ref = {(i % 2, i % 3 == 0): r for i, r in enumerate(res)}
     for i, r in enumerate(res):
         assert r == ref[(i % 2, i % 3 == 0)]
+
+
+def test_cost_model_picks_kernel_per_circuit(native):
+    """The serving cost model (host only): a QFT, mostly diagonal gates, goes
+    to the gate-list plan; a random layered circuit to the tensor-core plan."""
+    from paper_2205_06973_gb300 import autotune
+    n, g, _ = synth.qft_basis(26)
+    plan, tc, est = autotune.choose_plan(g, n)
+    assert not tc and len(est) == 2
+    plan.close()
+    n, g = synth.layered_28q(n=24, depth=30)
+    plan, tc, est = autotune.choose_plan(g, n)
+    assert tc
+    assert est[0]["est_s"] < est[1]["est_s"]
+    plan.close()
