@@ -219,6 +219,10 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
 k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const uint8_t *__restrict__ a_img,
          uint64_t n_tiles, int *__restrict__ err, double *__restrict__ dn, uint32_t dense_idx) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // the next pass on the stream may start its prologue on SMs this one has
+    // left (programmatic dependent launch); it waits for this grid before it
+    // touches the state
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     uint8_t *const base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *const sR = base;                                               // R image (B operand)
     uint64_t *const bars = reinterpret_cast<uint64_t *>(base + DENSE_A_BYTES);
@@ -245,6 +249,9 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    // the previous kernel on the stream (another pass) has completed and its
+    // writes (state, norm accumulators) are visible from here on
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
 
     // per-thread geometry shared by converters and epilogue: TMEM lane
     // quarter q and amplitude half h of the warp; column n = 32 q + lane
@@ -491,12 +498,23 @@ cudaError_t launch_dense6(void *sv, const DenseLaunch &L, const void *a_img, uin
     const bool a32 = (reinterpret_cast<uintptr_t>(sv) & 31) == 0;
     float2 *const p = reinterpret_cast<float2 *>(sv);
     const uint8_t *const a = reinterpret_cast<const uint8_t *>(a_img);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(DENSE_THREADS);
+    cfg.dynamicSmemBytes = DENSE_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (z >= 2 && a32)
-        k_dense6<4><<<(unsigned)grid, DENSE_THREADS, DENSE_SMEM, st>>>(p, L, a, n_tiles, d_err, d_norms, dense_idx);
+        e = cudaLaunchKernelEx(&cfg, k_dense6<4>, p, L, a, n_tiles, d_err, d_norms, dense_idx);
     else if (z >= 1)
-        k_dense6<2><<<(unsigned)grid, DENSE_THREADS, DENSE_SMEM, st>>>(p, L, a, n_tiles, d_err, d_norms, dense_idx);
+        e = cudaLaunchKernelEx(&cfg, k_dense6<2>, p, L, a, n_tiles, d_err, d_norms, dense_idx);
     else
-        k_dense6<1><<<(unsigned)grid, DENSE_THREADS, DENSE_SMEM, st>>>(p, L, a, n_tiles, d_err, d_norms, dense_idx);
+        e = cudaLaunchKernelEx(&cfg, k_dense6<1>, p, L, a, n_tiles, d_err, d_norms, dense_idx);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
