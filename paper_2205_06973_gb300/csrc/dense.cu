@@ -219,10 +219,6 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1)
 k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const uint8_t *__restrict__ a_img,
          uint64_t n_tiles, int *__restrict__ err, double *__restrict__ dn, uint32_t dense_idx) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    // the next pass on the stream may start its prologue on SMs this one has
-    // left (programmatic dependent launch); it waits for this grid before it
-    // touches the state
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     uint8_t *const base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *const sR = base;                                               // R image (B operand)
     uint64_t *const bars = reinterpret_cast<uint64_t *>(base + DENSE_A_BYTES);
@@ -422,6 +418,12 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
         for (int o = 16; o > 0; o >>= 1) out_norm += __shfl_xor_sync(0xffffffffu, out_norm, o);
         if (lane == 0) atomicAdd(dn + 1 + dense_idx, out_norm);
     }
+    // the CTA's work is done: once every CTA got here, the next pass on the
+    // stream may launch and run its prologue on the SMs this one leaves
+    // (programmatic dependent launch; it waits for this grid before it
+    // touches the state). Signalling only now keeps the waiting CTAs of the
+    // next pass from occupying SMs that other streams' kernels could use.
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     __syncthreads();
     if (warp == MMA_WARP) {
         tc_fence_after();
