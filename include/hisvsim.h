@@ -194,7 +194,18 @@ sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *nor
  * sv_batch_state   device address and byte size of circuit i's state.
  * sv_batch_copy_state  copy circuit i's state (bytes = its size) to host
  *                  memory; synchronises.
- * sv_batch_info    total amplitudes, work items and parts of the built program.
+ * sv_batch_info    total amplitudes, work items and parts of the built
+ *                  program's gate-list kernel.
+ * sv_batch_set_dense  (Algorithm 1, Sec. III-C, with the execute step of a
+ *                  part as one fused unitary) min_qubits > 0: every circuit of at least
+ *                  max(min_qubits, 13) qubits whose plan has parts of at most
+ *                  6 qubits runs on the batched tensor-core kernel, one
+ *                  64x64 split-BF16 pass per part (the k_dense6 arithmetic);
+ *                  its output is renormalised to unit norm after every pass
+ *                  (the states start in |0...0>). tiles_per_item: tiles of
+ *                  2^13 amplitudes per work item (0 = default 4). 0 turns it
+ *                  off (the default). Rebuilds the program.
+ * sv_batch_dense_info  circuits, work items and passes on the dense kernel.
  * sv_batch_sync    synchronise and report device errors.
  * sv_batch_destroy free everything the batch allocated. */
 typedef struct sv_batch sv_batch;
@@ -208,6 +219,8 @@ sv_status sv_batch_state(sv_batch *b, uint32_t i, void **dev_ptr, size_t *bytes)
 sv_status sv_batch_copy_state(sv_batch *b, uint32_t i, void *host_dst, size_t bytes);
 sv_status sv_batch_info(sv_batch *b, uint64_t *total_amplitudes, uint32_t *n_items, uint32_t *n_parts);
 sv_status sv_batch_sync(sv_batch *b);
+sv_status sv_batch_set_dense(sv_batch *b, int min_qubits, int tiles_per_item);
+sv_status sv_batch_dense_info(sv_batch *b, uint32_t *n_circuits, uint32_t *n_items, uint32_t *n_passes);
 /* Testing the failure path (no GPU fault involved): with on != 0 the last
  * work item waits for a tile count its circuit never reaches, so its bounded
  * wait gives up (about a second), the kernel records the error and ends, and

@@ -19,9 +19,12 @@ from .api import Plan
 
 class Batch:
     def __init__(self, circuits, method="dfs", k=9, warps_per_cta=0, tiles_per_item=0, stream=None,
-                 plans=None):
+                 plans=None, dense_min_qubits=0, dense_tiles_per_item=0):
         """circuits: list of (n_qubits, gates); or plans: list of built Plan
-        objects (the batch then owns them)."""
+        objects (the batch then owns them). dense_min_qubits > 0: circuits of
+        at least max(dense_min_qubits, 13) qubits are planned with parts of at
+        most 6 qubits and run on the batched tensor-core kernel (one fused
+        64x64 unitary per part); the others keep k and the gate-list kernel."""
         if plans is not None:
             circuits = [(p.n, None) for p in plans]
         self.n = len(circuits)
@@ -35,12 +38,19 @@ class Batch:
         self.h = h
         if plans is None:   # the partitioners run in C++ with the GIL released: plan in parallel
             with cf.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
-                plans = list(ex.map(lambda c: Plan(c[1], c[0], method, min(k, c[0])), circuits))
+                dmin = max(dense_min_qubits, 13) if dense_min_qubits else 0
+
+                def plan(c):
+                    kk = 6 if dmin and c[0] >= dmin else k
+                    return Plan(c[1], c[0], method, min(kk, c[0]))
+                plans = list(ex.map(plan, circuits))
         self.plans = plans
         for i, p in enumerate(self.plans):
             N.check(N.lib.sv_batch_set_plan(self.h, i, p.h))
         if warps_per_cta or tiles_per_item:
             N.check(N.lib.sv_batch_config(self.h, warps_per_cta, tiles_per_item))
+        if dense_min_qubits:
+            N.check(N.lib.sv_batch_set_dense(self.h, dense_min_qubits, dense_tiles_per_item))
 
     @classmethod
     def from_plans(cls, items, stream=None, warps_per_cta=0, tiles_per_item=0):
@@ -79,7 +89,10 @@ class Batch:
     def info(self):
         t, it, pa = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
         N.check(N.lib.sv_batch_info(self.h, ctypes.byref(t), ctypes.byref(it), ctypes.byref(pa)))
-        return {"amplitudes": t.value, "items": it.value, "parts": pa.value}
+        dc, di, dp = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        N.check(N.lib.sv_batch_dense_info(self.h, ctypes.byref(dc), ctypes.byref(di), ctypes.byref(dp)))
+        return {"amplitudes": t.value, "items": it.value, "parts": pa.value,
+                "dense_circuits": dc.value, "dense_items": di.value, "dense_passes": dp.value}
 
     def close(self):
         if getattr(self, "h", None):

@@ -2,12 +2,16 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "abi_internal.hpp"
 #include "batch.hpp"
+#include "dense_batch.hpp"
+#include "planner.hpp"
 
 using namespace hisv;
 
@@ -35,11 +39,14 @@ struct sv_batch {
     int warps = 8;                       // warps per CTA
     int chunk = 16;                      // tiles per queue item
     bool hold_last = false;              // testing: the last item waits for tiles that never complete
+    int dense_min = 0;                   // circuits of >= this many qubits (and >= 13) with parts of <= 6
+                                         // qubits run on the batched tensor-core kernel; 0 = off
+    int dense_chunk = 4;                 // tiles (2^13 amplitudes) per dense work item
     // device
     float2 *sv = nullptr;
     uint64_t *d_off = nullptr;
     uint32_t *d_nq = nullptr;
-    uint32_t *d_done = nullptr;          // n counters + 1 queue ticket
+    uint32_t *d_done = nullptr;          // n counters + the two queue tickets (gate lists, dense)
     int *d_err = nullptr;
     double *d_norms = nullptr;
     std::vector<double> h_norms;
@@ -48,6 +55,8 @@ struct sv_batch {
     BatchLaunch launch{};
     void *d_prog = nullptr;              // one allocation: items, parts, phases, ops, coefs
     uint32_t n_items = 0, n_parts = 0;
+    void *d_dprog = nullptr;             // one allocation: dense items, parts, R images, norm slots
+    uint32_t n_dense_items = 0, n_dense_parts = 0, n_dense_circ = 0;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
 };
@@ -58,7 +67,10 @@ static void drop_program(sv_batch *b) {
     b->gexec = nullptr;
     b->graph = nullptr;
     dev_free(b->d_prog, b->stream);   // after the launches already queued on the stream
+    dev_free(b->d_dprog, b->stream);
     b->d_prog = nullptr;
+    b->d_dprog = nullptr;
+    b->n_items = b->n_parts = b->n_dense_items = b->n_dense_parts = b->n_dense_circ = 0;
     b->built = false;
 }
 
@@ -89,7 +101,7 @@ sv_status sv_batch_create(uint32_t n_circuits, const int *n_qubits, void *stream
     cudaError_t e = dev_alloc(reinterpret_cast<void **>(&b->sv), sizeof(float2) * b->total, st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_off), sizeof(uint64_t) * n_circuits, st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_nq), sizeof(uint32_t) * n_circuits, st);
-    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_done), sizeof(uint32_t) * (n_circuits + 1), st);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_done), sizeof(uint32_t) * (n_circuits + 2), st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_err), sizeof(int), st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_norms), sizeof(double) * n_circuits, st);
     if (e != cudaSuccess) {
@@ -131,7 +143,134 @@ sv_status sv_batch_config(sv_batch *b, int warps_per_cta, int tiles_per_item) {
     return SV_OK;
 }
 
+// The dense circuits: the dense kernel is on, the circuit has enough qubits
+// and its plan's parts have at most 6 qubits, so the planner makes every
+// part a dense tensor-core pass. One DenseBatchPart and one R image per pass,
+// work items of dense_chunk tiles in wave order, one norm slot per pass.
+// Worker threads compile the circuits on all host cores; a dense circuit's R
+// images go straight to their place on the device (a batch of thousands of
+// circuits has hundreds of thousands of passes, 64 KiB of image each).
+struct DenseLayout {
+    std::vector<char> dense;             // per circuit
+    std::vector<uint32_t> base, npass;   // first pass, passes per circuit
+    uint32_t n_parts = 0, n_circ = 0;
+    std::vector<DenseBatchItem> items;
+    size_t s_items = 0, s_parts = 0, s_img = 0, s_dn = 0;
+};
+
+static void dense_layout(sv_batch *b, DenseLayout &D) {
+    D.dense.assign(b->n, 0);
+    D.base.assign(b->n, 0);
+    D.npass.assign(b->n, 0);
+    const int dmin = std::max(b->dense_min, DENSE_K + DENSE_COLS);
+    uint32_t maxP = 0;
+    for (uint32_t c = 0; c < b->n; c++) {
+        const sv_plan *p = b->plans[c];
+        if (b->dense_min <= 0 || p->n < dmin || p->max_part > DENSE_K) continue;
+        D.dense[c] = 1;
+        D.base[c] = D.n_parts;
+        D.npass[c] = p->n_parts;
+        D.n_parts += p->n_parts;
+        D.n_circ++;
+        maxP = std::max(maxP, p->n_parts);
+    }
+    for (uint32_t w = 0; w < maxP; w++)
+        for (uint32_t c = 0; c < b->n; c++) {
+            if (!D.dense[c] || w >= D.npass[c]) continue;
+            const uint32_t nt = 1u << (b->nq[c] - DENSE_K - DENSE_COLS);
+            for (uint32_t t0 = 0; t0 < nt; t0 += (uint32_t)b->dense_chunk) {
+                DenseBatchItem it;
+                it.part = D.base[c] + w;
+                it.tile_begin = t0;
+                it.tile_count = std::min<uint32_t>((uint32_t)b->dense_chunk, nt - t0);
+                it.wait = 4 * nt * w;   // every tile of the circuit's earlier passes, four warps each
+                D.items.push_back(it);
+            }
+        }
+    if (b->hold_last && !D.items.empty()) D.items.back().wait = 0xFFFFFFFFu;
+    auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+    D.s_items = al(D.items.size() * sizeof(DenseBatchItem));
+    D.s_parts = al((size_t)D.n_parts * sizeof(DenseBatchPart));
+    D.s_img = (size_t)D.n_parts * DENSE_A_BYTES;
+    D.s_dn = al((size_t)D.n_parts * sizeof(double));
+}
+
 static sv_status build_program(sv_batch *b) {
+    for (uint32_t c = 0; c < b->n; c++)
+        if (!b->plans[c]) return bfail(SV_ERR_ARG, "circuit " + std::to_string(c) + " has no plan");
+    DenseLayout D;
+    dense_layout(b, D);
+    char *dd = nullptr;
+    if (D.n_circ) {
+        cudaError_t e = dev_alloc(reinterpret_cast<void **>(&dd), D.s_items + D.s_parts + D.s_img + D.s_dn, b->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(SV_ERR_OOM, std::string("dense batch program: ") + cudaGetErrorString(e));
+        }
+        b->d_dprog = dd;
+        BCUDA(cudaStreamSynchronize(b->stream));   // the allocation exists before the workers copy into it
+    }
+    int dev = 0;
+    BCUDA(cudaGetDevice(&dev));
+    std::vector<Program> gl(b->n);                 // gate-list programs (circuits not on the dense kernel)
+    std::vector<DenseBatchPart> dparts(D.n_parts);
+    std::vector<std::string> errs(b->n);
+    std::atomic<uint32_t> next(0);
+    auto work = [&]() {
+        cudaSetDevice(dev);
+        for (uint32_t c = next++; c < b->n; c = next++) {
+            sv_plan *p = b->plans[c];
+            if (!D.dense[c]) {
+                if (!compile_program(p->gates, p->n, p->pog, p->n_parts, false, BATCH_TILE_QUBITS, BATCH_REG_BITS, 0,
+                                     gl[c], errs[c]) && errs[c].empty())
+                    errs[c] = "compile failed";
+                continue;
+            }
+            Program pr;
+            if (!compile_program(p->gates, p->n, p->pog, p->n_parts, false, BATCH_TILE_QUBITS, BATCH_REG_BITS, 1, pr,
+                                 errs[c])) {
+                if (errs[c].empty()) errs[c] = "compile failed";
+                continue;
+            }
+            bool all = pr.kind.size() == D.npass[c];
+            for (size_t w = 0; all && w < pr.kind.size(); w++) all = pr.kind[w] == 1 && pr.index[w] == w;
+            if (!all) {
+                errs[c] = "circuit " + std::to_string(c) + ": a part did not compile to a dense pass";
+                continue;
+            }
+            for (uint32_t w = 0; w < D.npass[c]; w++) {
+                const DenseLaunch &L = pr.dense[w];
+                DenseBatchPart &P = dparts[D.base[c] + w];
+                std::memset(&P, 0, sizeof(P));
+                P.sv_off = b->off[c];
+                P.outer_mask = L.outer_mask;
+                P.circuit = c;
+                P.dn_prev = w == 0 ? DENSE_BATCH_NO_PREV : D.base[c] + w - 1;
+                P.dn_out = D.base[c] + w;
+                std::memcpy(P.part_q, L.part_q, DENSE_K);
+                std::memcpy(P.col_q, L.col_q, DENSE_COLS);
+                P.n = (uint8_t)b->nq[c];
+            }
+            cudaError_t e = cudaMemcpy(dd + D.s_items + D.s_parts + (size_t)D.base[c] * DENSE_A_BYTES, pr.a_img.data(),
+                                       (size_t)D.npass[c] * DENSE_A_BYTES, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) errs[c] = std::string("R image upload: ") + cudaGetErrorString(e);
+        }
+    };
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = std::max(1u, std::min({nt, 32u, b->n}));
+    std::vector<std::thread> th;
+    for (unsigned k = 1; k < nt; k++) th.emplace_back(work);
+    work();
+    for (auto &t : th) t.join();
+    for (uint32_t c = 0; c < b->n; c++)
+        if (!errs[c].empty()) return bfail(SV_ERR_PARTITION, errs[c]);
+    if (D.n_circ) {
+        BCUDA(cudaMemcpy(dd, D.items.data(), D.items.size() * sizeof(DenseBatchItem), cudaMemcpyHostToDevice));
+        BCUDA(cudaMemcpy(dd + D.s_items, dparts.data(), dparts.size() * sizeof(DenseBatchPart), cudaMemcpyHostToDevice));
+        b->n_dense_items = (uint32_t)D.items.size();
+        b->n_dense_parts = D.n_parts;
+        b->n_dense_circ = D.n_circ;
+    }
     std::vector<PartLaunch> parts;
     std::vector<Phase> phases;
     std::vector<Op> ops;
@@ -139,12 +278,11 @@ static sv_status build_program(sv_batch *b) {
     std::vector<uint32_t> part_base(b->n), n_parts(b->n);
     uint32_t maxP = 0;
     for (uint32_t c = 0; c < b->n; c++) {
-        sv_plan *p = b->plans[c];
-        if (!p) return bfail(SV_ERR_ARG, "circuit " + std::to_string(c) + " has no plan");
-        Program prog;
-        std::string err;
-        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, false, BATCH_TILE_QUBITS, BATCH_REG_BITS, 0, prog, err))
-            return bfail(SV_ERR_PARTITION, err);
+        if (D.dense[c]) {
+            n_parts[c] = 0;
+            continue;
+        }
+        const Program &prog = gl[c];
         const uint32_t ph0 = (uint32_t)phases.size(), op0 = (uint32_t)ops.size(), cf0 = (uint32_t)coefs.size();
         part_base[c] = (uint32_t)parts.size();
         n_parts[c] = (uint32_t)prog.parts.size();
@@ -218,10 +356,21 @@ static sv_status build_program(sv_batch *b) {
     b->n_parts = (uint32_t)parts.size();
     int n_ctas = 0;
     BCUDA(batch_prepare(b->warps, &n_ctas));
-    // one graph: zero the tile counters and the ticket, then the persistent launch
+    // one graph: zero the tile counters, the tickets and the dense passes'
+    // norm slots, then the persistent launches (dense circuits, gate lists)
+    const size_t ds_items = D.s_items, ds_parts = D.s_parts, ds_img = D.s_img;
     BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaMemsetAsync(b->d_done, 0, sizeof(uint32_t) * (b->n + 1), b->stream);
-    if (ce == cudaSuccess) ce = launch_batch(B, b->warps, n_ctas, b->stream);
+    cudaError_t ce = cudaMemsetAsync(b->d_done, 0, sizeof(uint32_t) * (b->n + 2), b->stream);
+    if (ce == cudaSuccess && b->n_dense_items) {
+        double *dn = reinterpret_cast<double *>(dd + ds_items + ds_parts + ds_img);
+        ce = cudaMemsetAsync(dn, 0, sizeof(double) * b->n_dense_parts, b->stream);
+        if (ce == cudaSuccess)
+            ce = launch_dense6_batch(b->sv, reinterpret_cast<const DenseBatchPart *>(dd + ds_items),
+                                     reinterpret_cast<const DenseBatchItem *>(dd), b->n_dense_items,
+                                     dd + ds_items + ds_parts, b->d_done, b->d_done + b->n + 1, b->d_err, dn,
+                                     b->stream);
+    }
+    if (ce == cudaSuccess && B.n_items) ce = launch_batch(B, b->warps, n_ctas, b->stream);
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
     if (ce != cudaSuccess || ee != cudaSuccess) {
@@ -311,6 +460,24 @@ sv_status sv_batch_info(sv_batch *b, uint64_t *total_amplitudes, uint32_t *n_ite
     if (total_amplitudes) *total_amplitudes = b->total;
     if (n_items) *n_items = b->n_items;
     if (n_parts) *n_parts = b->n_parts;
+    return SV_OK;
+}
+
+sv_status sv_batch_set_dense(sv_batch *b, int min_qubits, int tiles_per_item) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    if (min_qubits < 0 || min_qubits > 30 || tiles_per_item < 0 || tiles_per_item > 4096)
+        return bfail(SV_ERR_ARG, "min_qubits in [0, 30] (0 = off), tiles_per_item in [1, 4096] (0 = default)");
+    b->dense_min = min_qubits;
+    b->dense_chunk = tiles_per_item ? tiles_per_item : 4;
+    drop_program(b);
+    return SV_OK;
+}
+
+sv_status sv_batch_dense_info(sv_batch *b, uint32_t *n_circuits, uint32_t *n_items, uint32_t *n_passes) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    if (n_circuits) *n_circuits = b->n_dense_circ;
+    if (n_items) *n_items = b->n_dense_items;
+    if (n_passes) *n_passes = b->n_dense_parts;
     return SV_OK;
 }
 

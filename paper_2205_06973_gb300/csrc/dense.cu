@@ -47,160 +47,11 @@
 #include <mutex>
 
 #include "dense.hpp"
+#include "dense_common.cuh"
 
 namespace hisv {
 
-namespace {
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
-                 ::"r"(smem_u32(slot)), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence() {
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-// One bounded poll of the barrier phase with the given parity.
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                 " selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-// Bounded wait for the phase of the given parity; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
-    for (uint32_t i = 0; i < limit; i++)
-        if (mbar_try(bar, parity)) return true;
-    return false;
-}
-// Plain arrive of this thread on an mbarrier.
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
-}
-// D[tmem] (+)= A[tmem] . B[smem desc]^T, BF16 in, FP32 accumulate.
-__device__ __forceinline__ void umma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
-                                             uint32_t accumulate) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
-                 ::"r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
-}
-// Arrive on the mbarrier once all previously issued MMAs of this thread complete.
-__device__ __forceinline__ void umma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                 ::"r"(smem_u32(bar)) : "memory");
-}
-// 32 consecutive TMEM columns of this thread's lane (32x32b shape).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                   "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
-// 16 consecutive TMEM columns of this thread's lane from registers (32x32b shape).
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-                 "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n"
-                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
-                   "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
-                   "r"(r[15])
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
-
-// W consecutive complex64 amplitudes (W = 1, 2, 4: 8, 16, 32 bytes, aligned
-// to their size), streaming (evict-first) load and store.
-template <int W>
-__device__ __forceinline__ void ld_amps(const float2 *p, float2 *x) {
-    if constexpr (W == 1) {
-        x[0] = __ldcs(p);
-    } else if constexpr (W == 2) {
-        const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
-        x[0] = make_float2(v.x, v.y);
-        x[1] = make_float2(v.z, v.w);
-    } else {
-        asm volatile("ld.global.cs.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                     : "=f"(x[0].x), "=f"(x[0].y), "=f"(x[1].x), "=f"(x[1].y), "=f"(x[2].x), "=f"(x[2].y),
-                       "=f"(x[3].x), "=f"(x[3].y)
-                     : "l"(p));
-    }
-}
-template <int W>
-__device__ __forceinline__ void st_amps(float2 *p, const float2 *y) {
-    if constexpr (W == 1) {
-        __stcs(p, y[0]);
-    } else if constexpr (W == 2) {
-        __stcs(reinterpret_cast<float4 *>(p), make_float4(y[0].x, y[0].y, y[1].x, y[1].y));
-    } else {
-        asm volatile("st.global.cs.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
-                     ::"l"(p), "f"(y[0].x), "f"(y[0].y), "f"(y[1].x), "f"(y[1].y), "f"(y[2].x), "f"(y[2].y),
-                       "f"(y[3].x), "f"(y[3].y)
-                     : "memory");
-    }
-}
-
-// Shared-memory matrix descriptor, K-major, 128-byte swizzle: start address,
-// leading byte offset (unused for this layout, 1), stride byte offset 1024
-// (between 8-row groups), descriptor version 1, layout type 2 (128B swizzle).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// Instruction descriptor of kind::f16: D format F32 (bits 4-5 = 1), A and B
-// BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// v deposited into the set bits of mask (v's bit j -> mask's j-th set bit).
-__device__ __forceinline__ uint64_t deposit_bits(uint64_t v, uint64_t mask) {
-    uint64_t out = 0;
-    while (mask) {
-        const uint64_t low = mask & (~mask + 1);
-        if (v & 1) out |= low;
-        v >>= 1;
-        mask ^= low;
-    }
-    return out;
-}
-// x + y over the bit positions of mask (x, y with bits only inside mask): the
-// carries run through the positions outside mask, which are set to one.
-__device__ __forceinline__ uint64_t masked_add(uint64_t x, uint64_t y, uint64_t mask) {
-    return ((x | ~mask) + y) & mask;
-}
-
-}  // namespace
+using namespace dense_detail;
 
 constexpr int EPI_WARPS = 4;      // one per TMEM lane quarter (warp w: quarter w)
 constexpr int CONV_WARPS = 8;     // two per TMEM lane quarter (warp 4 + w: quarter w % 4, half w / 4)

@@ -106,57 +106,85 @@ static std::vector<int> order_thread_slots(std::vector<int> cand, const std::vec
 
 void fused_unitary(const std::vector<GateRef> &gates, const std::vector<int> &ids, const int *qs, int k,
                    std::vector<double> &U) {
+    // U <- G U for each gate G in order, on the rows of the row-major 2^k x 2^k
+    // matrix (the same update on every column): pairs of rows for a one-qubit
+    // gate, quads for a two-qubit one
     const int D = 1 << k;
     U.assign((size_t)2 * D * D, 0.0);
     for (int i = 0; i < D; i++) U[2 * (D * i + i)] = 1.0;
-    std::vector<double> v(2 * D), w(2 * D);
+    double *u = U.data();
+    auto row = [&](int r) { return u + (size_t)2 * D * r; };
     for (int g : ids) {
         const GateRef &gr = gates[g];
         int loc[2] = {0, 0};
         for (int a = 0; a < gr.arity; a++)
             for (int j = 0; j < k; j++)
                 if (qs[j] == gr.q[a]) loc[a] = j;
-        double m[32];
-        if (gr.arity == 1) gate_matrix_1q(gr.kind, gr.theta, m);
-        else gate_matrix_2q(gr.kind, gr.theta, m);
-        for (int c = 0; c < D; c++) {   // column c of U is the image of basis state c
-            for (int r = 0; r < D; r++) {
-                v[2 * r] = U[2 * (D * r + c)];
-                v[2 * r + 1] = U[2 * (D * r + c) + 1];
+        if (gr.arity == 1) {
+            double m[8];
+            gate_matrix_1q(gr.kind, gr.theta, m);
+            const int s = 1 << loc[0];
+            for (int x = 0; x < D; x++) {
+                if (x & s) continue;
+                double *a = row(x), *b = row(x + s);
+                for (int c = 0; c < D; c++) {
+                    const double ar = a[2 * c], ai = a[2 * c + 1], br = b[2 * c], bi = b[2 * c + 1];
+                    a[2 * c] = m[0] * ar - m[1] * ai + m[2] * br - m[3] * bi;
+                    a[2 * c + 1] = m[0] * ai + m[1] * ar + m[2] * bi + m[3] * br;
+                    b[2 * c] = m[4] * ar - m[5] * ai + m[6] * br - m[7] * bi;
+                    b[2 * c + 1] = m[4] * ai + m[5] * ar + m[6] * bi + m[7] * br;
+                }
             }
-            w = v;
-            if (gr.arity == 1) {
-                const int s = 1 << loc[0];
-                for (int x = 0; x < D; x++) {
-                    if (x & s) continue;
-                    const double ar = v[2 * x], ai = v[2 * x + 1], br = v[2 * (x + s)], bi = v[2 * (x + s) + 1];
-                    for (int o = 0; o < 2; o++) {
-                        const double *mr = m + 4 * o;
-                        w[2 * (x + o * s)] = mr[0] * ar - mr[1] * ai + mr[2] * br - mr[3] * bi;
-                        w[2 * (x + o * s) + 1] = mr[0] * ai + mr[1] * ar + mr[2] * bi + mr[3] * br;
+            continue;
+        }
+        const int s0 = 1 << loc[0], s1 = 1 << loc[1];   // control, target
+        switch (gr.kind) {
+        case SV_GATE_CX:    // rows with the control set swap their target halves
+            for (int x = 0; x < D; x++)
+                if ((x & s0) && !(x & s1)) std::swap_ranges(row(x), row(x) + 2 * D, row(x + s1));
+            break;
+        case SV_GATE_SWAP:
+            for (int x = 0; x < D; x++)
+                if ((x & s0) && !(x & s1)) std::swap_ranges(row(x), row(x) + 2 * D, row(x - s0 + s1));
+            break;
+        case SV_GATE_CZ: case SV_GATE_CP: {
+            const double dr = gr.kind == SV_GATE_CZ ? -1.0 : std::cos(gr.theta);
+            const double di = gr.kind == SV_GATE_CZ ? 0.0 : std::sin(gr.theta);
+            for (int x = 0; x < D; x++)
+                if ((x & s0) && (x & s1)) {
+                    double *a = row(x);
+                    for (int c = 0; c < D; c++) {
+                        const double ar = a[2 * c], ai = a[2 * c + 1];
+                        a[2 * c] = ar * dr - ai * di;
+                        a[2 * c + 1] = ar * di + ai * dr;
                     }
                 }
-            } else {
-                const int s0 = 1 << loc[0], s1 = 1 << loc[1];
-                for (int x = 0; x < D; x++) {
-                    if ((x & s0) || (x & s1)) continue;
-                    const int idx[4] = {x, x + s0, x + s1, x + s0 + s1};
+        } break;
+        default: {   // any other two-qubit gate: its 4x4 matrix on quads of rows
+            double m[32];
+            gate_matrix_2q(gr.kind, gr.theta, m);
+            std::vector<double> t(8);
+            for (int x = 0; x < D; x++) {
+                if ((x & s0) || (x & s1)) continue;
+                double *rw[4] = {row(x), row(x + s0), row(x + s1), row(x + s0 + s1)};
+                for (int c = 0; c < D; c++) {
                     for (int r = 0; r < 4; r++) {
                         double re = 0, im = 0;
                         for (int cc = 0; cc < 4; cc++) {
                             const double mr = m[2 * (4 * r + cc)], mi = m[2 * (4 * r + cc) + 1];
-                            re += mr * v[2 * idx[cc]] - mi * v[2 * idx[cc] + 1];
-                            im += mr * v[2 * idx[cc] + 1] + mi * v[2 * idx[cc]];
+                            re += mr * rw[cc][2 * c] - mi * rw[cc][2 * c + 1];
+                            im += mr * rw[cc][2 * c + 1] + mi * rw[cc][2 * c];
                         }
-                        w[2 * idx[r]] = re;
-                        w[2 * idx[r] + 1] = im;
+                        t[2 * r] = re;
+                        t[2 * r + 1] = im;
+                    }
+                    for (int r = 0; r < 4; r++) {
+                        rw[r][2 * c] = t[2 * r];
+                        rw[r][2 * c + 1] = t[2 * r + 1];
                     }
                 }
             }
-            for (int r = 0; r < D; r++) {
-                U[2 * (D * r + c)] = w[2 * r];
-                U[2 * (D * r + c) + 1] = w[2 * r + 1];
-            }
+        }
         }
     }
 }

@@ -101,3 +101,106 @@ def test_batch_bounded_wait_reports_timeout_and_recovers():
         out = b.state_host(i).numpy().astype(np.complex128)
         assert np.abs(out - sim.run(n, g)).max() <= 1e-5, i
     b.close()
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _dense_mix():
+    """Circuits of 13..17 qubits for the tensor-core kernel and 10..12 for
+    the gate-list kernel, from the batch family plus a QFT and a layered
+    circuit (every gate kind of the layered generator)."""
+    circs = [c for c in _circuits(80) if 13 <= c[0] <= 17][:10]
+    circs += [c for c in _circuits(30, start=500) if c[0] <= 12][:4]
+    circs.append((14, synth.qft(14)))
+    circs.append((16, synth.layered(16, 8, seed=11)))
+    return circs
+
+
+def test_batch_dense_matches_oracle_per_circuit():
+    """Circuits of >= 13 qubits on the batched tensor-core kernel (parts of at
+    most 6 qubits as fused 64x64 unitaries, split BF16) and the rest on the
+    gate-list kernel, in one graph: every final state against the oracle
+    (max-abs 1e-5, relative L2 1e-4, fidelity 0.99999), unit norms, a
+    second run on the current states, and reset + run again."""
+    native()
+    from paper_2205_06973_gb300.batch import Batch
+    circs = _dense_mix()
+    b = Batch(circs, method="dagp", k=9, dense_min_qubits=13)
+    b.run(sync=True)
+    info = b.info()
+    n_dense = sum(1 for n, _ in circs if n >= 13)
+    assert info["dense_circuits"] == n_dense
+    assert info["dense_passes"] >= n_dense and info["dense_items"] >= info["dense_passes"]
+    refs = [sim.run(n, g) for n, g in circs]
+    _, norms = b.probs()
+    for i, (n, g) in enumerate(circs):
+        out = b.state_host(i).numpy().astype(np.complex128)
+        ref = refs[i]
+        assert np.abs(out - ref).max() <= 1e-5, i
+        assert _rel_l2(out, ref) <= 1e-4, i
+        assert abs(np.vdot(ref, out)) ** 2 >= 0.99999, i
+        assert abs(norms[i] - 1.0) <= 1e-5, i
+    b.run(sync=True)   # every circuit again, on its current state
+    for i in (0, 5, len(circs) - 1):
+        n, g = circs[i]
+        ref = sim.run(n, g, refs[i])
+        out = b.state_host(i).numpy().astype(np.complex128)
+        assert np.abs(out - ref).max() <= 1e-5, i
+    b.reset()
+    b.run(sync=True)
+    for i in (1, len(circs) - 2):
+        out = b.state_host(i).numpy().astype(np.complex128)
+        assert np.abs(out - refs[i]).max() <= 1e-5, i
+    b.close()
+
+
+@pytest.mark.parametrize("chunk", [1, 3, 64])
+def test_batch_dense_items_and_single_state_path(chunk):
+    """Work items of 1, 3 (ragged) and 64 tiles give the same states, and
+    those equal the single-state tensor-core path (sv_apply_parts with
+    SV_FLAG_TC_DENSE) on the same plan to rounding."""
+    native()
+    from paper_2205_06973_gb300 import api
+    from paper_2205_06973_gb300.batch import Batch
+    circs = [c for c in _circuits(60, start=40) if c[0] >= 15][:4]
+    circs.append((13, synth.layered(13, 10, seed=4)))
+    b = Batch(circs, method="dfs", k=9, dense_min_qubits=13, dense_tiles_per_item=chunk)
+    b.run(sync=True)
+    assert b.info()["dense_circuits"] == len(circs)
+    for i, (n, g) in enumerate(circs):
+        out = b.state_host(i).numpy()
+        st = api.State(n, "c64")
+        st.apply(b.plans[i], tc=True)
+        one = st.copy_to_host().numpy()
+        st.close()
+        assert np.abs(out - one).max() <= 1e-6, i
+        assert np.abs(out.astype(np.complex128) - sim.run(n, g)).max() <= 1e-5, i
+    b.close()
+
+
+def test_batch_dense_bounded_wait_reports_timeout_and_recovers():
+    """The tensor-core batch kernel's failure path without a GPU fault: its
+    last work item waits for a tile count that is never reached, the bounded
+    dependency wait gives up, the converters stop together, the other roles
+    drain and free the tensor memory, the run reports SV_ERR_TIMEOUT, and the
+    batch runs correctly once the hold is lifted."""
+    import time
+    N, _ = native()
+    from paper_2205_06973_gb300.batch import Batch
+    circs = [c for c in _circuits(40, start=220) if c[0] >= 13][:3]
+    b = Batch(circs, method="dfs", k=9, dense_min_qubits=13)
+    N.check(N.lib.sv_batch_hold_last_item(b.h, 1))
+    t0 = time.perf_counter()
+    with pytest.raises(N.SvError) as e:
+        b.run(sync=True)
+    assert e.value.status == N.SV_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60.0
+    N.check(N.lib.sv_batch_hold_last_item(b.h, 0))
+    b.reset()
+    b.run(sync=True)
+    for i, (n, g) in enumerate(circs):
+        out = b.state_host(i).numpy().astype(np.complex128)
+        assert np.abs(out - sim.run(n, g)).max() <= 1e-5, i
+    b.close()
