@@ -202,8 +202,11 @@ def cpu_baseline_oracle(n, gates, pog, n_parts, max_parts, budget_s=20.0):
 
 def batch_section():
     """4096 parameterised circuits (10-20 qubits, RY/RZ layers + CX ladder,
-    depth 10-50) in one persistent graph-captured launch; k, warps per CTA and
-    tiles per work item picked by the autotuner on 512 of them."""
+    depth 10-50) in one graph-captured launch pair: the circuits of >= 13
+    qubits as dense 64x64 tensor-core passes (parts of <= 6 qubits) in the
+    batched tensor-core kernel, the others on the gate-list kernel, whose k,
+    warps per CTA and tiles per work item the autotuner picks on 512 of
+    them."""
     import numpy as np
     import torch
     import synth
@@ -211,11 +214,11 @@ def batch_section():
     from paper_2205_06973_gb300.batch import Batch
     circs = synth.batch_circuits(4096)
     t0 = time.perf_counter()
-    choice = autotune.tune_batch("param4096", circs, method="dfs", use_cache=False)
+    choice = autotune.tune_batch("param4096", circs, method="dfs", use_cache=False, dense_min_qubits=13)
     tune_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     b = Batch(circs, method=choice["method"], k=choice["k"], warps_per_cta=choice["warps"],
-              tiles_per_item=choice["chunk"])
+              tiles_per_item=choice["chunk"], dense_min_qubits=13)
     plan_s = time.perf_counter() - t0
     b.run(sync=True)            # builds the work list and captures the graph
     b.reset()
@@ -239,11 +242,15 @@ def batch_section():
     info = b.info()
     b.close()
     return {"workload": "4096 parameterised circuits, 10-20 qubits (uniform), RY/RZ layers + CX ladder, "
-                        "depth 10-50, complex64, one persistent graph-captured launch",
+                        "depth 10-50, complex64, one graph: circuits of >= 13 qubits on the batched "
+                        "tensor-core kernel (DFS parts of <= 6 qubits as 64x64 split-BF16 passes, work in "
+                        "L2-sized circuit groups), the rest on the gate-list kernel",
             "circuits_per_s": round(4096 / ms * 1e3, 1), "ms_per_launch": round(ms, 2),
             "GBs": round(bytes_all / ms / 1e6, 1), "bytes_per_launch": bytes_all,
             "autotune": {k: choice[k] for k in ("method", "k", "warps", "chunk")}, "tune_s": round(tune_s, 1),
             "plan_s": round(plan_s, 1), "parts": info.get("parts"), "items": info.get("items"),
+            "dense_circuits": info.get("dense_circuits"), "dense_passes": info.get("dense_passes"),
+            "dense_items": info.get("dense_items"),
             "norm_min": float(np.min(norms)), "norm_max": float(np.max(norms))}
 
 

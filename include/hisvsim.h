@@ -203,8 +203,15 @@ sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *nor
  *                  64x64 split-BF16 pass per part (the k_dense6 arithmetic);
  *                  its output is renormalised to unit norm after every pass
  *                  (the states start in |0...0>). tiles_per_item: tiles of
- *                  2^13 amplitudes per work item (0 = default 4). 0 turns it
- *                  off (the default). Rebuilds the program.
+ *                  2^13 amplitudes per work item (0 = default 2).
+ *                  group_tiles: the dense circuits, sorted by pass count, are
+ *                  cut into groups holding about this many tiles of state
+ *                  (64 KiB each), each group's passes in wave order, group
+ *                  after group, so that a group's states can stay in L2
+ *                  between passes (0 = default 1024, 64 MiB; a value above
+ *                  the batch's total gives plain wave order).
+ *                  min_qubits = 0 turns it off (the default). Rebuilds the
+ *                  program.
  * sv_batch_dense_info  circuits, work items and passes on the dense kernel.
  * sv_batch_sync    synchronise and report device errors.
  * sv_batch_destroy free everything the batch allocated. */
@@ -219,7 +226,7 @@ sv_status sv_batch_state(sv_batch *b, uint32_t i, void **dev_ptr, size_t *bytes)
 sv_status sv_batch_copy_state(sv_batch *b, uint32_t i, void *host_dst, size_t bytes);
 sv_status sv_batch_info(sv_batch *b, uint64_t *total_amplitudes, uint32_t *n_items, uint32_t *n_parts);
 sv_status sv_batch_sync(sv_batch *b);
-sv_status sv_batch_set_dense(sv_batch *b, int min_qubits, int tiles_per_item);
+sv_status sv_batch_set_dense(sv_batch *b, int min_qubits, int tiles_per_item, int group_tiles);
 sv_status sv_batch_dense_info(sv_batch *b, uint32_t *n_circuits, uint32_t *n_items, uint32_t *n_passes);
 /* Testing the failure path (no GPU fault involved): with on != 0 the last
  * work item waits for a tile count its circuit never reaches, so its bounded

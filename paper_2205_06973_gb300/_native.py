@@ -79,7 +79,7 @@ _SIGS = {
     "sv_batch_copy_state": ([_vp, ctypes.c_uint32, _vp, ctypes.c_size_t], ctypes.c_int),
     "sv_batch_info": ([_vp, ctypes.POINTER(ctypes.c_uint64), _u32p, _u32p], ctypes.c_int),
     "sv_batch_sync": ([_vp], ctypes.c_int),
-    "sv_batch_set_dense": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "sv_batch_set_dense": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sv_batch_dense_info": ([_vp, _u32p, _u32p, _u32p], ctypes.c_int),
     "sv_batch_destroy": ([_vp], ctypes.c_int),
     "sv_last_error": ([], ctypes.c_char_p),

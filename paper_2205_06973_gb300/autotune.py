@@ -125,11 +125,14 @@ def tune_state(workload, n, gates, precision="c64", candidates=STATE_CANDIDATES,
 BATCH_CANDIDATES = tuple((k, w, c) for k in (8, 9) for w in (4, 8) for c in (2, 4, 8))
 
 
-def tune_batch(workload, circuits, method="dfs", candidates=BATCH_CANDIDATES, sample=512, use_cache=True):
+def tune_batch(workload, circuits, method="dfs", candidates=BATCH_CANDIDATES, sample=512, use_cache=True,
+               dense_min_qubits=0):
     """Fastest (k, warps per CTA, tiles per item) of the batched launch on the
-    first ``sample`` circuits."""
+    first ``sample`` circuits; with dense_min_qubits > 0 the larger circuits
+    run on the batched tensor-core kernel in the same launch and k, warps and
+    tiles apply to the others."""
     from .batch import Batch
-    key = f"batch:{workload}:c64"
+    key = f"batch:{workload}:c64:dense{dense_min_qubits}"
     if use_cache and cached(key):
         return cached(key)
     sub = circuits[:sample]
@@ -137,7 +140,7 @@ def tune_batch(workload, circuits, method="dfs", candidates=BATCH_CANDIDATES, sa
     by_k = {}
     for k, w, c in candidates:
         if k not in by_k:
-            by_k[k] = Batch(sub, method=method, k=k)
+            by_k[k] = Batch(sub, method=method, k=k, dense_min_qubits=dense_min_qubits)
         b = by_k[k]
         b.configure(w, c)
         b.run(sync=True)   # builds and captures

@@ -19,12 +19,15 @@ from .api import Plan
 
 class Batch:
     def __init__(self, circuits, method="dfs", k=9, warps_per_cta=0, tiles_per_item=0, stream=None,
-                 plans=None, dense_min_qubits=0, dense_tiles_per_item=0):
+                 plans=None, dense_min_qubits=0, dense_tiles_per_item=0, dense_group_tiles=0):
         """circuits: list of (n_qubits, gates); or plans: list of built Plan
         objects (the batch then owns them). dense_min_qubits > 0: circuits of
         at least max(dense_min_qubits, 13) qubits are planned with parts of at
         most 6 qubits and run on the batched tensor-core kernel (one fused
-        64x64 unitary per part); the others keep k and the gate-list kernel."""
+        64x64 unitary per part); the others keep k and the gate-list kernel.
+        dense_tiles_per_item / dense_group_tiles: work-item size and the size
+        of the L2-resident circuit groups of the dense work order, in 64 KiB
+        tiles (0 = defaults 2 and 1024)."""
         if plans is not None:
             circuits = [(p.n, None) for p in plans]
         self.n = len(circuits)
@@ -50,7 +53,7 @@ class Batch:
         if warps_per_cta or tiles_per_item:
             N.check(N.lib.sv_batch_config(self.h, warps_per_cta, tiles_per_item))
         if dense_min_qubits:
-            N.check(N.lib.sv_batch_set_dense(self.h, dense_min_qubits, dense_tiles_per_item))
+            N.check(N.lib.sv_batch_set_dense(self.h, dense_min_qubits, dense_tiles_per_item, dense_group_tiles))
 
     @classmethod
     def from_plans(cls, items, stream=None, warps_per_cta=0, tiles_per_item=0):

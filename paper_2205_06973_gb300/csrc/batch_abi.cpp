@@ -41,13 +41,14 @@ struct sv_batch {
     bool hold_last = false;              // testing: the last item waits for tiles that never complete
     int dense_min = 0;                   // circuits of >= this many qubits (and >= 13) with parts of <= 6
                                          // qubits run on the batched tensor-core kernel; 0 = off
-    int dense_chunk = 4;                 // tiles (2^13 amplitudes) per dense work item
+    int dense_chunk = 2;                 // tiles (2^13 amplitudes) per dense work item
+    int dense_group = 1024;              // tiles of state per group of circuits in the dense work order
     // device
     float2 *sv = nullptr;
     uint64_t *d_off = nullptr;
     uint32_t *d_nq = nullptr;
     uint32_t *d_done = nullptr;          // n counters + the two queue tickets (gate lists, dense)
-    int *d_err = nullptr;
+    int *d_err = nullptr;                // error word, then the dense kernel's record of a failed wait
     double *d_norms = nullptr;
     std::vector<double> h_norms;
     // compiled program (rebuilt when plans or the configuration change)
@@ -102,7 +103,7 @@ sv_status sv_batch_create(uint32_t n_circuits, const int *n_qubits, void *stream
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_off), sizeof(uint64_t) * n_circuits, st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_nq), sizeof(uint32_t) * n_circuits, st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_done), sizeof(uint32_t) * (n_circuits + 2), st);
-    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_err), sizeof(int), st);
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_err), sizeof(int) * DENSE_BATCH_ERR_WORDS, st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_norms), sizeof(double) * n_circuits, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -115,7 +116,7 @@ sv_status sv_batch_create(uint32_t n_circuits, const int *n_qubits, void *stream
     std::vector<uint32_t> nq32(b->nq.begin(), b->nq.end());
     BCUDA(cudaMemcpyAsync(b->d_off, b->off.data(), sizeof(uint64_t) * n_circuits, cudaMemcpyHostToDevice, b->stream));
     BCUDA(cudaMemcpyAsync(b->d_nq, nq32.data(), sizeof(uint32_t) * n_circuits, cudaMemcpyHostToDevice, b->stream));
-    BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+    BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int) * DENSE_BATCH_ERR_WORDS, b->stream));
     BCUDA(launch_batch_reset(b->sv, b->d_off, n_circuits, b->total, b->stream));
     BCUDA(cudaStreamSynchronize(b->stream));   // the host vectors above go out of scope
     *out = b.release();
@@ -163,7 +164,6 @@ static void dense_layout(sv_batch *b, DenseLayout &D) {
     D.base.assign(b->n, 0);
     D.npass.assign(b->n, 0);
     const int dmin = std::max(b->dense_min, DENSE_K + DENSE_COLS);
-    uint32_t maxP = 0;
     for (uint32_t c = 0; c < b->n; c++) {
         const sv_plan *p = b->plans[c];
         if (b->dense_min <= 0 || p->n < dmin || p->max_part > DENSE_K) continue;
@@ -172,21 +172,44 @@ static void dense_layout(sv_batch *b, DenseLayout &D) {
         D.npass[c] = p->n_parts;
         D.n_parts += p->n_parts;
         D.n_circ++;
-        maxP = std::max(maxP, p->n_parts);
     }
-    for (uint32_t w = 0; w < maxP; w++)
-        for (uint32_t c = 0; c < b->n; c++) {
-            if (!D.dense[c] || w >= D.npass[c]) continue;
-            const uint32_t nt = 1u << (b->nq[c] - DENSE_K - DENSE_COLS);
-            for (uint32_t t0 = 0; t0 < nt; t0 += (uint32_t)b->dense_chunk) {
-                DenseBatchItem it;
-                it.part = D.base[c] + w;
-                it.tile_begin = t0;
-                it.tile_count = std::min<uint32_t>((uint32_t)b->dense_chunk, nt - t0);
-                it.wait = 4 * nt * w;   // every tile of the circuit's earlier passes, four warps each
-                D.items.push_back(it);
-            }
+    // Groups of circuits whose states together hold about dense_group tiles
+    // (64 KiB each), circuits sorted by pass count so that a group's waves
+    // stay full; each group's items in wave order, one group after another.
+    // A group's states stay in L2 from one pass to the next.
+    std::vector<uint32_t> order;
+    for (uint32_t c = 0; c < b->n; c++)
+        if (D.dense[c]) order.push_back(c);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        return D.npass[x] != D.npass[y] ? D.npass[x] > D.npass[y] : b->nq[x] > b->nq[y];
+    });
+    size_t g0 = 0;
+    while (g0 < order.size()) {
+        size_t g1 = g0;
+        uint64_t tiles = 0;
+        uint32_t gP = 0;
+        while (g1 < order.size() && (g1 == g0 || tiles < (uint64_t)b->dense_group)) {
+            const uint32_t c = order[g1++];
+            tiles += 1ull << (b->nq[c] - DENSE_K - DENSE_COLS);
+            gP = std::max(gP, D.npass[c]);
         }
+        for (uint32_t w = 0; w < gP; w++)
+            for (size_t k = g0; k < g1; k++) {
+                const uint32_t c = order[k];
+                if (w >= D.npass[c]) continue;
+                const uint32_t nt = 1u << (b->nq[c] - DENSE_K - DENSE_COLS);
+                for (uint32_t t0 = 0; t0 < nt; t0 += (uint32_t)b->dense_chunk) {
+                    DenseBatchItem it{};
+                    it.part = D.base[c] + w;
+                    it.circuit = c;
+                    it.tile_begin = t0;
+                    it.tile_count = std::min<uint32_t>((uint32_t)b->dense_chunk, nt - t0);
+                    it.wait = 4 * nt * w;   // every tile of the circuit's earlier passes, four warps each
+                    D.items.push_back(it);
+                }
+            }
+        g0 = g1;
+    }
     if (b->hold_last && !D.items.empty()) D.items.back().wait = 0xFFFFFFFFu;
     auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
     D.s_items = al(D.items.size() * sizeof(DenseBatchItem));
@@ -384,12 +407,19 @@ static sv_status build_program(sv_batch *b) {
 }
 
 static sv_status batch_check(sv_batch *b) {
-    int h = 0;
-    BCUDA(cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    int h[DENSE_BATCH_ERR_WORDS] = {};
+    BCUDA(cudaMemcpyAsync(h, b->d_err, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
     BCUDA(cudaStreamSynchronize(b->stream));
-    if (h) {
-        BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
-        return bfail(SV_ERR_TIMEOUT, "a bounded wait of the batched kernel gave up");
+    if (h[0]) {
+        BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(h), b->stream));
+        std::string msg = "a bounded wait of the batched kernel gave up (wait site " + std::to_string(h[0]);
+        if (h[0] == 12) {   // the dense scheduler's dependency wait: item, circuit, target, counter seen
+            msg += "; item " + std::to_string((uint32_t)h[1]) + " circuit " + std::to_string((uint32_t)h[2]) +
+                   " waits for " + std::to_string((uint32_t)h[3]) + ", counter " + std::to_string((uint32_t)h[4]) +
+                   ", CTA " + std::to_string(h[5]) + " item #" + std::to_string(h[6]);
+        }
+        if (h[7]) msg += "; failed sites bitmask (bit 4 (site / 10 - 1) + site % 10): " + std::to_string(h[7]);
+        return bfail(SV_ERR_TIMEOUT, msg + ")");
     }
     return SV_OK;
 }
@@ -463,12 +493,14 @@ sv_status sv_batch_info(sv_batch *b, uint64_t *total_amplitudes, uint32_t *n_ite
     return SV_OK;
 }
 
-sv_status sv_batch_set_dense(sv_batch *b, int min_qubits, int tiles_per_item) {
+sv_status sv_batch_set_dense(sv_batch *b, int min_qubits, int tiles_per_item, int group_tiles) {
     if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
-    if (min_qubits < 0 || min_qubits > 30 || tiles_per_item < 0 || tiles_per_item > 4096)
-        return bfail(SV_ERR_ARG, "min_qubits in [0, 30] (0 = off), tiles_per_item in [1, 4096] (0 = default)");
+    if (min_qubits < 0 || min_qubits > 30 || tiles_per_item < 0 || tiles_per_item > 4096 || group_tiles < 0)
+        return bfail(SV_ERR_ARG, "min_qubits in [0, 30] (0 = off), tiles_per_item in [1, 4096] (0 = default), "
+                                 "group_tiles >= 0 (0 = default)");
     b->dense_min = min_qubits;
-    b->dense_chunk = tiles_per_item ? tiles_per_item : 4;
+    b->dense_chunk = tiles_per_item ? tiles_per_item : 2;
+    b->dense_group = group_tiles ? group_tiles : 1024;
     drop_program(b);
     return SV_OK;
 }

@@ -133,7 +133,8 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
         for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
             const uint32_t b = i & 1;
             // the MMAs of tile i - 2 (same A buffer) have completed
-            if (i >= 2 && !mbar_wait(&dfull[b], ((i >> 1) - 1) & 1, WAIT_LIMIT)) {
+            // warp-uniform: the tcgen05 stores below are .sync.aligned
+            if (!__all_sync(0xffffffffu, i < 2 || mbar_wait(&dfull[b], ((i >> 1) - 1) & 1, WAIT_LIMIT))) {
                 atomicExch(err, 1);
                 break;
             }
@@ -229,7 +230,7 @@ k_dense6(float2 *__restrict__ sv, const __grid_constant__ DenseLaunch L, const u
         uint32_t i = 0;
         for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, i++) {
             const uint32_t b = i & 1, u = i >> 1;
-            if (!mbar_wait(&dfull[b], u & 1, WAIT_LIMIT)) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&dfull[b], u & 1, WAIT_LIMIT))) {   // warp-uniform (tcgen05.ld)
                 atomicExch(err, 1);
                 break;
             }

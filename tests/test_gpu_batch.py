@@ -156,17 +156,19 @@ def test_batch_dense_matches_oracle_per_circuit():
     b.close()
 
 
-@pytest.mark.parametrize("chunk", [1, 3, 64])
-def test_batch_dense_items_and_single_state_path(chunk):
-    """Work items of 1, 3 (ragged) and 64 tiles give the same states, and
-    those equal the single-state tensor-core path (sv_apply_parts with
-    SV_FLAG_TC_DENSE) on the same plan to rounding."""
+@pytest.mark.parametrize("chunk,group", [(1, 1 << 30), (3, 5), (64, 1 << 30), (2, 1), (0, 0)])
+def test_batch_dense_items_and_single_state_path(chunk, group):
+    """Work items of 1, 3 (ragged) and 64 tiles, in plain wave order or in
+    circuit groups of 5 or 1 tiles of state (and the defaults), give the same
+    states, and those equal the single-state tensor-core path (sv_apply_parts
+    with SV_FLAG_TC_DENSE) on the same plan to rounding."""
     native()
     from paper_2205_06973_gb300 import api
     from paper_2205_06973_gb300.batch import Batch
     circs = [c for c in _circuits(60, start=40) if c[0] >= 15][:4]
     circs.append((13, synth.layered(13, 10, seed=4)))
-    b = Batch(circs, method="dfs", k=9, dense_min_qubits=13, dense_tiles_per_item=chunk)
+    b = Batch(circs, method="dfs", k=9, dense_min_qubits=13, dense_tiles_per_item=chunk,
+              dense_group_tiles=group)
     b.run(sync=True)
     assert b.info()["dense_circuits"] == len(circs)
     for i, (n, g) in enumerate(circs):
