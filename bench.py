@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-circuit batched launch")
+    ap.add_argument("--batch-circuits", type=int, default=4096,
+                    help="circuits of the batch section (a smaller batch for profiling)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sample")
     ap.add_argument("--oracle-report", action="store_true",
                     help="with --impl reference: time the oracle in both modes, 1 thread and all cores, on the "
@@ -65,7 +67,7 @@ def peaks():
 
 
 KERNEL_SOURCES = {
-    "k_dense6": ("dense.cu", "dense.hpp", "planner.cpp"),
+    "k_dense6": ("dense.cu", "dense.hpp", "dense_common.cuh", "planner.cpp"),
     "k_part": ("kernels.cu", "ops.cuh", "program.hpp", "planner.cpp"),
 }
 
@@ -200,7 +202,7 @@ def cpu_baseline_oracle(n, gates, pog, n_parts, max_parts, budget_s=20.0):
                       f"(32 B/amplitude per pass), {dt:.1f} s"}
 
 
-def batch_section():
+def batch_section(count=4096):
     """4096 parameterised circuits (10-20 qubits, RY/RZ layers + CX ladder,
     depth 10-50) in one graph-captured launch pair: the circuits of >= 13
     qubits as dense 64x64 tensor-core passes (parts of <= 6 qubits) in the
@@ -212,9 +214,9 @@ def batch_section():
     import synth
     from paper_2205_06973_gb300 import autotune
     from paper_2205_06973_gb300.batch import Batch
-    circs = synth.batch_circuits(4096)
+    circs = synth.batch_circuits(count)
     t0 = time.perf_counter()
-    choice = autotune.tune_batch("param4096", circs, method="dfs", use_cache=False, dense_min_qubits=13)
+    choice = autotune.tune_batch(f"param{count}", circs, method="dfs", use_cache=False, dense_min_qubits=13)
     tune_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     b = Batch(circs, method=choice["method"], k=choice["k"], warps_per_cta=choice["warps"],
@@ -241,11 +243,11 @@ def batch_section():
     _, norms = b.probs()
     info = b.info()
     b.close()
-    return {"workload": "4096 parameterised circuits, 10-20 qubits (uniform), RY/RZ layers + CX ladder, "
+    return {"workload": f"{count} parameterised circuits, 10-20 qubits (uniform), RY/RZ layers + CX ladder, "
                         "depth 10-50, complex64, one graph: circuits of >= 13 qubits on the batched "
                         "tensor-core kernel (DFS parts of <= 6 qubits as 64x64 split-BF16 passes, work in "
                         "L2-sized circuit groups), the rest on the gate-list kernel",
-            "circuits_per_s": round(4096 / ms * 1e3, 1), "ms_per_launch": round(ms, 2),
+            "circuits_per_s": round(count / ms * 1e3, 1), "ms_per_launch": round(ms, 2),
             "GBs": round(bytes_all / ms / 1e6, 1), "bytes_per_launch": bytes_all,
             "autotune": {k: choice[k] for k in ("method", "k", "warps", "chunk")}, "tune_s": round(tune_s, 1),
             "plan_s": round(plan_s, 1), "parts": info.get("parts"), "items": info.get("items"),
@@ -397,7 +399,7 @@ def run_ours(a):
 
     batch = serving = None
     if rank == 0 and not a.no_batch:
-        batch = batch_section()
+        batch = batch_section(a.batch_circuits)
     if rank == 0 and not a.no_serving:
         serving = serving_section()
 
