@@ -161,21 +161,23 @@ __device__ __forceinline__ void geometry(const DenseBatchPart &P, uint32_t n_col
 }
 
 // Converter part of one tile: 32 amplitudes of the lane's column (half h),
-// split to BF16 and written into TMEM (hi at ta, lo at ta + 64).
+// all loaded before any is converted (the loads mostly hit L2; their latency
+// bounds the kernel, so as many as possible are in flight), split to BF16 and
+// written into TMEM (hi at ta, lo at ta + 64).
 template <int W>
 __device__ __forceinline__ void convert_tile(const float2 *src, const Geo &g, uint32_t ta) {
+    float2 xa[32];
+#pragma unroll
+    for (int j = 0; j < 32; j += W) {
+        uint64_t o = 0;
+#pragma unroll
+        for (int bb = 0; bb < 5; bb++)
+            if ((j >> bb) & 1) o |= g.pbit[bb];
+        ld_amps_cg<W>(src + o, xa + j);
+    }
 #pragma unroll
     for (int gg = 0; gg < 2; gg++) {
-        float2 x[16];
-#pragma unroll
-        for (int j = 0; j < 16; j += W) {
-            const int m = 16 * gg + j;
-            uint64_t o = 0;
-#pragma unroll
-            for (int bb = 0; bb < 5; bb++)
-                if ((m >> bb) & 1) o |= g.pbit[bb];
-            ld_amps_cg<W>(src + o, x + j);
-        }
+        const float2 *x = xa + 16 * gg;
         uint32_t hi[16], lo[16];
 #pragma unroll
         for (int j = 0; j < 16; j++) {
