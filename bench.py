@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--batch-circuits", type=int, default=4096,
                     help="circuits of the batch section (a smaller batch for profiling)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sample")
+    ap.add_argument("--partition-quality", action="store_true",
+                    help="CPU only: part counts of Nat, DFS and dagP against the exact optimum on small "
+                         "circuits (one JSON line), then exit")
     ap.add_argument("--oracle-report", action="store_true",
                     help="with --impl reference: time the oracle in both modes, 1 thread and all cores, on the "
                          "configurations' workloads (bounded prefixes, scaled), one JSON line each")
@@ -533,12 +536,69 @@ def oracle_report():
         subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference"], env=env, check=True)
 
 
+def partition_quality():
+    """Part counts of the Nat, DFS and dagP builders against the exact
+    optimum (SV_PART_EXACT; the comparison Sec. V-A makes with an ILP): 54
+    small random layered circuits (6-8 qubits, depth 2-4, both gate sets, k
+    3-5) and small instances of the benchmark families (QFT, layered,
+    parameterised). One JSON line; host library only."""
+    import synth
+    from paper_2205_06973_gb300 import api
+
+    def count(g, n, m, k):
+        p = api.Plan(g, n, m, k)
+        c = p.export()[1]
+        p.close()
+        return c
+
+    def rows(cases):
+        out = []
+        for name, n, g, k in cases:
+            t0 = time.perf_counter()
+            opt = count(g, n, "exact", k)
+            r = {"case": name, "gates": len(g), "k": k, "exact": opt, "exact_s": round(time.perf_counter() - t0, 3)}
+            for m in ("nat", "dfs", "dagp"):
+                r[m] = count(g, n, m, k)
+            out.append(r)
+        return out
+
+    def summary(rs):
+        s = {}
+        for m in ("nat", "dfs", "dagp"):
+            ex = [r[m] - r["exact"] for r in rs]
+            s[m] = {"optimal": sum(e == 0 for e in ex), "of": len(rs),
+                    "mean_excess_parts": round(sum(ex) / len(ex), 3), "max_excess_parts": max(ex),
+                    "mean_ratio": round(sum(r[m] / r["exact"] for r in rs) / len(rs), 3)}
+        return s
+
+    rand = []
+    for n in (6, 7, 8):
+        for d in (2, 3, 4):
+            for two_q in (("CX",), ("CX", "CZ")):
+                for k in (3, 4, 5):
+                    seed = 1000 * n + 100 * d + 10 * len(two_q) + k
+                    rand.append((f"layered{n}d{d}{'cxcz' if len(two_q) > 1 else 'cx'}k{k}", n,
+                                 synth.layered(n, d, seed=seed, two_q=two_q), k))
+    fam = []
+    for n, k in ((6, 3), (8, 4), (10, 5), (10, 4)):
+        fam.append((f"qft{n}k{k}", n, synth.qft(n), k))
+    for n, d, k in ((8, 5, 4), (10, 5, 5), (10, 6, 5), (10, 6, 6)):
+        fam.append((f"layered{n}d{d}k{k}", n, synth.layered(n, d, seed=5), k))
+    for n, d, k in ((8, 3, 4), (10, 3, 5), (10, 4, 5), (10, 4, 6)):
+        fam.append((f"param{n}d{d}k{k}", n, synth.param(n, d, seed=4), k))
+    r1, r2 = rows(rand), rows(fam)
+    print(json.dumps({"partition_quality": {"random_small": summary(r1), "families": summary(r2),
+                                            "family_cases": r2}}))
+
+
 def main():
     if os.environ.get("HISV_ORACLE_TIMING"):
         _oracle_timing()
         return
     a = parse()
-    if a.impl == "reference" and a.oracle_report:
+    if a.partition_quality:
+        partition_quality()
+    elif a.impl == "reference" and a.oracle_report:
         oracle_report()
     elif a.impl == "reference":
         run_reference(a)

@@ -44,8 +44,12 @@ typedef enum {
 
 typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_precision;
 
-/* Part builders of Sec. IV-B; SV_PART_NONE runs gate by gate (one pass per gate). */
-typedef enum { SV_PART_NONE = 0, SV_PART_NAT = 1, SV_PART_DFS = 2, SV_PART_DAGP = 3 } sv_method;
+/* Part builders of Sec. IV-B; SV_PART_NONE runs gate by gate (one pass per gate).
+ * SV_PART_EXACT: the minimum number of parts over all acyclic partitions with
+ * L <= k (the optimum of the paper's ILP comparison, Sec. V-A), by breadth-first
+ * search over the gate DAG's down-sets; for small circuits (at most 256
+ * gates and a bounded search), SV_ERR_ARG beyond. */
+typedef enum { SV_PART_NONE = 0, SV_PART_NAT = 1, SV_PART_DFS = 2, SV_PART_DAGP = 3, SV_PART_EXACT = 4 } sv_method;
 
 /* Gate kinds. Matrices (Sec. II-A defines X, Y, Z, H; the rest are the
  * textbook conventions): RX(t) = [[c,-is],[-is,c]], RY(t) = [[c,-s],[s,c]]

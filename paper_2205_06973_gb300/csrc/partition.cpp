@@ -21,6 +21,7 @@
 #include "partition.hpp"
 
 #include <algorithm>
+#include <array>
 #include <functional>
 #include <map>
 #include <queue>
@@ -579,6 +580,117 @@ std::vector<uint32_t> part_dagp(const Dag &dag, int k) {
     std::vector<std::vector<int>> parts;
     for (int u : M.live()) parts.push_back(M.gates[u]);
     return schedule_parts(dag, parts_to_pog(dag.G, parts));
+}
+
+// ---------------------------------------------------------------- exact ---
+// Minimum number of parts over all acyclic partitions with L <= k (the
+// optimum the paper's ILP comparison measures dagP against, Sec. V-A). The
+// parts of an acyclic partition, listed in a topological order of the part
+// graph, have down-set prefixes, so a partition is a chain of down-sets and
+// the optimum is a shortest path in the lattice of down-sets. Moving a gate
+// that could join an earlier part into it never adds a part, so some optimal
+// chain has every part inclusion-maximal given its prefix; such a part is
+// fixed by its qubit set Q (|Q| = min(k, qubits used)): all gates on Q whose
+// predecessors are in the prefix or the part. Breadth-first search over the
+// down-sets with those steps; gates are in circuit order, a topological
+// order, so one ascending sweep builds a part. Circuits of at most
+// EXACT_MAX_GATES gates; the search is bounded and fails beyond it.
+namespace {
+constexpr int EXACT_MAX_GATES = 256;
+using GateSet = std::array<uint64_t, EXACT_MAX_GATES / 64>;
+inline bool has(const GateSet &s, int g) { return (s[g >> 6] >> (g & 63)) & 1; }
+inline void put(GateSet &s, int g) { s[g >> 6] |= 1ull << (g & 63); }
+}  // namespace
+
+bool part_exact(const Dag &dag, int k, std::vector<uint32_t> &pog, std::string &err) {
+    const int G = dag.G, n = dag.n;
+    if (G > EXACT_MAX_GATES) {
+        err = "exact part builder: at most " + std::to_string(EXACT_MAX_GATES) + " gates";
+        return false;
+    }
+    pog.assign(G, 0);
+    if (G == 0) return true;
+    GateSet all{};
+    for (int g = 0; g < G; g++) put(all, g);
+    // the qubit sets Q: every subset of the circuit's qubits of size min(k, used)
+    uint64_t used = 0;
+    for (int g = 0; g < G; g++) used |= dag.qmask[g];
+    std::vector<int> uq;
+    for (int q = 0; q < n; q++)
+        if ((used >> q) & 1) uq.push_back(q);
+    const int r = std::min<int>(k, (int)uq.size());
+    std::vector<uint64_t> qsets;
+    std::vector<int> pick(r);
+    for (int i = 0; i < r; i++) pick[i] = i;
+    while (true) {
+        uint64_t m = 0;
+        for (int i = 0; i < r; i++) m |= 1ull << uq[pick[i]];
+        qsets.push_back(m);
+        if (qsets.size() > (1u << 20)) {
+            err = "exact part builder: too many qubit sets";
+            return false;
+        }
+        int i = r - 1;
+        while (i >= 0 && pick[i] == (int)uq.size() - r + i) i--;
+        if (i < 0) break;
+        pick[i]++;
+        for (int j = i + 1; j < r; j++) pick[j] = pick[j - 1] + 1;
+    }
+    std::map<GateSet, GateSet> parent;   // down-set -> its predecessor on a shortest chain
+    parent[GateSet{}] = GateSet{};
+    std::vector<GateSet> level{GateSet{}};
+    uint64_t work = 0;
+    while (!level.empty() && !parent.count(all)) {
+        std::vector<GateSet> next;
+        for (const GateSet &D : level) {
+            for (uint64_t Q : qsets) {
+                work += (uint64_t)G;
+                if (work > (1ull << 32)) {
+                    err = "exact part builder: search too large for this circuit";
+                    return false;
+                }
+                GateSet E = D;
+                bool grew = false;
+                for (int g = 0; g < G; g++) {
+                    if (has(E, g) || (dag.qmask[g] & ~Q) != 0) continue;
+                    bool ready = true;
+                    for (int p : dag.preds[g])
+                        if (!has(E, p)) {
+                            ready = false;
+                            break;
+                        }
+                    if (ready) {
+                        put(E, g);
+                        grew = true;
+                    }
+                }
+                if (!grew || parent.count(E)) continue;
+                parent[E] = D;
+                next.push_back(E);
+                if (parent.size() > (1u << 22)) {
+                    err = "exact part builder: search too large for this circuit";
+                    return false;
+                }
+            }
+        }
+        level.swap(next);
+    }
+    if (!parent.count(all)) {
+        err = "exact part builder: no partition found";
+        return false;
+    }
+    std::vector<std::vector<int>> parts;
+    for (GateSet E = all; E != GateSet{};) {
+        const GateSet D = parent[E];
+        std::vector<int> part;
+        for (int g = 0; g < G; g++)
+            if (has(E, g) && !has(D, g)) part.push_back(g);
+        parts.push_back(part);
+        E = D;
+    }
+    std::reverse(parts.begin(), parts.end());
+    pog = schedule_parts(dag, parts_to_pog(G, parts));
+    return true;
 }
 
 }  // namespace hisv

@@ -35,6 +35,9 @@ bool build_dag(const std::vector<GateRef> &gates, int n, Dag &dag, std::string &
 std::vector<uint32_t> part_nat(const Dag &dag, int k);
 std::vector<uint32_t> part_dfs(const Dag &dag, int k, uint64_t seed, int trials);
 std::vector<uint32_t> part_dagp(const Dag &dag, int k);
+// The minimum number of parts (breadth-first search over down-sets); small
+// circuits only (<= 256 gates, bounded search), false with a message beyond.
+bool part_exact(const Dag &dag, int k, std::vector<uint32_t> &pog, std::string &err);
 std::vector<uint32_t> schedule_parts(const Dag &dag, const std::vector<uint32_t> &pog);
 
 }  // namespace hisv
