@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--method", default="dagp", choices=["nat", "dfs", "dagp"])
+    ap.add_argument("--method", default="dagp", choices=["nat", "dfs", "dagp", "beam"],
+                    help="part builder with --k (the reference arm's oracle has nat, dfs, dagp; beam maps to dagp)")
     ap.add_argument("--k", type=int, default=0, help="part qubit limit (0: autotuned default)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--tc", type=int, default=0, help="with --k: run parts of <= 6 qubits on the tensor cores")
@@ -304,7 +305,8 @@ def run_ours(a):
     k, tc, method = choice["k"], bool(choice["tc"]), choice["method"]
     if choice.get("tile"):
         st = api.State(n, "c64", tile=choice["tile"])
-    plan = api.Plan(gates, n, method, k)
+    from paper_2205_06973_gb300.autotune import BEAM_WIDTH
+    plan = api.Plan(gates, n, method, k, dfs_trials=BEAM_WIDTH if method == "beam" else 16)
     stats = plan.stats("c64", choice.get("tile", 0), tc=tc)
     passes = stats["passes"]
     bytes_per_pass = 2 * st.nbytes
@@ -442,7 +444,8 @@ def run_reference(a):
     # so a k = 6 pass takes ~21 s on 16 Arm cores and a k = 10 pass ~3.3 s;
     # the metric (bytes of one whole-state part pass per second) is the same
     k = a.k or 10
-    pog = np.asarray(opart.partition(gates, n, a.method, k, seed=0), dtype=np.uint32)
+    method = a.method if a.method in ("nat", "dfs", "dagp") else "dagp"
+    pog = np.asarray(opart.partition(gates, n, method, k, seed=0), dtype=np.uint32)
     P = int(pog.max()) + 1
     parts = [[g for g, s in zip(gates, pog == p) if s] for p in range(P)]
     psi = np.zeros(1 << n, dtype=np.complex128)
@@ -464,7 +467,7 @@ def run_reference(a):
     bytes_per_pass = 2 * 16 * (1 << n)
     value = bytes_per_pass / dt / 1e9
     cpu = {"value": round(value, 3), "unit": UNIT, "cores": sim.num_threads(), "kind": "oracle",
-           "sample": f"one part pass per step ({a.steps} steps) of the {a.method} k={k} plan, "
+           "sample": f"one part pass per step ({a.steps} steps) of the {method} k={k} plan, "
                      "Algorithm 1 mode, complex128"}
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,

@@ -48,8 +48,15 @@ typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_precision;
  * SV_PART_EXACT: the minimum number of parts over all acyclic partitions with
  * L <= k (the optimum of the paper's ILP comparison, Sec. V-A), by breadth-first
  * search over the gate DAG's down-sets; for small circuits (at most 256
- * gates and a bounded search), SV_ERR_ARG beyond. */
-typedef enum { SV_PART_NONE = 0, SV_PART_NAT = 1, SV_PART_DFS = 2, SV_PART_DAGP = 3, SV_PART_EXACT = 4 } sv_method;
+ * gates and a bounded search), SV_ERR_ARG beyond.
+ * SV_PART_BEAM: beam search over the same down-sets for circuits of any size
+ * (each kept prefix grows one candidate part from every available gate,
+ * adding the qubit that lets the most gates in, up to k; the widest prefixes
+ * survive); deterministic; the beam width is sv_plan_build's dfs_trials
+ * argument (<= 0: 16). */
+typedef enum {
+    SV_PART_NONE = 0, SV_PART_NAT = 1, SV_PART_DFS = 2, SV_PART_DAGP = 3, SV_PART_EXACT = 4, SV_PART_BEAM = 5
+} sv_method;
 
 /* Gate kinds. Matrices (Sec. II-A defines X, Y, Z, H; the rest are the
  * textbook conventions): RX(t) = [[c,-is],[-is,c]], RY(t) = [[c,-s],[s,c]]
@@ -127,7 +134,8 @@ sv_status sv_set_tile(sv_state *s, int tile_qubits);
  *   gates, n_gates  the circuit in execution order (copied; caller keeps ownership)
  *   n_qubits        qubits of the circuit (gate qubits must be < n_qubits)
  *   k               part qubit limit L_m (ignored for SV_PART_NONE)
- *   seed, dfs_trials  random DFS orders for SV_PART_DFS (dfs_trials <= 0: 16)
+ *   seed, dfs_trials  random DFS orders for SV_PART_DFS (dfs_trials <= 0: 16);
+ *                   for SV_PART_BEAM dfs_trials is the beam width (<= 0: 16)
  * Parts are numbered in execution order: Kahn order of the part graph, ties to
  * the part holding the smallest gate index; gates of a part keep their order.
  * Returns SV_ERR_PARTITION if a gate has more than k qubits, SV_ERR_ARG for a

@@ -14,9 +14,9 @@ LIB_PATH = os.path.join(HERE, "libhisvsim.so")
 
 SV_OK, SV_ERR_ARG, SV_ERR_OOM, SV_ERR_CUDA, SV_ERR_PARTITION, SV_ERR_TIMEOUT, SV_ERR_BUSY, SV_ERR_INTERNAL = range(8)
 SV_C64, SV_C128 = 0, 1
-SV_PART_NONE, SV_PART_NAT, SV_PART_DFS, SV_PART_DAGP, SV_PART_EXACT = 0, 1, 2, 3, 4
+SV_PART_NONE, SV_PART_NAT, SV_PART_DFS, SV_PART_DAGP, SV_PART_EXACT, SV_PART_BEAM = 0, 1, 2, 3, 4, 5
 METHODS = {"none": SV_PART_NONE, "nat": SV_PART_NAT, "dfs": SV_PART_DFS, "dagp": SV_PART_DAGP,
-           "exact": SV_PART_EXACT}
+           "exact": SV_PART_EXACT, "beam": SV_PART_BEAM}
 SV_FLAG_GATEWISE = 0x1
 SV_FLAG_SYNC = 0x2
 SV_FLAG_TC_DENSE = 0x4

@@ -69,9 +69,11 @@ def _time_apply(st, plan, tc, reps):
 
 
 STATE_CANDIDATES = (
-    ("dagp", 6, True, 0), ("dagp", 5, True, 0), ("dfs", 6, True, 0), ("dagp", 8, True, 0),
-    ("dagp", 10, False, 0), ("dagp", 12, False, 0), ("dagp", 8, False, 0),
+    ("beam", 6, True, 0), ("dagp", 6, True, 0), ("beam", 5, True, 0), ("dfs", 6, True, 0),
+    ("beam", 8, True, 0), ("beam", 10, False, 0), ("dagp", 10, False, 0), ("beam", 12, False, 0),
+    ("dagp", 8, False, 0),
 )
+BEAM_WIDTH = 64   # beam builder width for the tuned plans (0.3 s for 2520 gates)
 
 
 def tune_state(workload, n, gates, precision="c64", candidates=STATE_CANDIDATES, reps=1, state=None,
@@ -91,7 +93,7 @@ def tune_state(workload, n, gates, precision="c64", candidates=STATE_CANDIDATES,
         if k > n:
             continue
         t0 = time.perf_counter()
-        plan = api.Plan(gates, n, method, k)
+        plan = api.Plan(gates, n, method, k, dfs_trials=BEAM_WIDTH if method == "beam" else 16)
         plan_s = time.perf_counter() - t0
         try:
             if tile:

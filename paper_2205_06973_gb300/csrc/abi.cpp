@@ -180,7 +180,7 @@ sv_status sv_plan_build(const sv_gate *gates, size_t n_gates, int n, sv_method m
     *out = nullptr;
     if (n < 1 || n > 36) return fail(SV_ERR_ARG, "n_qubits must be in [1, 36]");
     if (n_gates && !gates) return fail(SV_ERR_ARG, "gates is NULL");
-    if (m < SV_PART_NONE || m > SV_PART_EXACT) return fail(SV_ERR_ARG, "bad method");
+    if (m < SV_PART_NONE || m > SV_PART_BEAM) return fail(SV_ERR_ARG, "bad method");
     std::unique_ptr<sv_plan> p(new sv_plan());
     p->n = n;
     p->method = m;
@@ -211,6 +211,7 @@ sv_status sv_plan_build(const sv_gate *gates, size_t n_gates, int n, sv_method m
         if (m == SV_PART_NAT) p->pog = part_nat(dag, k);
         else if (m == SV_PART_DFS) p->pog = part_dfs(dag, k, seed, dfs_trials);
         else if (m == SV_PART_DAGP) p->pog = part_dagp(dag, k);
+        else if (m == SV_PART_BEAM) p->pog = part_beam(dag, k, dfs_trials);
         else if (!part_exact(dag, k, p->pog, err)) return fail(SV_ERR_ARG, err);
         for (uint32_t x : p->pog) p->n_parts = std::max(p->n_parts, x + 1);
         std::vector<uint64_t> pm(p->n_parts, 0);

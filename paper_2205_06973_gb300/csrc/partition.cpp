@@ -693,4 +693,140 @@ bool part_exact(const Dag &dag, int k, std::vector<uint32_t> &pog, std::string &
     return true;
 }
 
+// ----------------------------------------------------------------- beam ---
+// Beam search over the same lattice of down-sets as the exact builder, for
+// circuits of any size: from each kept down-set D, candidate parts are grown
+// from every available gate g0: start with Q = qubits(g0) and the closure of
+// D on Q (all gates on Q whose predecessors are in D or the closure), then
+// add, while |Q| < k, the qubit of a gate blocked only by Q that makes the
+// closure largest (ties: the smaller qubit). Each level keeps the `width`
+// down-sets covering the most gates (ties: the lexicographically smaller
+// gate set); the first level that covers every gate gives the partition.
+// A greedy width of 1 already picks each part's qubit set by its gate count,
+// where dagP bisects; wider beams recover from early choices.
+std::vector<uint32_t> part_beam(const Dag &dag, int k, int width) {
+    const int G = dag.G, W = (G + 63) / 64;
+    if (G == 0) return {};
+    if (width < 1) width = 16;
+    using Bits = std::vector<uint64_t>;
+    auto in = [](const Bits &b, int g) { return (b[g >> 6] >> (g & 63)) & 1; };
+    struct Node {
+        Bits D;
+        int count;
+        int parent;
+    };
+    std::vector<Node> nodes;
+    nodes.push_back({Bits(W, 0), 0, -1});
+    std::vector<int> beam{0};
+    std::vector<uint32_t> mark(G, 0);
+    uint32_t gen = 0;
+    std::vector<int> stack, added, trial, avail;
+    // closure of D on Q, grown from the available gates: the added gates
+    // (marked with the current generation)
+    auto closure = [&](const Bits &D, uint64_t Q, std::vector<int> &out) {
+        ++gen;
+        out.clear();
+        stack.clear();
+        for (int g : avail)
+            if ((dag.qmask[g] & ~Q) == 0) stack.push_back(g);
+        while (!stack.empty()) {
+            const int g = stack.back();
+            stack.pop_back();
+            if (mark[g] == gen || (dag.qmask[g] & ~Q) != 0) continue;
+            bool ok = true;
+            for (int p : dag.preds[g])
+                if (!in(D, p) && mark[p] != gen) {
+                    ok = false;
+                    break;
+                }
+            if (!ok) continue;
+            mark[g] = gen;
+            out.push_back(g);
+            for (int t : dag.succs[g])
+                if (!in(D, t) && mark[t] != gen) stack.push_back(t);
+        }
+    };
+    int done = -1;
+    while (done < 0) {
+        // next level: candidate down-set -> (count, parent); ordered for determinism
+        std::map<Bits, std::pair<int, int>> next;
+        for (int ni : beam) {
+            const Bits D = nodes[ni].D;
+            avail.clear();
+            for (int g = 0; g < G; g++) {
+                if (in(D, g)) continue;
+                bool ok = true;
+                for (int p : dag.preds[g])
+                    if (!in(D, p)) {
+                        ok = false;
+                        break;
+                    }
+                if (ok) avail.push_back(g);
+            }
+            for (int g0 : avail) {
+                uint64_t Q = dag.qmask[g0];
+                closure(D, Q, added);
+                while (popc(Q) < k) {
+                    // qubits of the gates that only Q keeps out of the closure
+                    uint64_t cq = 0;
+                    auto consider = [&](int h) {
+                        if (in(D, h) || mark[h] == gen) return;
+                        for (int p : dag.preds[h])
+                            if (!in(D, p) && mark[p] != gen) return;
+                        cq |= dag.qmask[h];
+                    };
+                    for (int h : avail) consider(h);
+                    for (int a : added)
+                        for (int h : dag.succs[a]) consider(h);
+                    cq &= ~Q;
+                    if (!cq) break;
+                    int best_q = -1;
+                    size_t best_n = 0;
+                    for (uint64_t m = cq; m; m &= m - 1) {
+                        const int q = __builtin_ctzll(m);
+                        closure(D, Q | (1ull << q), trial);
+                        if (best_q < 0 || trial.size() > best_n) {
+                            best_q = q;
+                            best_n = trial.size();
+                        }
+                    }
+                    Q |= 1ull << best_q;
+                    closure(D, Q, added);
+                }
+                if (added.empty()) continue;
+                Bits E = D;
+                for (int g : added) E[g >> 6] |= 1ull << (g & 63);
+                const int cnt = nodes[ni].count + (int)added.size();
+                auto it = next.find(E);
+                if (it == next.end()) next.emplace(std::move(E), std::make_pair(cnt, ni));
+            }
+        }
+        // keep the `width` best: most gates, then the smaller gate set (map order)
+        std::vector<std::pair<int, const Bits *>> order;
+        for (auto &kv : next) order.push_back({kv.second.first, &kv.first});
+        std::stable_sort(order.begin(), order.end(),
+                         [](const std::pair<int, const Bits *> &a, const std::pair<int, const Bits *> &b) {
+                             return a.first > b.first;
+                         });
+        beam.clear();
+        for (size_t i = 0; i < order.size() && (int)i < width; i++) {
+            const auto &val = next[*order[i].second];
+            nodes.push_back({*order[i].second, val.first, val.second});
+            beam.push_back((int)nodes.size() - 1);
+            if (val.first == G && done < 0) done = (int)nodes.size() - 1;
+        }
+        if (beam.empty()) break;   // unreachable: some gate is always available
+    }
+    std::vector<std::vector<int>> parts;
+    for (int ni = done; ni > 0; ni = nodes[ni].parent) {
+        const Bits &E = nodes[ni].D, &D = nodes[nodes[ni].parent].D;
+        std::vector<int> part;
+        for (int g = 0; g < G; g++)
+            if (in(E, g) && !in(D, g)) part.push_back(g);
+        parts.push_back(part);
+    }
+    std::reverse(parts.begin(), parts.end());
+    return schedule_parts(dag, parts_to_pog(G, parts));
+}
+
 }  // namespace hisv

@@ -38,6 +38,9 @@ std::vector<uint32_t> part_dagp(const Dag &dag, int k);
 // The minimum number of parts (breadth-first search over down-sets); small
 // circuits only (<= 256 gates, bounded search), false with a message beyond.
 bool part_exact(const Dag &dag, int k, std::vector<uint32_t> &pog, std::string &err);
+// Beam search over down-sets with parts grown from each available gate (any
+// circuit size); width <= 0: 16.
+std::vector<uint32_t> part_beam(const Dag &dag, int k, int width);
 std::vector<uint32_t> schedule_parts(const Dag &dag, const std::vector<uint32_t> &pog);
 
 }  // namespace hisv

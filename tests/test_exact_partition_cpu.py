@@ -67,3 +67,35 @@ def test_exact_refuses_large_circuits():
     with pytest.raises(N.SvError) as e:
         api.Plan(g, 8, "exact", 4)
     assert e.value.status == N.SV_ERR_ARG
+
+
+def test_beam_builder_valid_deterministic_and_near_optimal():
+    """The beam builder (SV_PART_BEAM) gives valid acyclic partitions, the
+    same one on every call, never fewer parts than the optimum, and on the
+    small family instances at most one part more."""
+    cases = [(8, synth.qft(8), 4), (10, synth.layered(10, 6, seed=5), 5), (10, synth.param(10, 4, seed=4), 5),
+             (10, synth.qft(10), 4)]
+    for n, g, k in cases:
+        _, opt = _parts(g, n, "exact", k)
+        pog, P = _parts(g, n, "beam", k)
+        assert pt.check_partition(g, n, k, pog) == P
+        assert _parts(g, n, "beam", k) == (pog, P)
+        assert opt <= P <= opt + 1, (n, k, P, opt)
+    for seed in range(20):
+        n, k = 6, 3
+        g = _rand(n, 14, 300 + seed)
+        pog, P = _parts(g, n, "beam", k)
+        assert pt.check_partition(g, n, k, pog) == P >= pt.brute_force_min_parts(g, n, k)
+
+
+def test_beam_builder_on_the_benchmark_circuits():
+    """Fewer parts than dagP on the 28-qubit layered circuit and the 33-qubit
+    QFT (the passes of the benchmark steps), and a valid partition."""
+    n, g = synth.layered_28q()
+    p = api.Plan(g, n, "beam", 6, dfs_trials=64)
+    pog, P = p.export()
+    p.close()
+    assert pt.check_partition(g, n, 6, [int(x) for x in pog]) == P
+    assert P < _parts(g, n, "dagp", 6)[1]
+    q = synth.qft(33)
+    assert _parts(q, 33, "beam", 6)[1] < _parts(q, 33, "dagp", 6)[1]

@@ -105,6 +105,25 @@ def test_layered_20q_parts(method, k):
         assert max_abs(out, ref) <= TOL[precision]
 
 
+@pytest.mark.parametrize("k,tc", [(6, True), (8, False), (10, False)])
+def test_beam_plans(k, tc):
+    """Plans of the beam part builder (fewer passes than dagP on the
+    benchmark circuits) on the tensor-core and gate-list paths: the
+    layered recipe at 20 qubits and a QFT of a basis state at 16 qubits
+    against the oracle and the closed form."""
+    n, g = synth.layered_28q(n=20, depth=20)
+    ref = sim.run(n, g)
+    out = run_gpu(n, g, method="beam", k=k, precision="c64", tc=tc)
+    assert max_abs(out, ref) <= TOL["c64"]
+    if not tc:
+        out = run_gpu(n, g, method="beam", k=k, precision="c128")
+        assert max_abs(out, ref) <= TOL["c128"]
+    x = synth.SplitMix64(19).randint(1 << 16)
+    ref = cf.qft_basis_amplitude(16, x, np.arange(1 << 16))
+    out = run_gpu(16, synth.qft(16), method="beam", k=k, precision="c64", basis=x, tc=tc)
+    assert max_abs(out, ref) <= TOL["c64"]
+
+
 @pytest.mark.parametrize("n", [10, 14, 18])
 def test_qft_basis_closed_form(n):
     x = synth.SplitMix64(3 + n).randint(1 << n)
