@@ -209,10 +209,10 @@ def cpu_baseline_oracle(n, gates, pog, n_parts, max_parts, budget_s=20.0):
 def batch_section(count=4096):
     """4096 parameterised circuits (10-20 qubits, RY/RZ layers + CX ladder,
     depth 10-50) in one graph-captured launch pair: the circuits of >= 13
-    qubits as dense 64x64 tensor-core passes (parts of <= 6 qubits) in the
-    batched tensor-core kernel, the others on the gate-list kernel, whose k,
-    warps per CTA and tiles per work item the autotuner picks on 512 of
-    them."""
+    qubits as dense 64x64 tensor-core passes (beam-search parts of <= 6
+    qubits) in the batched tensor-core kernel, the others on the gate-list
+    kernel, whose part builder (DFS or beam), k, warps per CTA and tiles per
+    work item the autotuner picks on 512 of them."""
     import numpy as np
     import torch
     import synth
@@ -220,7 +220,8 @@ def batch_section(count=4096):
     from paper_2205_06973_gb300.batch import Batch
     circs = synth.batch_circuits(count)
     t0 = time.perf_counter()
-    choice = autotune.tune_batch(f"param{count}", circs, method="dfs", use_cache=False, dense_min_qubits=13)
+    choice = autotune.tune_batch(f"param{count}", circs, methods=("dfs", "beam"), use_cache=False,
+                                 dense_min_qubits=13)
     tune_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     b = Batch(circs, method=choice["method"], k=choice["k"], warps_per_cta=choice["warps"],
@@ -249,7 +250,7 @@ def batch_section(count=4096):
     b.close()
     return {"workload": f"{count} parameterised circuits, 10-20 qubits (uniform), RY/RZ layers + CX ladder, "
                         "depth 10-50, complex64, one graph: circuits of >= 13 qubits on the batched "
-                        "tensor-core kernel (DFS parts of <= 6 qubits as 64x64 split-BF16 passes, work in "
+                        "tensor-core kernel (beam-search parts of <= 6 qubits as 64x64 split-BF16 passes, work in "
                         "L2-sized circuit groups), the rest on the gate-list kernel",
             "circuits_per_s": round(count / ms * 1e3, 1), "ms_per_launch": round(ms, 2),
             "GBs": round(bytes_all / ms / 1e6, 1), "bytes_per_launch": bytes_all,

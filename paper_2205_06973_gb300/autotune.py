@@ -128,38 +128,41 @@ BATCH_CANDIDATES = tuple((k, w, c) for k in (8, 9) for w in (4, 8) for c in (2, 
 
 
 def tune_batch(workload, circuits, method="dfs", candidates=BATCH_CANDIDATES, sample=512, use_cache=True,
-               dense_min_qubits=0):
-    """Fastest (k, warps per CTA, tiles per item) of the batched launch on the
-    first ``sample`` circuits; with dense_min_qubits > 0 the larger circuits
-    run on the batched tensor-core kernel in the same launch and k, warps and
-    tiles apply to the others."""
+               dense_min_qubits=0, methods=None):
+    """Fastest (part builder, k, warps per CTA, tiles per item) of the batched
+    launch on the first ``sample`` circuits; ``methods`` lists the builders
+    tried for the gate-list circuits (default: just ``method``). With
+    dense_min_qubits > 0 the larger circuits run on the batched tensor-core
+    kernel in the same launch (beam-search plans) and the tuned choice
+    applies to the others."""
     from .batch import Batch
-    key = f"batch:{workload}:c64:dense{dense_min_qubits}"
+    methods = tuple(methods) if methods else (method,)
+    key = f"batch:{workload}:c64:dense{dense_min_qubits}:{'+'.join(methods)}"
     if use_cache and cached(key):
         return cached(key)
     sub = circuits[:sample]
     trials = []
-    by_k = {}
-    for k, w, c in candidates:
-        if k not in by_k:
-            by_k[k] = Batch(sub, method=method, k=k, dense_min_qubits=dense_min_qubits)
-        b = by_k[k]
-        b.configure(w, c)
-        b.run(sync=True)   # builds and captures
-        b.reset()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(b.stream)
-        b.run()
-        e1.record(b.stream)
-        e1.synchronize()
-        b.sync()
-        trials.append({"k": k, "warps": w, "chunk": c, "ms": round(e0.elapsed_time(e1), 3)})
-    for b in by_k.values():
+    built = {}
+    for m in methods:
+        for k, w, c in candidates:
+            if (m, k) not in built:
+                built[(m, k)] = Batch(sub, method=m, k=k, dense_min_qubits=dense_min_qubits)
+            b = built[(m, k)]
+            b.configure(w, c)
+            b.run(sync=True)   # builds and captures
+            b.reset()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(b.stream)
+            b.run()
+            e1.record(b.stream)
+            e1.synchronize()
+            b.sync()
+            trials.append({"method": m, "k": k, "warps": w, "chunk": c, "ms": round(e0.elapsed_time(e1), 3)})
+    for b in built.values():
         b.close()
     best = min(trials, key=lambda r: r["ms"])
     out = dict(best)
-    out["method"] = method
     out["trials"] = trials
     _store(key, out)
     return out

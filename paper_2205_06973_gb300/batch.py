@@ -19,7 +19,8 @@ from .api import Plan
 
 class Batch:
     def __init__(self, circuits, method="dfs", k=9, warps_per_cta=0, tiles_per_item=0, stream=None,
-                 plans=None, dense_min_qubits=0, dense_tiles_per_item=0, dense_group_tiles=0):
+                 plans=None, dense_min_qubits=0, dense_tiles_per_item=0, dense_group_tiles=0,
+                 dense_method="beam", dense_beam_width=4):
         """circuits: list of (n_qubits, gates); or plans: list of built Plan
         objects (the batch then owns them). dense_min_qubits > 0: circuits of
         at least max(dense_min_qubits, 13) qubits are planned with parts of at
@@ -27,7 +28,9 @@ class Batch:
         64x64 unitary per part); the others keep k and the gate-list kernel.
         dense_tiles_per_item / dense_group_tiles: work-item size and the size
         of the L2-resident circuit groups of the dense work order, in 64 KiB
-        tiles (0 = defaults 2 and 1024)."""
+        tiles (0 = defaults 2 and 1024). dense_method / dense_beam_width: the
+        part builder of the dense circuits (the beam builder halves the
+        passes of the parameterised ladder circuits against DFS)."""
         if plans is not None:
             circuits = [(p.n, None) for p in plans]
         self.n = len(circuits)
@@ -44,8 +47,9 @@ class Batch:
                 dmin = max(dense_min_qubits, 13) if dense_min_qubits else 0
 
                 def plan(c):
-                    kk = 6 if dmin and c[0] >= dmin else k
-                    return Plan(c[1], c[0], method, min(kk, c[0]))
+                    if dmin and c[0] >= dmin:
+                        return Plan(c[1], c[0], dense_method, 6, dfs_trials=dense_beam_width)
+                    return Plan(c[1], c[0], method, min(k, c[0]))
                 plans = list(ex.map(plan, circuits))
         self.plans = plans
         for i, p in enumerate(self.plans):
