@@ -185,14 +185,14 @@ def estimate_s(n, stats, tc):
     return t
 
 
-def choose_plan(gates, n, candidates=(("dagp", 6, True), ("dagp", 10, False))):
+def choose_plan(gates, n, candidates=(("beam", 6, True), ("beam", 10, False))):
     """Build each candidate plan and keep the one the cost model rates
     fastest; returns (plan, tc, estimates). The other plans are closed."""
     from . import api
     best = None
     est = []
     for method, k, tc in candidates:
-        plan = api.Plan(gates, n, method, min(k, n))
+        plan = api.Plan(gates, n, method, min(k, n), dfs_trials=16)
         e = estimate_s(n, plan.stats("c64", 0, tc=tc), tc)
         est.append({"method": method, "k": k, "tc": tc, "est_s": e})
         if best is None or e < best[2]:

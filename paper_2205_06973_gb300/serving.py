@@ -15,9 +15,11 @@ a free slot. Admitted states stay on the device until their result is taken.
   stream has the higher priority, so small requests are not queued behind
   the passes of large ones. Each large request runs the plan the cost model
   of ``autotune.choose_plan`` rates fastest: the tensor-core dense plan
-  (dagP, k = 6) or the gate-list plan (dagP, k = 10; faster for circuits made
-  mostly of diagonal gates such as the QFT). With ``tc=False`` large requests
-  use ``method_large`` / ``k_large`` on the gate-list kernel.
+  (beam-search parts, k = 6) or the gate-list plan (beam-search parts,
+  k = 10; faster for circuits made mostly of diagonal gates such as the QFT).
+  With ``tc=False`` large requests use ``method_large`` / ``k_large`` on the
+  gate-list kernel. Small requests are planned with the beam builder (k = 9,
+  width 4) by default.
 
 A request's result is its probability vector summary: the norm (FP64
 accumulation on the device), the probability of |0...0> and the most likely
@@ -77,7 +79,7 @@ def _summary(probs: torch.Tensor):
 
 class Server:
     def __init__(self, budget_bytes=170e9, max_slots=4096, small_n=20, batch_max=512, k_small=9,
-                 k_large=6, tc=True, method_small="dfs", method_large="dagp", mode="parts",
+                 k_large=6, tc=True, method_small="beam", method_large="dagp", mode="parts",
                  keep_states=False, planners=8, large_running=2):
         self.budget = float(budget_bytes)
         self.max_slots = max_slots
@@ -125,7 +127,8 @@ class Server:
             if self.mode != "parts":
                 return self.pool.submit(lambda: (Plan(r.gates, r.n, "none", min(k, r.n)), False))
             if small or not self.tc:
-                return self.pool.submit(lambda: (Plan(r.gates, r.n, method, min(k, r.n)), False))
+                return self.pool.submit(lambda: (Plan(r.gates, r.n, method, min(k, r.n),
+                                                      dfs_trials=4 if method == "beam" else 16), False))
             return self.pool.submit(lambda: autotune.choose_plan(r.gates, r.n)[:2])
 
         while i < len(reqs) or pending or small_wait or large_wait or running_large or batch_run:
