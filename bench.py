@@ -196,7 +196,8 @@ def cpu_baseline_oracle(n, gates, pog, n_parts, max_parts, budget_s=20.0):
         sub = [g for g, s in zip(gates, sel) if s]
         psi = sim.run_alg1(n, sub, [0] * len(sub), 1, psi)
         done += 1
-        if time.perf_counter() - t0 > budget_s:
+        el = time.perf_counter() - t0
+        if el + el / done > budget_s:   # the next part would end past the budget
             break
     dt = time.perf_counter() - t0
     bytes_per_pass = 2 * 16 * (1 << n)

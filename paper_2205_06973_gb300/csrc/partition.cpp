@@ -645,7 +645,7 @@ bool part_exact(const Dag &dag, int k, std::vector<uint32_t> &pog, std::string &
         for (const GateSet &D : level) {
             for (uint64_t Q : qsets) {
                 work += (uint64_t)G;
-                if (work > (1ull << 32)) {
+                if (work > (1ull << 30)) {   // about a second of host time
                     err = "exact part builder: search too large for this circuit";
                     return false;
                 }
