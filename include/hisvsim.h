@@ -51,9 +51,9 @@ typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_precision;
  * gates and a bounded search), SV_ERR_ARG beyond.
  * SV_PART_BEAM: beam search over the same down-sets for circuits of any size
  * (each kept prefix grows one candidate part from every available gate,
- * adding the qubit that lets the most gates in, up to k; the widest prefixes
- * survive); deterministic; the beam width is sv_plan_build's dfs_trials
- * argument (<= 0: 16). */
+ * adding the qubit that lets the most gates in, up to k, looking one qubit
+ * further at widths >= 32; the widest prefixes survive); deterministic; the
+ * beam width is sv_plan_build's dfs_trials argument (<= 0: 16). */
 typedef enum {
     SV_PART_NONE = 0, SV_PART_NAT = 1, SV_PART_DFS = 2, SV_PART_DAGP = 3, SV_PART_EXACT = 4, SV_PART_BEAM = 5
 } sv_method;

@@ -699,7 +699,9 @@ bool part_exact(const Dag &dag, int k, std::vector<uint32_t> &pog, std::string &
 // from every available gate g0: start with Q = qubits(g0) and the closure of
 // D on Q (all gates on Q whose predecessors are in D or the closure), then
 // add, while |Q| < k, the qubit of a gate blocked only by Q that makes the
-// closure largest (ties: the smaller qubit). Each level keeps the `width`
+// closure largest (ties: the smaller qubit; widths of 32 and more rank a
+// qubit by the largest closure one more qubit can reach, then by its own
+// closure). Each level keeps the `width`
 // down-sets covering the most gates (ties: the lexicographically smaller
 // gate set); the first level that covers every gate gives the partition.
 // A greedy width of 1 already picks each part's qubit set by its gate count,
@@ -782,12 +784,38 @@ std::vector<uint32_t> part_beam(const Dag &dag, int k, int width) {
                     if (!cq) break;
                     int best_q = -1;
                     size_t best_n = 0;
+                    const bool look = width >= 32 && popc(Q) + 2 <= k;
                     for (uint64_t m = cq; m; m &= m - 1) {
                         const int q = __builtin_ctzll(m);
                         closure(D, Q | (1ull << q), trial);
-                        if (best_q < 0 || trial.size() > best_n) {
+                        size_t score = trial.size();
+                        if (look) {
+                            // wide beams look one qubit further: the score is the
+                            // largest closure after the best follow-up qubit
+                            uint64_t cq2 = 0;
+                            const uint32_t g1 = gen;
+                            auto consider2 = [&](int h) {
+                                if (in(D, h) || mark[h] == g1) return;
+                                for (int p : dag.preds[h])
+                                    if (!in(D, p) && mark[p] != g1) return;
+                                cq2 |= dag.qmask[h];
+                            };
+                            for (int h : avail) consider2(h);
+                            for (int a : trial)
+                                for (int h : dag.succs[a]) consider2(h);
+                            cq2 &= ~(Q | (1ull << q));
+                            std::vector<int> t2;
+                            size_t best2 = trial.size();
+                            for (uint64_t m2 = cq2; m2; m2 &= m2 - 1) {
+                                const int q2 = __builtin_ctzll(m2);
+                                closure(D, Q | (1ull << q) | (1ull << q2), t2);
+                                best2 = std::max(best2, t2.size());
+                            }
+                            score = best2 * 1024 + trial.size();
+                        }
+                        if (best_q < 0 || score > best_n) {
                             best_q = q;
-                            best_n = trial.size();
+                            best_n = score;
                         }
                     }
                     Q |= 1ull << best_q;
