@@ -542,7 +542,7 @@ def oracle_report():
 
 
 def partition_quality():
-    """Part counts of the Nat, DFS and dagP builders against the exact
+    """Part counts of the Nat, DFS, dagP and beam (width 16) builders against the exact
     optimum (SV_PART_EXACT; the comparison Sec. V-A makes with an ILP): 54
     small random layered circuits (6-8 qubits, depth 2-4, both gate sets, k
     3-5) and small instances of the benchmark families (QFT, layered,
@@ -562,14 +562,14 @@ def partition_quality():
             t0 = time.perf_counter()
             opt = count(g, n, "exact", k)
             r = {"case": name, "gates": len(g), "k": k, "exact": opt, "exact_s": round(time.perf_counter() - t0, 3)}
-            for m in ("nat", "dfs", "dagp"):
+            for m in ("nat", "dfs", "dagp", "beam"):
                 r[m] = count(g, n, m, k)
             out.append(r)
         return out
 
     def summary(rs):
         s = {}
-        for m in ("nat", "dfs", "dagp"):
+        for m in ("nat", "dfs", "dagp", "beam"):
             ex = [r[m] - r["exact"] for r in rs]
             s[m] = {"optimal": sum(e == 0 for e in ex), "of": len(rs),
                     "mean_excess_parts": round(sum(ex) / len(ex), 3), "max_excess_parts": max(ex),
