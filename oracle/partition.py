@@ -35,6 +35,11 @@ listed in the design notes of the repository):
 * Schedule: Kahn order of the part graph with a min-heap keyed by each
   part's smallest gate index; parts are renumbered 0..P-1 in that order.
 
+Beyond the paper: ``beam`` states the repository's beam-search builder from
+its definition (see its docstring) so that the C++ builder's partitions are
+checked bit for bit, and ``brute_force_min_parts`` gives the optimum on tiny
+DAGs.
+
 Gates are ``(name, qubits, theta)`` tuples (``synth``).
 """
 from __future__ import annotations
@@ -608,6 +613,123 @@ def schedule(dag: Dag, pog):
     return [newid[p] for p in pog]
 
 
+def beam(gates, n, k, width=16):
+    """The repository's beam-search builder, written from its definition (it
+    is an addition, not one of the paper's three builders). A partition is a
+    chain of down-sets D_0 = {} < D_1 < ... < D_P = all gates; a step adds
+    one part X = D_{i+1} - D_i.
+
+    closure(D, Q): every gate whose qubits lie in Q and whose predecessors
+    are in D or the closure (the largest such set).
+    From a kept prefix D, every available gate g0 (ascending) seeds one
+    candidate: Q = qubits(g0), then while |Q| < k, among the qubits (not in
+    Q) of the gates outside closure(D, Q) whose predecessors are all in it,
+    add the one whose closure adds the most gates (the smallest such qubit);
+    at width >= 32, while two more qubits fit, a qubit q scores
+    1024 * (most gates added by closure(D, Q + q + q2) over the same kind of
+    follow-up qubit q2, or by closure(D, Q + q) if larger) + gates added by
+    closure(D, Q + q). The candidate is D + closure(D, Q) if that adds a gate;
+    a down-set reached twice keeps its first parent (kept prefixes in order,
+    seeds ascending). Each level keeps the `width` candidates covering the
+    most gates, ties to the smaller gate set compared as 64-gate words from
+    gate 0 (bit 63 of a word most significant); the first kept candidate
+    covering every gate ends the search. Parts are then numbered by
+    ``schedule``."""
+    dag = Dag(gates, n)
+    _check_arity(dag, k)
+    G = dag.G
+    if G == 0:
+        return []
+    if width < 1:
+        width = 16
+    W = (G + 63) // 64
+    full = (1 << G) - 1
+
+    def closure(D, Q):
+        E = D
+        for g in range(G):   # gate order is topological: one sweep reaches the fixed point
+            if (E >> g) & 1 or dag.qmask[g] & ~Q:
+                continue
+            if all((E >> p) & 1 for p in dag.preds[g]):
+                E |= 1 << g
+        return E
+
+    def blocked_qubits(E):
+        m = 0
+        for h in range(G):
+            if not (E >> h) & 1 and all((E >> p) & 1 for p in dag.preds[h]):
+                m |= dag.qmask[h]
+        return m
+
+    def popcount(x):
+        return bin(x).count("1")
+
+    def words(E):
+        return tuple((E >> (64 * i)) & ((1 << 64) - 1) for i in range(W))
+
+    nodes = [(0, None)]       # (down-set, parent node): a down-set can recur at a later level
+    level = [(0, 0, 0)]       # (down-set, gates covered, node)
+    while True:
+        cand = {}             # down-set -> (gates covered, parent node); first insertion kept
+        order = []
+        for D, cnt, node in level:
+            avail = [g for g in range(G) if not (D >> g) & 1 and all((D >> p) & 1 for p in dag.preds[g])]
+            for g0 in avail:
+                Q = dag.qmask[g0]
+                E = closure(D, Q)
+                while popcount(Q) < k:
+                    cq = blocked_qubits(E) & ~Q
+                    if not cq:
+                        break
+                    look = width >= 32 and popcount(Q) + 2 <= k
+                    best_q, best_s = -1, -1
+                    for q in range(n):
+                        if not (cq >> q) & 1:
+                            continue
+                        E1 = closure(D, Q | (1 << q))
+                        added = popcount(E1) - popcount(D)
+                        score = added
+                        if look:
+                            best2 = added
+                            cq2 = blocked_qubits(E1) & ~(Q | (1 << q))
+                            for q2 in range(n):
+                                if (cq2 >> q2) & 1:
+                                    E2 = closure(D, Q | (1 << q) | (1 << q2))
+                                    best2 = max(best2, popcount(E2) - popcount(D))
+                            score = best2 * 1024 + added
+                        if score > best_s:
+                            best_q, best_s = q, score
+                    Q |= 1 << best_q
+                    E = closure(D, Q)
+                if E == D or E in cand:
+                    continue
+                cand[E] = (popcount(E), node)
+                order.append(E)
+        order.sort(key=lambda E: (-cand[E][0], words(E)))
+        level = []
+        for E in order[:width]:
+            nodes.append((E, cand[E][1]))
+            level.append((E, cand[E][0], len(nodes) - 1))
+        done = [node for E, c, node in level if c == G]
+        if done:
+            break
+    chain = []
+    node = done[0]
+    while node:
+        chain.append(nodes[node][0])
+        node = nodes[node][1]
+    chain.reverse()
+    pog = [0] * G
+    prev = 0
+    for i, E in enumerate(chain):
+        X = E & ~prev
+        for g in range(G):
+            if (X >> g) & 1:
+                pog[g] = i
+        prev = E
+    return schedule(dag, pog)
+
+
 def partition(gates, n, method, k, seed=0, trials=16):
     if method == "nat":
         return nat(gates, n, k)
@@ -615,6 +737,8 @@ def partition(gates, n, method, k, seed=0, trials=16):
         return dfs(gates, n, k, seed=seed, trials=trials)
     if method == "dagp":
         return dagp(gates, n, k)
+    if method == "beam":
+        return beam(gates, n, k, width=trials)
     raise ValueError(method)
 
 

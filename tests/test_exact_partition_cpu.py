@@ -99,3 +99,24 @@ def test_beam_builder_on_the_benchmark_circuits():
     assert P < _parts(g, n, "dagp", 6)[1]
     q = synth.qft(33)
     assert _parts(q, 33, "beam", 6)[1] < _parts(q, 33, "dagp", 6)[1]
+
+
+def test_beam_builder_bit_exact_with_oracle():
+    """The C++ beam builder against the oracle's own implementation of the
+    same definition: the same part of every gate, for widths 1, 4, 16 and
+    32 (the look-ahead), on the three families and on a 252-gate circuit
+    whose gate sets span four 64-bit words."""
+    cases = [(8, synth.qft(8), 4), (8, synth.layered(8, 4, seed=3), 4), (8, synth.param(8, 3, seed=2), 4),
+             (10, synth.qft(10), 5), (10, synth.layered(10, 5, seed=5), 5), (10, synth.param(10, 4, seed=4), 5)]
+    for n, g, k in cases:
+        for w in (1, 4, 16, 32):
+            p = api.Plan(g, n, "beam", k, dfs_trials=w)
+            pog = [int(x) for x in p.export()[0]]
+            p.close()
+            assert pog == pt.beam(g, n, k, w), (n, k, w)
+    n, g = 12, synth.layered(12, 14, seed=9)
+    for w in (4, 32):
+        p = api.Plan(g, n, "beam", 6, dfs_trials=w)
+        pog = [int(x) for x in p.export()[0]]
+        p.close()
+        assert pog == pt.beam(g, n, 6, w), w
