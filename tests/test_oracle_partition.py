@@ -160,3 +160,22 @@ def test_dagp_quality_on_layered():
         assert d <= max(pt.nat(g, n, k)) + 1
     g = synth.qft(16)
     assert max(pt.dagp(g, 16, 6)) + 1 <= max(pt.nat(g, 16, 6)) + 1
+
+
+def test_oracle_beam_valid_and_not_below_optimum():
+    """The oracle's beam builder is pinned by the validity conditions of the
+    partitioning problem and by the brute-force optimum (never fewer parts;
+    it is a heuristic: each prefix grows one greedy candidate per available
+    gate, so even an unlimited width need not reach the optimum, and on
+    these tiny DAGs it mostly does)."""
+    hits = 0
+    for seed in range(25):
+        n = 5
+        g = _rand(n, 10, 700 + seed)
+        k = 2 + seed % 3
+        opt = pt.brute_force_min_parts(g, n, k)
+        for w in (1, 4, 1 << 20):
+            pog = pt.beam(g, n, k, w)
+            assert pt.check_partition(g, n, k, pog) >= opt
+        hits += pt.check_partition(g, n, k, pt.beam(g, n, k, 16)) == opt
+    assert hits >= 15, hits
