@@ -189,3 +189,29 @@ def test_cost_model_picks_kernel_per_circuit(native):
         plan, tc, est = autotune.choose_plan(g, n)
         assert tc and est[0]["est_s"] < est[1]["est_s"]
         plan.close()
+
+
+def test_new_builders_and_batch_entry_points_validate_arguments(native):
+    """Argument checks that need no device: an unknown method, the exact and
+    beam builders on an empty circuit and with k below a gate's arity, the
+    beam width default, and the dense batch entry points on a NULL batch."""
+    from paper_2205_06973_gb300.api import Plan
+    arr = native.encode_gates([("H", (0,), 0.0)])
+    h = ctypes.c_void_p()
+    st = native.lib.sv_plan_build(ctypes.cast(arr, ctypes.c_void_p), 1, 2, 6, 2, 0, 0, ctypes.byref(h))
+    assert st == native.SV_ERR_ARG and b"method" in native.lib.sv_last_error()
+    for m in ("exact", "beam"):
+        p = Plan([], 3, m, 2)
+        assert p.export()[1] == 0
+        p.close()
+        with pytest.raises(native.SvError) as e:
+            Plan([("CX", (0, 1), 0.0)], 2, m, 1)
+        assert e.value.status == native.SV_ERR_PARTITION
+    g = [("H", (q,), 0.0) for q in range(4)] + [("CX", (q, q + 1), 0.0) for q in range(3)]
+    a = Plan(g, 4, "beam", 2, dfs_trials=0).export()
+    b = Plan(g, 4, "beam", 2, dfs_trials=16).export()
+    assert list(a[0]) == list(b[0]) and a[1] == b[1]
+    assert native.lib.sv_batch_set_dense(None, 13, 0, 0) == native.SV_ERR_ARG
+    n1, n2, n3 = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    assert native.lib.sv_batch_dense_info(None, ctypes.byref(n1), ctypes.byref(n2), ctypes.byref(n3)) == \
+        native.SV_ERR_ARG
