@@ -119,6 +119,7 @@ class Server:
         s_i = 0
         planned = {}
         host = {"plan_wait_s": 0.0, "batch_build_s": 0.0, "batches": 0, "batched_requests": 0, "large_tc": 0}
+        batch_times, batch_sizes, large_times = [], [], []   # launch -> results, per micro-batch / large request
 
         def now():
             return (time.perf_counter() - t0) / time_scale
@@ -195,6 +196,7 @@ class Server:
                     res = Result(r.rid, r.n, r.arrival, start, now(), norm, p0, am, pm,
                                  st.copy_to_host() if self.keep else None)
                     results.append(res)
+                    large_times.append(res.done - start)
                     st.close()
                     plan.close()
                     used -= self.state_bytes(r.n)
@@ -208,6 +210,8 @@ class Server:
                 probs, norms = b.probs()
                 torch.cuda.current_stream().wait_stream(b.stream)
                 done_t = now()
+                batch_times.append(done_t - start)
+                batch_sizes.append(len(take))
                 for j, r in enumerate(take):
                     p = probs[int(b.offsets[j]):int(b.offsets[j + 1])]
                     p0, am, pm = _summary(p)
@@ -229,5 +233,13 @@ class Server:
         stats = {"requests": len(results), "wall_s": wall, "circuits_per_s": len(results) / max(wall, 1e-9),
                  "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                  "mean_s": float(lat.mean()), "mode": self.mode, **host}
+        # where the latency goes: time from a micro-batch's (large request's)
+        # launch to its results, and the micro-batch sizes
+        for name, v in (("batch_s", batch_times), ("large_s", large_times)):
+            if v:
+                stats[name + "_mean"] = round(float(np.mean(v)), 4)
+                stats[name + "_max"] = round(float(np.max(v)), 4)
+        if batch_sizes:
+            stats["batch_size_max"] = int(max(batch_sizes))
         results.sort(key=lambda r: r.rid)
         return results, stats
