@@ -29,6 +29,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "state-vector part passes GB/s (HBM traffic of the passes / time)"
 UNIT = "GB/s"
+DTYPE_TC = ("c64 state; split-BF16 x3 tensor-core products, FP32 accumulate in TMEM, per-pass rescale "
+            "to the input norm")
+DTYPE_FP32 = "c64 state; FP32 arithmetic"
 WORKLOAD = ("random layered circuit, 28 qubits, depth 60 (H/RX/RZ on every qubit, then CX/CZ on a "
             "random disjoint pairing; 2520 gates, seed 2), complex64 state, part-fused passes")
 
@@ -413,7 +416,7 @@ def run_ours(a):
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
                 "warmup": max(a.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 arithmetic)", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_TC if tc else DTYPE_FP32, "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_qubits": n, "gates": len(gates), "method": method,
                            "k": k, "tensor_core_dense_parts": stats["dense"], "passes": passes,
                            "phases": stats["phases"], "ops": stats["ops"],

@@ -266,9 +266,13 @@ sv_status sv_batch_destroy(sv_batch *b);
  *              SV_NOALLOC_MAX_BLOCKS is rejected with SV_ERR_ARG
  *   stream     cudaStream_t (NULL = legacy default stream); stream-ordered,
  *              no synchronisation.
- * The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Every call shares the one array, which keeps
+ * Every call made outside a stream capture looks the array's device address
+ * up (cudaGetSymbolAddress) with the caller's device current, so a device
+ * reset or a new context never leaves a stale address; a call made during a
+ * capture reuses the last address found on that device, so make the first
+ * call on a device before any stream capture (otherwise SV_ERR_ARG). A device
+ * ordinal of 64 or more is rejected with SV_ERR_ARG. Every call shares the
+ * one array, which keeps
  * the last call's contents; each call writes every partial sum it reads, so
  * nothing needs clearing, but calls that overlap on the GPU (different
  * streams, or threads without ordering) race on it. */

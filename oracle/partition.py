@@ -13,8 +13,8 @@ Written from Sec. IV of the paper:
   graph that keeps it acyclic and L <= L_m). L of a convex part equals the
   number of wire edges entering it plus the entry vertices inside it.
 
-Where the paper leaves details open, these readings are used (each is
-listed in the design notes of the repository):
+Where Sec. IV-B leaves details open (it defers the builders' internals to
+external work), these readings are used:
 
 * Nat: gate g joins the open part iff L(part + g) <= k, else the part is
   closed and g opens the next one.

@@ -56,18 +56,35 @@ extern "C" sv_status sv_probs_noalloc(const void *dev_state, int n_qubits, sv_pr
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    if (e != cudaSuccess) {
         return noalloc_fail(SV_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    }
+    if (dev < 0 || dev >= 64) {
+        return noalloc_fail(SV_ERR_ARG, "device ordinal " + std::to_string(dev) +
+                                            " is outside the 64 devices this entry point tracks");
+    }
+    // The address is looked up again on every call made outside a stream
+    // capture (cheap, no allocation), so a device reset or a new context on
+    // the same ordinal never leaves a stale pointer behind; during a capture
+    // (where the lookup is not allowed) the last address found is used.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cap);
+    if (e != cudaSuccess) {
+        return noalloc_fail(SV_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
     }
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_ready[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             e = cudaGetSymbolAddress(&g_addr[dev], g_probs_scratch);
             if (e != cudaSuccess) {
+                g_ready[dev] = false;
                 return noalloc_fail(SV_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             }
             g_ready[dev] = true;
+        } else if (!g_ready[dev]) {
+            return noalloc_fail(SV_ERR_ARG, "first call on this device made during a stream capture: call it "
+                                            "once outside the capture first");
         }
         scratch = g_addr[dev];
     }

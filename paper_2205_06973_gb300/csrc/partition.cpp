@@ -1,6 +1,7 @@
 // Gate DAG and the Nat / DFS / dagP part builders (Sec. IV of the paper).
 //
-// Readings of details the paper leaves open (shared with the design notes):
+// Readings of details the paper leaves open (Sec. IV-B defers the builders' details to
+// external work; each reading below is this library's and the oracle's alike):
 //  * Nat (Sec. IV-B): gate g joins the open part iff L(part + g) <= k; else
 //    the part is closed and g opens the next one.
 //  * DFS (Sec. IV-B): trial r draws from SplitMix64(seed ^ r*0x9E3779B97F4A7C15);
