@@ -54,7 +54,12 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-circuit batched launch")
     ap.add_argument("--batch-circuits", type=int, default=4096,
                     help="circuits of the batch section (a smaller batch for profiling)")
-    ap.add_argument("--no-serving", action="store_true", help="skip the serving sample")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
+    ap.add_argument("--serving-window", type=float, default=3.0,
+                    help="seconds of the request stream's arrivals served in the serving section")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="serve the whole 20000-request stream (60 s of arrivals, then drain; minutes), "
+                         "one JSON line, then exit")
     ap.add_argument("--partition-quality", action="store_true",
                     help="CPU only: part counts of Nat, DFS and dagP against the exact optimum on small "
                          "circuits (one JSON line), then exit")
@@ -265,28 +270,78 @@ def batch_section(count=4096):
             "norm_min": float(np.min(norms)), "norm_max": float(np.max(norms))}
 
 
-def serving_section():
-    """The serving loop on a bounded sample of the request stream (Poisson,
-    20000 requests / 60 s, 10-33 qubits with 80 % <= 20, three families): its
-    first 300 requests of at most 26 qubits, replayed at their arrival times,
-    part-fused and gate by gate."""
+def _serving_requests(count, window_s=None, max_n=33):
+    """The serving stream (seed 5: 20000 Poisson arrivals over 60 s, 10-33
+    qubits with 80 % <= 20, three families): its first ``count`` requests of at
+    most max_n qubits, or every request arriving in the first window_s
+    seconds."""
     import synth
-    from paper_2205_06973_gb300.serving import Request, Server
+    from paper_2205_06973_gb300.serving import Request
     arr = synth.serving_arrivals(20000, 60.0, seed=5)
     reqs, i = [], 0
-    while len(reqs) < 300:
+    while i < len(arr) and (window_s is None or arr[i] <= window_s) and (window_s is not None or len(reqs) < count):
         n, fam, g = synth.serving_request(i, seed=5)
-        if n <= 26:
+        if n <= max_n:
             reqs.append(Request(len(reqs), n, g, arr[i], fam))
         i += 1
-    out = {"workload": "first 300 requests with n <= 26 of the 20000-request stream (seed 5), "
-                       "arrival times replayed", "n_large": sum(r.n > 20 for r in reqs)}
+    return reqs
+
+
+def _serving_stats(st):
+    return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items() if k != "mode"}
+
+
+def serving_section(window_s=3.0):
+    """The serving loop on the request stream: (1) every request arriving in
+    the stream's first window_s seconds, all qubit counts (10-33, states up to
+    64 GiB, admission by 8 * 2^n bytes against 170 GB), part-fused, served to
+    the end (drain); (2) the first 300 requests of at most 26 qubits,
+    part-fused and gate by gate (gate by gate takes minutes per 33-qubit
+    request, so the comparison runs on this sample)."""
+    from paper_2205_06973_gb300.serving import Server
+    win = _serving_requests(None, window_s=window_s)
+    srv = Server(budget_bytes=170e9)
+    _, st = srv.run(win)
+    srv.close()
+    out = {"stream": {"workload": f"every request of the first {window_s:g} s of arrivals of the 20000-request "
+                                  "stream (seed 5), 10-33 qubits, arrival times replayed, served until drained",
+                      "n_requests": len(win), "n_min": min(r.n for r in win), "n_max": max(r.n for r in win),
+                      "n_27_33": sum(r.n >= 27 for r in win), **_serving_stats(st)}}
+    sample = _serving_requests(300, max_n=26)
+    out["sample"] = {"workload": "first 300 requests with n <= 26 of the same stream, arrival times replayed",
+                     "n_large": sum(r.n > 20 for r in sample)}
     for mode in ("parts", "gatewise"):
-        _, st = Server(budget_bytes=170e9, mode=mode).run(reqs)
-        out[mode] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items() if k != "mode"}
-    out["throughput_vs_gate_by_gate"] = round(out["parts"]["circuits_per_s"] / out["gatewise"]["circuits_per_s"], 2)
-    out["p99_vs_gate_by_gate"] = round(out["gatewise"]["p99_s"] / out["parts"]["p99_s"], 2)
+        srv = Server(budget_bytes=170e9, mode=mode)
+        _, st = srv.run(sample)
+        srv.close()
+        out["sample"][mode] = _serving_stats(st)
+    sp = out["sample"]
+    sp["throughput_vs_gate_by_gate"] = round(sp["parts"]["circuits_per_s"] / sp["gatewise"]["circuits_per_s"], 2)
+    sp["p99_vs_gate_by_gate"] = round(sp["gatewise"]["p99_s"] / sp["parts"]["p99_s"], 2)
     return out
+
+
+def serving_full():
+    """The whole serving stream (20000 requests over 60 s, 10-33 qubits,
+    170 GB budget), part-fused, until drained. One JSON line."""
+    import torch
+    from paper_2205_06973_gb300.serving import Server
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    reqs = _serving_requests(20000)
+    gen_s = time.perf_counter() - t0
+    clk = ClockSampler(0)
+    clk.start()
+    srv = Server(budget_bytes=170e9)
+    res, st = srv.run(reqs)
+    srv.close()
+    clocks = clk.stop()
+    print(json.dumps({"serving_full": {"workload": "the 20000-request stream (seed 5): Poisson arrivals over 60 s, "
+                                                   "10-33 qubits (80 % <= 20), layered / QFT / parameterised, "
+                                                   "complex64, admission by 8 * 2^n bytes against 170 GB",
+                                       "generate_s": round(gen_s, 1), "clocks": clocks,
+                                       "norm_min": min(r.norm for r in res), "norm_max": max(r.norm for r in res),
+                                       **_serving_stats(st)}}), flush=True)
 
 
 def run_ours(a):
@@ -411,7 +466,7 @@ def run_ours(a):
     if rank == 0 and not a.no_batch:
         batch = batch_section(a.batch_circuits)
     if rank == 0 and not a.no_serving:
-        serving = serving_section()
+        serving = serving_section(a.serving_window)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
@@ -606,6 +661,8 @@ def main():
     a = parse()
     if a.partition_quality:
         partition_quality()
+    elif a.serving_full:
+        serving_full()
     elif a.impl == "reference" and a.oracle_report:
         oracle_report()
     elif a.impl == "reference":

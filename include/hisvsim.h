@@ -174,6 +174,14 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags);
  * and the norm sum_x |a_x|^2 accumulated in FP64 into *norm_out (host, may be
  * NULL). Synchronises the stream when norm_out is not NULL. */
 sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *norm_out);
+/* Summary of the same distribution without writing it (no device memory
+ * beyond the state's own scratch): *norm_out = sum_x |a_x|^2, *p0_out =
+ * |a_0|^2, *pmax_out = max_x |a_x|^2 and *argmax_out = the smallest x that
+ * reaches it, all computed in FP64 from the stored amplitudes (Sec. II-A:
+ * measuring gives x with probability |a_x|^2). Any output may be NULL.
+ * Synchronises the stream. */
+sv_status sv_measure_summary(sv_state *s, double *norm_out, double *p0_out, uint64_t *argmax_out,
+                             double *pmax_out);
 
 /* ---------------------------------------------------------------- batch ---
  * Many small, independent circuits run in ONE persistent kernel launch that a
@@ -232,6 +240,11 @@ sv_status sv_batch_create(uint32_t n_circuits, const int *n_qubits, void *stream
 sv_status sv_batch_set_plan(sv_batch *b, uint32_t i, sv_plan *p);
 sv_status sv_batch_config(sv_batch *b, int warps_per_cta, int tiles_per_item);
 sv_status sv_batch_run(sv_batch *b, uint32_t flags);
+/* sv_batch_prepare: build the batch's device program and capture its graph
+ * (what the first sv_batch_run does) without launching it, so that a host
+ * thread can prepare the next batch while another batch runs. It waits for
+ * the batch's own stream (the program upload); the capture is thread-local. */
+sv_status sv_batch_prepare(sv_batch *b);
 sv_status sv_batch_reset(sv_batch *b);
 sv_status sv_batch_probs(sv_batch *b, void *dev_out, double *norms_host);
 sv_status sv_batch_state(sv_batch *b, uint32_t i, void **dev_ptr, size_t *bytes);

@@ -69,6 +69,9 @@ _SIGS = {
     "sv_plan_destroy": ([_vp], ctypes.c_int),
     "sv_apply_parts": ([_vp, _vp, ctypes.c_uint32], ctypes.c_int),
     "sv_measure_probs": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "sv_measure_summary": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "sv_batch_prepare": ([_vp], ctypes.c_int),
     "sv_probs_noalloc": ([_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "sv_batch_create": ([ctypes.c_uint32, _vp, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
     "sv_batch_set_plan": ([_vp, ctypes.c_uint32, _vp], ctypes.c_int),

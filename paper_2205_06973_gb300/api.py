@@ -107,6 +107,15 @@ class State:
         N.check(N.lib.sv_measure_probs(self.h, ptr, 1 if fp64 else 0, ctypes.byref(norm)))
         return norm.value
 
+    def summary(self):
+        """(norm, |a_0|^2, argmax_x |a_x|^2, max |a_x|^2) in FP64 without a
+        probability vector (sv_measure_summary; synchronises)."""
+        nrm, p0, pm = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        am = ctypes.c_uint64()
+        N.check(N.lib.sv_measure_summary(self.h, ctypes.byref(nrm), ctypes.byref(p0), ctypes.byref(am),
+                                         ctypes.byref(pm)))
+        return nrm.value, p0.value, am.value, pm.value
+
     def sync(self):
         N.check(N.lib.sv_sync(self.h))
 

@@ -60,16 +60,22 @@ class Batch:
             N.check(N.lib.sv_batch_set_dense(self.h, dense_min_qubits, dense_tiles_per_item, dense_group_tiles))
 
     @classmethod
-    def from_plans(cls, items, stream=None, warps_per_cta=0, tiles_per_item=0):
-        """items: list of (n_qubits, Plan)."""
+    def from_plans(cls, items, stream=None, warps_per_cta=0, tiles_per_item=0, dense_min_qubits=0):
+        """items: list of (n_qubits, Plan). dense_min_qubits as for the
+        constructor; the plans of those circuits must have parts of at most
+        6 qubits to run on the batched tensor-core kernel."""
         return cls(None, plans=[p for _, p in items], stream=stream, warps_per_cta=warps_per_cta,
-                   tiles_per_item=tiles_per_item)
+                   tiles_per_item=tiles_per_item, dense_min_qubits=dense_min_qubits)
 
     def configure(self, warps_per_cta=0, tiles_per_item=0):
         N.check(N.lib.sv_batch_config(self.h, warps_per_cta, tiles_per_item))
 
     def run(self, sync=False):
         N.check(N.lib.sv_batch_run(self.h, N.SV_FLAG_SYNC if sync else 0))
+
+    def prepare(self):
+        """Build the device program and capture the graph without launching."""
+        N.check(N.lib.sv_batch_prepare(self.h))
 
     def reset(self):
         N.check(N.lib.sv_batch_reset(self.h))

@@ -34,6 +34,11 @@ sv_status fail(sv_status st, const std::string &msg) {
     } while (0)
 
 constexpr int kProbBlocks = 152 * 8;
+// per-state reduction scratch: kProbBlocks partial sums and the norm
+// (sv_measure_probs), then 3 * kProbBlocks block results and 4 outputs
+// (sv_measure_summary)
+constexpr int kSummaryAt = kProbBlocks + 1;
+constexpr int kPartialsLen = kSummaryAt + 3 * kProbBlocks + 4;
 }  // namespace
 
 namespace hisv {
@@ -80,7 +85,7 @@ sv_status sv_create(int n, sv_precision prec, void *dev_buf, size_t dev_buf_byte
         }
         s->owns = true;
     }
-    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&s->d_partials), sizeof(double) * (kProbBlocks + 1), s->stream);
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&s->d_partials), sizeof(double) * kPartialsLen, s->stream);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&s->d_err), sizeof(int), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
     if (e != cudaSuccess) {
@@ -433,6 +438,21 @@ sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *nor
         CUDA_TRY(cudaStreamSynchronize(s->stream));
         *norm_out = s->h_norm;
     }
+    return SV_OK;
+}
+
+sv_status sv_measure_summary(sv_state *s, double *norm_out, double *p0_out, uint64_t *argmax_out,
+                             double *pmax_out) {
+    if (!s) return fail(SV_ERR_ARG, "state is NULL");
+    double *scratch = s->d_partials + kSummaryAt, *d_out = scratch + 3 * kProbBlocks;
+    CUDA_TRY(launch_summary(is_fp64(s), s->buf, s->n, scratch, kProbBlocks, d_out, s->stream));
+    double h[4];
+    CUDA_TRY(cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (norm_out) *norm_out = h[0];
+    if (p0_out) *p0_out = h[1];
+    if (pmax_out) *pmax_out = h[2];
+    if (argmax_out) std::memcpy(argmax_out, &h[3], sizeof(uint64_t));
     return SV_OK;
 }
 

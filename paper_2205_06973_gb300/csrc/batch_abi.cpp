@@ -438,6 +438,18 @@ sv_status sv_batch_run(sv_batch *b, uint32_t flags) {
     return SV_OK;
 }
 
+sv_status sv_batch_prepare(sv_batch *b) {
+    if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
+    if (!b->built) {
+        sv_status st = build_program(b);
+        if (st != SV_OK) {
+            drop_program(b);
+            return st;
+        }
+    }
+    return SV_OK;
+}
+
 sv_status sv_batch_hold_last_item(sv_batch *b, int on) {
     if (!b) return bfail(SV_ERR_ARG, "batch is NULL");
     b->hold_last = on != 0;

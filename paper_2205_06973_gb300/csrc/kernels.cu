@@ -408,6 +408,109 @@ cudaError_t launch_probs(bool fp64, const void *sv, int n, void *out, int out_fp
     return cudaGetLastError();
 }
 
+// Summary of the probability distribution without writing it: per block the
+// FP64 sum of |a_x|^2 and the largest |a_x|^2 with its index (ties to the
+// smaller index), then one block combines them.
+__device__ __forceinline__ void better(double &p, uint64_t &i, double q, uint64_t j) {
+    if (q > p || (q == p && j < i)) {
+        p = q;
+        i = j;
+    }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) k_summary(const typename CT<Real>::T *__restrict__ sv, uint64_t N,
+                                                  double *__restrict__ sums, double *__restrict__ maxs,
+                                                  uint64_t *__restrict__ idxs) {
+    typedef typename CT<Real>::T C;
+    __shared__ double rs[8], rm[8];
+    __shared__ uint64_t ri[8];
+    double acc = 0.0, best = -1.0;
+    uint64_t bi = ~0ull;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+        const C v = __ldcs(sv + i);
+        const double re = (double)v.x, im = (double)v.y;
+        const double p = re * re + im * im;
+        acc += p;
+        better(best, bi, p, i);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const double q = __shfl_xor_sync(0xffffffffu, best, o);
+        const uint64_t j = __shfl_xor_sync(0xffffffffu, bi, o);
+        better(best, bi, q, j);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rs[threadIdx.x >> 5] = acc;
+        rm[threadIdx.x >> 5] = best;
+        ri[threadIdx.x >> 5] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0, m = -1.0;
+        uint64_t mi = ~0ull;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            s += rs[w];
+            better(m, mi, rm[w], ri[w]);
+        }
+        sums[blockIdx.x] = s;
+        maxs[blockIdx.x] = m;
+        idxs[blockIdx.x] = mi;
+    }
+}
+
+// out[0] = sum |a|^2, out[1] = |a_0|^2, out[2] = max |a_x|^2, out[3] = its index (bits)
+template <typename Real>
+__global__ void k_summary_final(const typename CT<Real>::T *__restrict__ sv, const double *__restrict__ sums,
+                                const double *__restrict__ maxs, const uint64_t *__restrict__ idxs, int nb,
+                                double *__restrict__ out) {
+    __shared__ double rs[256], rm[256];
+    __shared__ uint64_t ri[256];
+    double s = 0.0, m = -1.0;
+    uint64_t mi = ~0ull;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        s += sums[i];
+        better(m, mi, maxs[i], idxs[i]);
+    }
+    rs[threadIdx.x] = s;
+    rm[threadIdx.x] = m;
+    ri[threadIdx.x] = mi;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            rs[threadIdx.x] += rs[threadIdx.x + w];
+            better(rm[threadIdx.x], ri[threadIdx.x], rm[threadIdx.x + w], ri[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double re = (double)sv[0].x, im = (double)sv[0].y;
+        out[0] = rs[0];
+        out[1] = re * re + im * im;
+        out[2] = rm[0];
+        out[3] = __longlong_as_double((long long)ri[0]);
+    }
+}
+
+cudaError_t launch_summary(bool fp64, const void *sv, int n, double *scratch, int nblocks, double *out,
+                           cudaStream_t st) {
+    const uint64_t N = 1ull << n;
+    uint64_t need = (N + 255) / 256;
+    int nb = (int)(need < (uint64_t)nblocks ? need : (uint64_t)nblocks);
+    if (nb < 1) nb = 1;
+    double *sums = scratch, *maxs = scratch + nblocks;
+    uint64_t *idxs = reinterpret_cast<uint64_t *>(scratch + 2 * nblocks);
+    if (fp64) {
+        k_summary<double><<<nb, 256, 0, st>>>((const double2 *)sv, N, sums, maxs, idxs);
+        k_summary_final<double><<<1, 256, 0, st>>>((const double2 *)sv, sums, maxs, idxs, nb, out);
+    } else {
+        k_summary<float><<<nb, 256, 0, st>>>((const float2 *)sv, N, sums, maxs, idxs);
+        k_summary_final<float><<<1, 256, 0, st>>>((const float2 *)sv, sums, maxs, idxs, nb, out);
+    }
+    return cudaGetLastError();
+}
+
 template <typename Real>
 __global__ void k_set_one(typename CT<Real>::T *sv, uint64_t idx) {
     typename CT<Real>::T v;

@@ -26,6 +26,11 @@ cudaError_t launch_gate2(bool fp64, void *sv, int n, int q0, int q1, const doubl
 cudaError_t launch_probs(bool fp64, const void *sv, int n, void *out, int out_fp64, double *partials,
                          int nblocks, double *d_norm, cudaStream_t st);
 
+// Norm, |a_0|^2 and the largest |a_x|^2 with its index (ties to the smaller
+// index), FP64, without a probability vector: scratch holds 3 * nblocks
+// doubles, out 4 (out[3] holds the index's bits).
+cudaError_t launch_summary(bool fp64, const void *sv, int n, double *scratch, int nblocks, double *out,
+                           cudaStream_t st);
 cudaError_t launch_set_basis(bool fp64, void *sv, int n, uint64_t idx, cudaStream_t st);
 
 }  // namespace hisv

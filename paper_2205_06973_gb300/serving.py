@@ -1,32 +1,46 @@
 """Serving loop with continuous batching over the C ABI.
 
-Requests (a circuit on n qubits and an arrival time) are admitted in arrival
-order once their state fits: 8 * 2^n bytes against a device byte budget and
-a free slot. Admitted states stay on the device until their result is taken.
+Requests (a circuit on n qubits and an arrival time) are admitted once their
+state fits: 8 * 2^n bytes against a device byte budget and a free slot.
+Admitted states stay on the device until their result is taken.
 
-* Small circuits (n <= small_n) are collected into micro-batches: whenever
-  the batched kernel is idle, every admitted small request that has not
-  started runs in one batched persistent launch (sv_batch_*), so requests
-  that arrived while the previous batch was on the GPU join the next one.
-* Large circuits get their own state and CUDA stream and run their part
-  passes (sv_apply_parts) beside the batch; at most ``large_running`` of
-  them at a time, in arrival order (each pass fills the GPU, so sharing it
-  among many large requests only stretches all their latencies). The batch
-  stream has the higher priority, so small requests are not queued behind
-  the passes of large ones. Each large request runs the plan the cost model
-  of ``autotune.choose_plan`` rates fastest: the tensor-core dense plan
+* Admission. Small requests (n <= small_n) and large ones queue apart, each
+  in arrival order. A large request at the head of its queue that does not
+  fit waits for memory to free up, without holding back the small requests
+  behind it; small states are admitted within a share of the budget
+  (``small_budget``, default 1/8), so they cannot starve the large head.
+* Planning never blocks the loop. Each request's plan is built on a worker
+  thread as it arrives (small and large requests on separate pools, so small
+  plans never queue behind the large requests' plan choice); a request joins
+  a micro-batch, or starts, only once its plan is ready.
+* Small requests run in micro-batches on the batched persistent launch
+  (sv_batch_*): the circuits of >= 13 qubits on the batched tensor-core
+  kernel (beam-search parts of <= 6 qubits), the others on the gate-list
+  kernel, in one graph. A builder thread assembles the next micro-batch
+  (allocation, program upload, graph capture) from the ready small requests
+  while the current one runs, and its graph is launched on the next of two
+  batch streams behind the running one, so the GPU goes from one
+  micro-batch to the next without a host round trip. Requests that arrive
+  meanwhile join the batch after.
+* Large requests get their own state and CUDA stream and run their part
+  passes (sv_apply_parts) beside the batches; at most ``large_running`` of
+  them at a time (each pass fills the GPU, so sharing it among many large
+  requests only stretches all their latencies). The batch streams have the
+  higher priority. Each large request runs the plan the cost model of
+  ``autotune.choose_plan`` rates fastest: the tensor-core dense plan
   (beam-search parts, k = 6) or the gate-list plan (beam-search parts,
-  k = 10; faster for circuits made mostly of diagonal gates such as the QFT).
-  With ``tc=False`` large requests use ``method_large`` / ``k_large`` on the
-  gate-list kernel. Small requests are planned with the beam builder (k = 9,
-  width 4) by default.
+  k = 10). With ``tc=False`` large requests use ``method_large`` /
+  ``k_large`` on the gate-list kernel.
 
-A request's result is its probability vector summary: the norm (FP64
-accumulation on the device), the probability of |0...0> and the most likely
-basis state with its probability; the full state can be kept for checks.
-Latency = completion time - arrival time. ``mode="gatewise"`` serves the same
-stream with one plain pass per gate for every request (no batching), the
-comparison the paper's per-gate simulators correspond to.
+A request's result is a summary of its probability distribution (Sec. II-A):
+the norm (FP64 accumulation on the device), the probability of |0...0> and
+the most likely basis state with its probability; large requests get it from
+a device reduction that writes no probability vector (sv_measure_summary),
+so the only device memory a request holds is its state. The full state can
+be kept for checks. Latency = completion time - arrival time.
+``mode="gatewise"`` serves the same stream with one plain pass per gate for
+every request (no batching), the comparison the paper's per-gate simulators
+correspond to.
 """
 from __future__ import annotations
 
@@ -38,10 +52,11 @@ import time
 import numpy as np
 import torch
 
-from . import _native as N
 from . import autotune
 from .api import Plan, State
 from .batch import Batch
+
+N_CLASSES = ((10, 20), (21, 26), (27, 33))
 
 
 @dataclasses.dataclass
@@ -58,6 +73,7 @@ class Result:
     rid: int
     n: int
     arrival: float
+    admitted: float
     start: float
     done: float
     norm: float
@@ -71,17 +87,17 @@ class Result:
         return self.done - self.arrival
 
 
-def _summary(probs: torch.Tensor):
-    p0 = float(probs[0].item())
-    am = int(torch.argmax(probs).item())
-    return p0, am, float(probs[am].item())
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
 
 
 class Server:
     def __init__(self, budget_bytes=170e9, max_slots=4096, small_n=20, batch_max=512, k_small=9,
                  k_large=6, tc=True, method_small="beam", method_large="dagp", mode="parts",
-                 keep_states=False, planners=8, large_running=2):
+                 keep_states=False, planners=8, large_planners=4, large_running=2, dense_min_qubits=13,
+                 small_budget=None):
         self.budget = float(budget_bytes)
+        self.small_budget = float(small_budget) if small_budget is not None else self.budget / 8
         self.max_slots = max_slots
         self.small_n = small_n
         self.batch_max = batch_max
@@ -92,154 +108,241 @@ class Server:
         self.method_large = method_large
         self.mode = mode
         self.keep = keep_states
-        self.large_running = large_running
+        self.large_running = max(1, large_running)
+        self.dense_min = dense_min_qubits if (tc and mode == "parts") else 0
         self.pool = cf.ThreadPoolExecutor(max_workers=planners)
-        self.streams = [torch.cuda.Stream() for _ in range(max(1, large_running))]
+        self.pool_large = cf.ThreadPoolExecutor(max_workers=large_planners)
+        self.builder = cf.ThreadPoolExecutor(max_workers=1)
+        self.streams = [torch.cuda.Stream() for _ in range(self.large_running)]
         lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
-        self.batch_stream = torch.cuda.Stream(priority=hi)
+        self.batch_streams = [torch.cuda.Stream(priority=hi) for _ in range(2)]
 
     @staticmethod
     def state_bytes(n):
         return 8 * (1 << n)
 
+    def _small(self, r):
+        return r.n <= self.small_n and self.mode == "parts"
+
+    def _plan(self, r):
+        """Built on a worker thread: (plan, tc)."""
+        if self.mode != "parts":
+            return Plan(r.gates, r.n, "none", min(self.k_large, r.n)), False
+        if self._small(r):
+            if self.dense_min and r.n >= self.dense_min:
+                return Plan(r.gates, r.n, "beam", 6, dfs_trials=4), True
+            return Plan(r.gates, r.n, self.method_small, min(self.k_small, r.n),
+                        dfs_trials=4 if self.method_small == "beam" else 16), False
+        if not self.tc:
+            return Plan(r.gates, r.n, self.method_large, min(self.k_large, r.n)), False
+        return autotune.choose_plan(r.gates, r.n)[:2]
+
+    def _build_batch(self, take, plans, stream):
+        """Built on the builder thread: the micro-batch with its graph captured."""
+        t0 = time.perf_counter()
+        b = Batch.from_plans([(r.n, p) for r, p in zip(take, plans)], stream=stream,
+                             dense_min_qubits=self.dense_min)
+        b.prepare()
+        return b, time.perf_counter() - t0
+
+    @staticmethod
+    def _new_state(n, stream):
+        try:
+            return State(n, "c64", stream=stream)
+        except torch.cuda.OutOfMemoryError:
+            # blocks of other sizes cached by torch's allocator: return them and retry
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            return State(n, "c64", stream=stream)
+
     def run(self, requests, time_scale=1.0, log=None):
         """Serve the requests (sorted by arrival); arrival times are replayed
         on the wall clock scaled by time_scale. Returns (results, stats)."""
         reqs = sorted(requests, key=lambda r: r.arrival)
-        pending = collections.deque()
-        small_wait = []                    # admitted small requests not started
-        large_wait = collections.deque()   # admitted large requests not started
-        running_large = []                 # (req, state, plan, event, start)
-        batch_run = None                   # (reqs, batch, event, start)
+        pend_small = collections.deque()      # arrived, not admitted (arrival order)
+        pend_large = collections.deque()
+        small_wait = collections.deque()      # admitted small requests not in a batch
+        large_wait = []                       # admitted large requests not started
+        running_large = []                    # (req, state, plan, event, start)
+        building = None                       # (take, future) of the next micro-batch
+        in_flight = collections.deque()       # launched micro-batches: (take, batch, event, start)
+        futures = {}
+        admitted_at = {}
         used = 0.0
+        small_used = 0.0
         slots = 0
         results = []
         i = 0
+        bsi = 0                               # next batch stream
+        lsi = 0                               # next large-request stream
+        host = {"batch_build_s": 0.0, "batches": 0, "batched_requests": 0, "large_tc": 0,
+                "admission_stalls": 0, "peak_used_bytes": 0.0}
+        batch_times, batch_sizes, large_times = [], [], []
+        stalled = False
         t0 = time.perf_counter()
-        s_i = 0
-        planned = {}
-        host = {"plan_wait_s": 0.0, "batch_build_s": 0.0, "batches": 0, "batched_requests": 0, "large_tc": 0}
-        batch_times, batch_sizes, large_times = [], [], []   # launch -> results, per micro-batch / large request
 
         def now():
             return (time.perf_counter() - t0) / time_scale
 
-        def plan_future(r, method, k, small):
-            if self.mode != "parts":
-                return self.pool.submit(lambda: (Plan(r.gates, r.n, "none", min(k, r.n)), False))
-            if small or not self.tc:
-                return self.pool.submit(lambda: (Plan(r.gates, r.n, method, min(k, r.n),
-                                                      dfs_trials=4 if method == "beam" else 16), False))
-            return self.pool.submit(lambda: autotune.choose_plan(r.gates, r.n)[:2])
+        def finish(r, start, done, norm, p0, am, pm, state):
+            nonlocal used, small_used, slots
+            results.append(Result(r.rid, r.n, r.arrival, admitted_at.pop(r.rid), start, done, norm, p0, am, pm,
+                                  state))
+            used -= self.state_bytes(r.n)
+            if self._small(r):
+                small_used -= self.state_bytes(r.n)
+            slots -= 1
 
-        while i < len(reqs) or pending or small_wait or large_wait or running_large or batch_run:
+        while (i < len(reqs) or pend_small or pend_large or small_wait or large_wait or running_large
+               or building or in_flight):
             t = now()
             while i < len(reqs) and reqs[i].arrival <= t:
                 r = reqs[i]
-                pending.append(r)
-                small = r.n <= self.small_n and self.mode == "parts"
-                planned[r.rid] = plan_future(r, self.method_small if small else self.method_large,
-                                             self.k_small if small else self.k_large, small)
+                small = self._small(r)
+                futures[r.rid] = (self.pool if small else self.pool_large).submit(self._plan, r)
+                (pend_small if small else pend_large).append(r)
                 i += 1
-            # admission in arrival order
-            while pending:
-                r = pending[0]
+            # admission: large requests in arrival order while the head fits
+            while pend_large:
+                r = pend_large[0]
                 b = self.state_bytes(r.n)
                 if slots >= self.max_slots or used + b > self.budget:
+                    if not stalled:
+                        host["admission_stalls"] += 1
+                    stalled = True
                     break
-                pending.popleft()
+                stalled = False
+                pend_large.popleft()
                 used += b
                 slots += 1
-                if r.n <= self.small_n and self.mode == "parts":
-                    small_wait.append(r)
-                else:
-                    large_wait.append(r)
-            # large requests start in arrival order as running slots free up
-            while large_wait and len(running_large) < max(1, self.large_running):
-                r = large_wait.popleft()
-                st = State(r.n, "c64", stream=self.streams[s_i % len(self.streams)])
-                s_i += 1
-                w0 = time.perf_counter()
-                plan, tc = planned.pop(r.rid).result()
-                host["plan_wait_s"] += time.perf_counter() - w0
+                admitted_at[r.rid] = now()
+                large_wait.append(r)
+            # small requests in arrival order beside them, within a share of
+            # the budget (small_budget), so the memory finished large requests
+            # free always reaches a waiting large head
+            while pend_small:
+                r = pend_small[0]
+                b = self.state_bytes(r.n)
+                if slots >= self.max_slots or used + b > self.budget or small_used + b > self.small_budget:
+                    break
+                pend_small.popleft()
+                used += b
+                small_used += b
+                slots += 1
+                admitted_at[r.rid] = now()
+                small_wait.append(r)
+            host["peak_used_bytes"] = max(host["peak_used_bytes"], used)
+            # large requests start as running slots free up, once planned
+            j = 0
+            while j < len(large_wait) and len(running_large) < self.large_running:
+                r = large_wait[j]
+                f = futures[r.rid]
+                if not f.done():
+                    j += 1
+                    continue
+                large_wait.pop(j)
+                plan, tc = futures.pop(r.rid).result()
                 host["large_tc"] += int(tc)
+                st = self._new_state(r.n, self.streams[lsi % len(self.streams)])
+                lsi += 1
                 start = now()
                 st.apply(plan, gatewise=self.mode != "parts", tc=tc)
                 ev = torch.cuda.Event()
                 ev.record(st.stream)
                 running_large.append((r, st, plan, ev, start))
-            # the batched kernel takes every waiting small request when idle
-            if batch_run is None and small_wait:
-                take, small_wait = small_wait[: self.batch_max], small_wait[self.batch_max:]
-                w0 = time.perf_counter()
-                plans = [planned.pop(r.rid).result()[0] for r in take]
-                w1 = time.perf_counter()
-                host["plan_wait_s"] += w1 - w0
-                start = now()
-                b = Batch.from_plans([(r.n, p) for r, p in zip(take, plans)], stream=self.batch_stream)
-                b.run()
-                host["batch_build_s"] += time.perf_counter() - w1
+            # the next micro-batch: every admitted small request whose plan is ready
+            if building is None and small_wait and len(in_flight) < 2:
+                take = []
+                rest = collections.deque()
+                while small_wait:
+                    r = small_wait.popleft()
+                    if len(take) < self.batch_max and futures[r.rid].done():
+                        take.append(r)
+                    else:
+                        rest.append(r)
+                small_wait = rest
+                if take:
+                    plans = [futures.pop(r.rid).result()[0] for r in take]
+                    stream = self.batch_streams[bsi % 2]
+                    bsi += 1
+                    building = (take, self.builder.submit(self._build_batch, take, plans, stream))
+            if building is not None and building[1].done() and len(in_flight) < 2:
+                take, fut = building
+                building = None
+                b, build_s = fut.result()
+                host["batch_build_s"] += build_s
                 host["batches"] += 1
                 host["batched_requests"] += len(take)
+                if in_flight:
+                    b.stream.wait_event(in_flight[-1][2])   # runs right after the batch in flight
+                b.run()
                 ev = torch.cuda.Event()
                 ev.record(b.stream)
-                batch_run = (take, b, ev, start)
+                in_flight.append((take, b, ev, now()))
             # completions
             still = []
             for r, st, plan, ev, start in running_large:
                 if ev.query():
-                    st.sync()
-                    probs = torch.empty(1 << r.n, dtype=torch.float32, device="cuda")
-                    with torch.cuda.stream(st.stream):
-                        norm = st.probs(probs)
-                        p0, am, pm = _summary(probs)
-                    res = Result(r.rid, r.n, r.arrival, start, now(), norm, p0, am, pm,
-                                 st.copy_to_host() if self.keep else None)
-                    results.append(res)
-                    large_times.append(res.done - start)
+                    norm, p0, am, pm = st.summary()
+                    done = now()
+                    finish(r, start, done, norm, p0, am, pm, st.copy_to_host() if self.keep else None)
+                    large_times.append(done - start)
                     st.close()
                     plan.close()
-                    used -= self.state_bytes(r.n)
-                    slots -= 1
                 else:
                     still.append((r, st, plan, ev, start))
             running_large = still
-            if batch_run is not None and batch_run[2].query():
-                take, b, ev, start = batch_run
+            if in_flight and in_flight[0][2].query():
+                take, b, ev, start = in_flight.popleft()
                 b.sync()
                 probs, norms = b.probs()
-                torch.cuda.current_stream().wait_stream(b.stream)
-                done_t = now()
-                batch_times.append(done_t - start)
+                ph = probs.cpu().numpy()
+                done = now()
+                batch_times.append(done - start)
                 batch_sizes.append(len(take))
                 for j, r in enumerate(take):
-                    p = probs[int(b.offsets[j]):int(b.offsets[j + 1])]
-                    p0, am, pm = _summary(p)
-                    results.append(Result(r.rid, r.n, r.arrival, start, done_t, float(norms[j]), p0, am, pm,
-                                          b.state_host(j) if self.keep else None))
-                    used -= self.state_bytes(r.n)
-                    slots -= 1
+                    p = ph[int(b.offsets[j]):int(b.offsets[j + 1])]
+                    am = int(np.argmax(p))
+                    finish(r, start, done, float(norms[j]), float(p[0]), am, float(p[am]),
+                           b.state_host(j) if self.keep else None)
                 b.close()
-                batch_run = None
-            if not (running_large or batch_run) and i < len(reqs) and not pending and not small_wait \
-                    and not large_wait:
+            idle = not (running_large or building or in_flight)
+            if idle and i < len(reqs) and not (pend_small or pend_large or small_wait or large_wait):
                 wait = reqs[i].arrival - now()
                 if wait > 0:
                     time.sleep(min(wait * time_scale, 0.01))
-            elif running_large or batch_run:
+            else:
                 time.sleep(0.0002)
         wall = now()
-        lat = np.array([r.latency for r in results]) if results else np.zeros(1)
+        last_arrival = reqs[-1].arrival if reqs else 0.0
+        stats = self._stats(results, wall, last_arrival, host, batch_times, batch_sizes, large_times)
+        results.sort(key=lambda r: r.rid)
+        return results, stats
+
+    def _stats(self, results, wall, last_arrival, host, batch_times, batch_sizes, large_times):
+        lat = [r.latency for r in results] or [0.0]
+        adm = [r.admitted - r.arrival for r in results] or [0.0]
         stats = {"requests": len(results), "wall_s": wall, "circuits_per_s": len(results) / max(wall, 1e-9),
-                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                 "mean_s": float(lat.mean()), "mode": self.mode, **host}
-        # where the latency goes: time from a micro-batch's (large request's)
-        # launch to its results, and the micro-batch sizes
+                 "p50_s": _pct(lat, 50), "p99_s": _pct(lat, 99), "mean_s": float(np.mean(lat)),
+                 "drain_s": max(0.0, wall - last_arrival), "admit_wait_p99_s": _pct(adm, 99),
+                 "admit_wait_max_s": float(np.max(adm)), "mode": self.mode, **host}
+        by_class = {}
+        for lo, hi in N_CLASSES:
+            v = [r.latency for r in results if lo <= r.n <= hi]
+            if v:
+                by_class[f"{lo}-{hi}"] = {"requests": len(v), "p50_s": round(_pct(v, 50), 4),
+                                          "p99_s": round(_pct(v, 99), 4), "max_s": round(max(v), 4)}
+        stats["by_n"] = by_class
+        # where the latency goes: launch -> results per micro-batch and large request
         for name, v in (("batch_s", batch_times), ("large_s", large_times)):
             if v:
                 stats[name + "_mean"] = round(float(np.mean(v)), 4)
                 stats[name + "_max"] = round(float(np.max(v)), 4)
         if batch_sizes:
             stats["batch_size_max"] = int(max(batch_sizes))
-        results.sort(key=lambda r: r.rid)
-        return results, stats
+            stats["batch_size_mean"] = round(float(np.mean(batch_sizes)), 1)
+        return stats
+
+    def close(self):
+        for p in (self.pool, self.pool_large, self.builder):
+            p.shutdown(wait=True)

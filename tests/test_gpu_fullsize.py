@@ -81,7 +81,7 @@ def test_benchmark_plans_match_oracle(layered28):
     n, g, ref = layered28
     for method, k, tc, _tile in STATE_CANDIDATES:
         stats = _check(api, n, g, ref, method, k, tc=tc, dfs_trials=BEAM_WIDTH if method == "beam" else 16)
-        if tc:
+        if tc and k <= 6:
             assert stats["dense"] == stats["passes"]
 
 

@@ -102,3 +102,49 @@ def test_served_mix_fidelity():
         fid = abs(np.vdot(ref, psi)) ** 2
         assert fid >= 0.99999, (r.rid, r.n, r.family, fid)
         assert np.abs(psi - ref).max() <= 1e-5, (r.rid, r.n, r.family)
+
+
+def test_large_requests_of_the_stream():
+    """A seeded sample of the serving stream's requests of 25-28 qubits (the
+    first four, seed 5), served together through admission and the large-
+    request path: each state has fidelity >= 0.99999 and max-abs <= 1e-5
+    against an FP64 reference (the closed form for the QFT family, the CPU
+    oracle up to 26 qubits, else the complex128 gate-list path), and the
+    device summary (norm, |a_0|^2, most likely state) matches the state."""
+    import torch
+    from oracle import closed_form as cf
+    _, api = native()
+    from paper_2205_06973_gb300.serving import Request, Server
+    arr = synth.serving_arrivals(20000, 60.0, seed=5)
+    reqs, i = [], 0
+    while len(reqs) < 4:
+        n, fam, g = synth.serving_request(i, seed=5)
+        if 25 <= n <= 28:
+            reqs.append(Request(len(reqs), n, g, arr[i] - arr[0] if reqs else 0.0, fam))
+        i += 1
+    srv = Server(budget_bytes=170e9, keep_states=True)
+    res, stats = srv.run(reqs)
+    srv.close()
+    assert stats["requests"] == 4
+    for r, out in zip(reqs, res):
+        psi = out.state.numpy().astype(np.complex128)
+        if r.family == "qft":
+            ref = cf.qft_state(sim.basis(r.n))
+        elif r.n <= 26:
+            ref = sim.run(r.n, r.gates)
+        else:
+            plan = api.Plan(r.gates, r.n, "dagp", 10)
+            st = api.State(r.n, "c128")
+            st.apply(plan, sync=True)
+            ref = st.copy_to_host().numpy()
+            st.close()
+            plan.close()
+        fid = abs(np.vdot(ref, psi)) ** 2
+        assert fid >= 0.99999, (r.rid, r.n, r.family, fid)
+        assert np.abs(psi - ref).max() <= 1e-5, (r.rid, r.n, r.family)
+        p = psi.real ** 2 + psi.imag ** 2
+        assert abs(out.norm - p.sum()) <= 1e-6, r.rid
+        assert abs(out.p0 - p[0]) <= 1e-9, r.rid
+        assert abs(out.pmax - p.max()) <= 1e-9 and p[out.argmax] >= p.max() - 1e-9, r.rid
+        del psi, ref, p
+        torch.cuda.empty_cache()
