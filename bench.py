@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--k", type=int, default=0, help="part qubit limit (0: autotuned default)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--tc", type=int, default=0, help="with --k: run parts of <= 6 qubits on the tensor cores")
+    ap.add_argument("--jit", type=int, default=0, help="with --k: gate-list parts on the plan's specialised kernels")
+    ap.add_argument("--no-grid", action="store_true", help="skip the builder x k grid and the complex128 line")
     ap.add_argument("--n", type=int, default=28)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
@@ -80,7 +82,8 @@ def peaks():
 
 KERNEL_SOURCES = {
     "k_dense6": ("dense.cu", "dense.hpp", "dense_common.cuh", "planner.cpp"),
-    "k_part": ("kernels.cu", "ops.cuh", "program.hpp", "planner.cpp"),
+    "k_part": ("kernels.cu", "ops.cuh", "ops_core.cuh", "program.hpp", "planner.cpp"),
+    "hisv_part": ("jit.cpp", "jit_prelude.cuh", "ops_core.cuh", "program.hpp", "planner.cpp"),
 }
 
 
@@ -344,6 +347,96 @@ def serving_full():
                                        **_serving_stats(st)}}), flush=True)
 
 
+# flops per amplitude of each gate kind in the paper's model of a gate pass
+# (Sec. III-A: a general one-qubit gate is a 2x2 complex matrix-vector
+# product per amplitude pair, 14 flops per amplitude): diagonal gates
+# multiply the amplitudes of their non-unit entries (RZ: all; P/S/T: half;
+# CP: a quarter), permutations and sign changes cost none
+GATE_FLOPS = {"H": 14, "RX": 14, "RY": 14, "X": 0, "Y": 0, "Z": 0, "RZ": 6, "P": 3, "S": 3, "T": 3,
+              "CX": 0, "CZ": 0, "SWAP": 0, "CP": 1.5}
+
+
+def circuit_flops(n, gates):
+    return sum(GATE_FLOPS[g[0]] for g in gates) * float(1 << n)
+
+
+def alu_peaks():
+    """Measured FMA rates of the CUDA cores (sv_alu_probe), FLOP/s."""
+    import ctypes
+    from paper_2205_06973_gb300 import _native as N
+    out = {}
+    for name, fp64 in (("fp64", 1), ("fp32", 0)):
+        v = ctypes.c_double()
+        N.check(N.lib.sv_alu_probe(fp64, ctypes.byref(v)))
+        out[name] = v.value
+    return out
+
+
+def _timed(st, plan, tc=False, jit=False, reps=2):
+    import torch
+    st.apply(plan, sync=True, tc=tc, jit=jit)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st.stream)
+    for _ in range(reps):
+        st.apply(plan, tc=tc, jit=jit)
+    e1.record(st.stream)
+    e1.synchronize()
+    st.sync()
+    return e0.elapsed_time(e1) / reps
+
+
+def grid_section(n, gates, st, peak):
+    """The paper's three builders at k in {8, 10, 12} on the complex64 state:
+    passes, time per step and pass GB/s (fraction of the measured copy
+    bandwidth) on the interpreter kernel and on the plan's specialised
+    kernels."""
+    from paper_2205_06973_gb300 import api
+    rows = []
+    for method in ("nat", "dfs", "dagp"):
+        for k in (8, 10, 12):
+            plan = api.Plan(gates, n, method, k)
+            passes = plan.stats("c64")["passes"]
+            row = {"method": method, "k": k, "passes": passes}
+            for name, jit in (("interpreter", False), ("specialised", True)):
+                if jit:
+                    row["compile_s"] = round(plan.specialise("c64"), 2)
+                ms = _timed(st, plan, jit=jit)
+                gbs = passes * 2 * st.nbytes / (ms / 1e3) / 1e9
+                row[name] = {"ms": round(ms, 2), "GBs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+            plan.close()
+            rows.append(row)
+    return {"workload": "28-qubit layered circuit, complex64 state (2 GiB), gate-list parts",
+            "peak_GBs": peak, "rows": rows}
+
+
+def c128_section(n, gates, peak, fp64_peak):
+    """The same circuit on a complex128 state (4 GiB, the paper's precision):
+    time per step, pass GB/s against the copy bandwidth and the circuit's
+    algorithmic FP64 flops (GATE_FLOPS) per second against the measured FP64
+    FMA rate, on the interpreter and on the specialised kernels."""
+    from paper_2205_06973_gb300 import api
+    st = api.State(n, "c128")
+    flops = circuit_flops(n, gates)
+    rows = []
+    for method, k, jit in (("dagp", 10, False), ("dagp", 10, True), ("beam", 10, True), ("beam", 12, True)):
+        plan = api.Plan(gates, n, method, k, dfs_trials=16)
+        passes = plan.stats("c128")["passes"]
+        cs = plan.specialise("c128") if jit else 0.0
+        ms = _timed(st, plan, jit=jit, reps=1)
+        gbs = passes * 2 * st.nbytes / (ms / 1e3) / 1e9
+        fl = flops / (ms / 1e3)
+        rows.append({"method": method, "k": k, "kernel": "specialised" if jit else "interpreter", "passes": passes,
+                     "ms": round(ms, 1), "GBs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
+                     "fp64_tflops": round(fl / 1e12, 3), "fp64_frac": round(fl / fp64_peak, 4),
+                     "compile_s": round(cs, 2)})
+        plan.close()
+    norm = st.probs()
+    st.close()
+    return {"workload": "28-qubit layered circuit, complex128 state (4 GiB)", "algorithmic_fp64_flops": flops,
+            "fp64_peak_tflops": round(fp64_peak / 1e12, 3), "rows": rows, "norm": norm}
+
+
 def run_ours(a):
     import torch
     ws, rank, local = dist_env()
@@ -358,22 +451,25 @@ def run_ours(a):
     n, gates = synth.layered_28q(n=a.n)
     st = api.State(n, "c64", tile=a.tile)
     if a.k:
-        choice = {"method": a.method, "k": a.k, "tc": bool(a.tc), "tile": a.tile, "trials": []}
+        choice = {"method": a.method, "k": a.k, "tc": bool(a.tc), "tile": a.tile, "jit": bool(a.jit), "trials": []}
     else:
         from paper_2205_06973_gb300 import autotune
         choice = autotune.tune_state(f"layered{n}", n, gates, "c64", state=st, use_cache=False)
     k, tc, method = choice["k"], bool(choice["tc"]), choice["method"]
+    jit = bool(choice.get("jit"))
     if choice.get("tile"):
         st = api.State(n, "c64", tile=choice["tile"])
     from paper_2205_06973_gb300.autotune import BEAM_WIDTH
     plan = api.Plan(gates, n, method, k, dfs_trials=BEAM_WIDTH if method == "beam" else 16)
     stats = plan.stats("c64", choice.get("tile", 0), tc=tc)
+    if jit:
+        plan.specialise("c64", choice.get("tile", 0), tc=tc)
     passes = stats["passes"]
     bytes_per_pass = 2 * st.nbytes
     bytes_per_step = passes * bytes_per_pass
 
     for _ in range(max(a.warmup, 3)):
-        st.apply(plan, tc=tc)
+        st.apply(plan, tc=tc, jit=jit)
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
@@ -383,7 +479,7 @@ def run_ours(a):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st.stream)
     for _ in range(a.steps):
-        st.apply(plan, tc=tc)
+        st.apply(plan, tc=tc, jit=jit)
     e1.record(st.stream)
     torch.cuda.synchronize()
     barrier(ws)
@@ -397,8 +493,9 @@ def run_ours(a):
     launch_ms = ms / passes
     peak, peak_kind = peaks()
     achieved = bytes_per_pass / (launch_ms / 1e3) / 1e9
-    kernel = "k_dense6" if (tc and stats["dense"] * 2 >= passes) else "k_part"
-    wkey = f"layered{n}_{method}_k{k}_c64_{'tc' if tc else 't' + str(choice.get('tile') or 'auto')}"
+    kernel = "k_dense6" if (tc and stats["dense"] * 2 >= passes) else ("hisv_part" if jit else "k_part")
+    wkey = (f"layered{n}_{method}_k{k}_c64_{'tc' if tc else 't' + str(choice.get('tile') or 'auto')}"
+            f"{'_jit' if jit else ''}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                 "traffic": traffic_from_profile(kernel, wkey), "kernel": kernel,
@@ -415,7 +512,7 @@ def run_ours(a):
         host_out = [torch.empty(1 << n, dtype=torch.complex64).pin_memory() for _ in range(2)]
         for i in range(2):
             sts[i].upload(host_in)
-            sts[i].apply(plan, tc=tc)
+            sts[i].apply(plan, tc=tc, jit=jit)
             sts[i].download(host_out[i])
         for x in sts:
             x.sync()
@@ -427,7 +524,7 @@ def run_ours(a):
             if i >= 2:
                 x.sync()          # its step i-2 result has reached host memory
             x.upload(host_in)
-            x.apply(plan, tc=tc)
+            x.apply(plan, tc=tc, jit=jit)
             x.download(host_out[i % 2])
         for x in sts:
             x.sync()
@@ -462,6 +559,13 @@ def run_ours(a):
         cpu = cpu_baseline_oracle(n, gates, pog, P, max_parts=64, budget_s=20.0)
         cpu["sample"] += f" ({method} k={k} plan)"
 
+    grid = c128 = alu = None
+    if rank == 0 and not a.no_grid:
+        alu = alu_peaks()
+        grid = grid_section(n, gates, st, peak)
+        c128 = c128_section(n, gates, peak, alu["fp64"])
+        alu = {k: round(v / 1e12, 3) for k, v in alu.items()}
+
     batch = serving = None
     if rank == 0 and not a.no_batch:
         batch = batch_section(a.batch_circuits)
@@ -480,6 +584,7 @@ def run_ours(a):
                            "l2": "state (2 GiB) larger than L2 (129 MB); no flush needed"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": passes * a.steps, "compare": compare, "norm": norm,
+                "grid": grid, "c128": c128, "alu_peak_tflops": alu,
                 "batch": batch, "serving": serving}
         print(json.dumps(line), flush=True)
     st.close()

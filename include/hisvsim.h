@@ -88,6 +88,12 @@ typedef struct sv_plan sv_plan;
 #define SV_FLAG_TC_DENSE 0x4u   /* complex64, n >= 13: parts of at most 6 qubits run as one fused
                                    64x64 unitary on the tensor cores (split BF16, FP32
                                    accumulation); other parts keep the gate-list kernel */
+#define SV_FLAG_SPECIALISE 0x8u /* gate-list parts run as kernels generated for this plan, with
+                                   the tile layout, register phases and every gate (with its
+                                   coefficients) compiled in (NVRTC, sm_103a); compiled at the
+                                   first apply for the precision and tile (or by
+                                   sv_plan_specialise) and kept in the plan. Same arithmetic as
+                                   the interpreter kernel; SV_ERR_CUDA if NVRTC is missing */
 
 /* ---------------------------------------------------------------- state ---
  * sv_create: make an n-qubit state (1 <= n <= 36) initialised to |0...0>.
@@ -156,6 +162,24 @@ sv_status sv_plan_export(const sv_plan *p, uint32_t *part_of_gate, size_t n_gate
  * pointer may be NULL). Compiles on the host if needed; no device work. */
 sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int tile_qubits, uint32_t flags, uint32_t *passes,
                         uint32_t *phases, uint32_t *ops, uint32_t *dense);
+/* sv_plan_specialise: generate and compile the plan's specialised part
+ * kernels (SV_FLAG_SPECIALISE) for the precision, tile (0 = default) and
+ * flags (SV_FLAG_TC_DENSE: only the parts that stay on the gate-list kernel)
+ * now instead of at the first apply. load = 0 compiles on the host only and
+ * discards the code (no device needed: a check of the generated source);
+ * load = 1 loads it into the plan for the current device. *compile_seconds
+ * (may be NULL) receives the wall time of the compilation. Errors: SV_ERR_ARG
+ * (bad tile), SV_ERR_PARTITION (plan does not compile), SV_ERR_CUDA (NVRTC
+ * missing, compile or load error; sv_last_error has the log). Host thread
+ * safe like sv_apply_parts. */
+sv_status sv_plan_specialise(sv_plan *p, sv_precision prec, int tile_qubits, uint32_t flags, int load,
+                             double *compile_seconds);
+/* sv_plan_source: the generated CUDA source of gate-list part i (execution
+ * order among the gate-list parts) of the plan's program for prec, tile and
+ * flags, copied NUL-terminated into buf (cap bytes); *len receives the
+ * source length. Host only. */
+sv_status sv_plan_source(sv_plan *p, sv_precision prec, int tile_qubits, uint32_t flags, uint32_t part, char *buf,
+                         size_t cap, size_t *len);
 sv_status sv_plan_destroy(sv_plan *p);
 
 /* ---------------------------------------------------------------- apply ---
@@ -293,6 +317,14 @@ sv_status sv_batch_destroy(sv_batch *b);
 #define SV_NOALLOC_DEFAULT_BLOCKS 1216
 sv_status sv_probs_noalloc(const void *dev_state, int n_qubits, sv_precision prec, void *dev_probs,
                            int out_fp64, double *dev_norm, int n_blocks, void *stream);
+
+/* sv_alu_probe: the measured FMA rate of the current device's CUDA cores in
+ * FP64 (fp64 != 0) or FP32, in FLOP/s (an FMA counts two): the roofline of
+ * the complex128 path, which is bound by FP64 arithmetic rather than by HBM
+ * (Sec. III-A counts the flops of a gate). Best of a few timed launches of
+ * independent FMA chains on every SM; synchronises the device's legacy
+ * stream. Not part of the paper; a measurement helper of this library. */
+sv_status sv_alu_probe(int fp64, double *flops_per_s);
 
 /* Thread-local description of the last non-OK status (never NULL). */
 const char *sv_last_error(void);

@@ -20,6 +20,7 @@ METHODS = {"none": SV_PART_NONE, "nat": SV_PART_NAT, "dfs": SV_PART_DFS, "dagp":
 SV_FLAG_GATEWISE = 0x1
 SV_FLAG_SYNC = 0x2
 SV_FLAG_TC_DENSE = 0x4
+SV_FLAG_SPECIALISE = 0x8
 SV_NOALLOC_MAX_BLOCKS = 4096
 
 GATE_KINDS = ("H", "X", "Y", "Z", "S", "T", "RX", "RY", "RZ", "P", "CX", "CZ", "CP", "SWAP")
@@ -67,11 +68,16 @@ _SIGS = {
     "sv_plan_export": ([_vp, _vp, ctypes.c_size_t, _u32p], ctypes.c_int),
     "sv_plan_stats": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p], ctypes.c_int),
     "sv_plan_destroy": ([_vp], ctypes.c_int),
+    "sv_plan_specialise": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.c_int,
+                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "sv_plan_source": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_char_p,
+                        ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "sv_apply_parts": ([_vp, _vp, ctypes.c_uint32], ctypes.c_int),
     "sv_measure_probs": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "sv_measure_summary": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "sv_batch_prepare": ([_vp], ctypes.c_int),
+    "sv_alu_probe": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "sv_probs_noalloc": ([_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "sv_batch_create": ([ctypes.c_uint32, _vp, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
     "sv_batch_set_plan": ([_vp, ctypes.c_uint32, _vp], ctypes.c_int),

@@ -40,6 +40,24 @@ class Plan:
                                     ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
         return {"passes": a.value, "phases": b.value, "ops": c.value, "dense": d.value}
 
+    def specialise(self, precision="c64", tile=0, tc=False, load=True):
+        """Generate and compile the plan's specialised part kernels
+        (SV_FLAG_SPECIALISE) now; load=False only compiles (no device).
+        Returns the compile time in seconds."""
+        s = ctypes.c_double()
+        N.check(N.lib.sv_plan_specialise(self.h, N.SV_C128 if precision == "c128" else N.SV_C64, tile,
+                                         N.SV_FLAG_TC_DENSE if tc else 0, 1 if load else 0, ctypes.byref(s)))
+        return s.value
+
+    def source(self, part, precision="c64", tile=0, tc=False):
+        """Generated CUDA source of gate-list part ``part``."""
+        n = ctypes.c_size_t()
+        args = (self.h, N.SV_C128 if precision == "c128" else N.SV_C64, tile, N.SV_FLAG_TC_DENSE if tc else 0, part)
+        N.check(N.lib.sv_plan_source(*args, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value + 1)
+        N.check(N.lib.sv_plan_source(*args, buf, n.value + 1, ctypes.byref(n)))
+        return buf.value.decode()
+
     def close(self):
         if self.h:
             N.lib.sv_plan_destroy(self.h)
@@ -96,9 +114,9 @@ class State:
         N.check(N.lib.sv_download(self.h, ctypes.c_void_p(out.data_ptr()), self.nbytes))
         return out
 
-    def apply(self, plan: Plan, gatewise=False, sync=False, tc=False):
+    def apply(self, plan: Plan, gatewise=False, sync=False, tc=False, jit=False):
         flags = ((N.SV_FLAG_GATEWISE if gatewise else 0) | (N.SV_FLAG_SYNC if sync else 0)
-                 | (N.SV_FLAG_TC_DENSE if tc else 0))
+                 | (N.SV_FLAG_TC_DENSE if tc else 0) | (N.SV_FLAG_SPECIALISE if jit else 0))
         N.check(N.lib.sv_apply_parts(self.h, plan.h, flags))
 
     def probs(self, out=None, fp64=False):

@@ -55,23 +55,27 @@ def cached_k(workload, method, precision):
     return None
 
 
-def _time_apply(st, plan, tc, reps):
-    st.apply(plan, sync=True, tc=tc)
+def _time_apply(st, plan, tc, reps, jit=False):
+    st.apply(plan, sync=True, tc=tc, jit=jit)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st.stream)
     for _ in range(reps):
-        st.apply(plan, tc=tc)
+        st.apply(plan, tc=tc, jit=jit)
     e1.record(st.stream)
     e1.synchronize()
     st.sync()
     return e0.elapsed_time(e1) / reps
 
 
+# (part builder, k, tensor-core dense parts, tile (0 = default), specialised
+# gate-list kernels)
 STATE_CANDIDATES = (
-    ("beam", 6, True, 0), ("dagp", 6, True, 0), ("beam", 5, True, 0), ("dfs", 6, True, 0),
-    ("beam", 8, True, 0), ("beam", 10, False, 0), ("dagp", 10, False, 0), ("beam", 12, False, 0),
-    ("dagp", 8, False, 0),
+    ("beam", 6, True, 0, False), ("dagp", 6, True, 0, False), ("beam", 5, True, 0, False),
+    ("dfs", 6, True, 0, False), ("beam", 8, True, 0, False), ("beam", 10, False, 0, False),
+    ("dagp", 10, False, 0, False), ("beam", 12, False, 0, False), ("dagp", 8, False, 0, False),
+    ("beam", 8, False, 0, True), ("beam", 10, False, 0, True), ("beam", 12, False, 0, True),
+    ("dagp", 10, False, 0, True), ("beam", 8, True, 0, True),
 )
 BEAM_WIDTH = 64   # beam builder width for the tuned plans (0.3 s for 2520 gates)
 
@@ -87,7 +91,9 @@ def tune_state(workload, n, gates, precision="c64", candidates=STATE_CANDIDATES,
     own = state is None
     st = state if state is not None else api.State(n, precision)
     trials = []
-    for method, k, tc, tile in candidates:
+    for cand in candidates:
+        method, k, tc, tile = cand[:4]
+        jit = cand[4] if len(cand) > 4 else False
         if precision == "c128" and tc:
             continue
         if k > n:
@@ -95,23 +101,26 @@ def tune_state(workload, n, gates, precision="c64", candidates=STATE_CANDIDATES,
         t0 = time.perf_counter()
         plan = api.Plan(gates, n, method, k, dfs_trials=BEAM_WIDTH if method == "beam" else 16)
         plan_s = time.perf_counter() - t0
+        compile_s = 0.0
         try:
             if tile:
                 from . import _native as N
                 N.check(N.lib.sv_set_tile(st.h, tile))
-            ms = _time_apply(st, plan, tc, reps)
+            if jit:
+                compile_s = plan.specialise(precision, tile, tc=tc)
+            ms = _time_apply(st, plan, tc, reps, jit=jit)
             stats = plan.stats(precision, tile, tc=tc)
-        except Exception as e:   # a configuration the library rejects (tile too small)
+        except Exception as e:   # a configuration the library rejects (tile too small, no NVRTC)
             if log:
-                log(f"tune: skip {method} k={k} tc={tc} tile={tile}: {e}")
+                log(f"tune: skip {method} k={k} tc={tc} tile={tile} jit={jit}: {e}")
             plan.close()
             continue
         finally:
             if tile:
                 from . import _native as N
                 N.lib.sv_set_tile(st.h, 0)
-        trials.append({"method": method, "k": k, "tc": tc, "tile": tile, "ms": round(ms, 3),
-                       "passes": stats["passes"], "plan_s": round(plan_s, 3)})
+        trials.append({"method": method, "k": k, "tc": tc, "tile": tile, "jit": jit, "ms": round(ms, 3),
+                       "passes": stats["passes"], "plan_s": round(plan_s, 3), "compile_s": round(compile_s, 2)})
         plan.close()
     if own:
         st.close()

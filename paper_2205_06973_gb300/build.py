@@ -21,7 +21,12 @@ LIB = os.path.join(HERE, "libhisvsim.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "dense.cu", "dense_batch.cu", "noalloc.cu", "batch.cu", "abi.cpp", "batch_abi.cpp", "partition.cpp", "planner.cpp", "qasm.cpp"]
+SOURCES = ["kernels.cu", "dense.cu", "dense_batch.cu", "noalloc.cu", "batch.cu", "abi.cpp", "batch_abi.cpp",
+           "partition.cpp", "planner.cpp", "qasm.cpp", "jit.cpp"]
+# headers handed to the run-time compiler (NVRTC) by jit.cpp, embedded as
+# string literals: name in the generated include file -> source header
+JIT_HEADERS = (("kJitOpsCore", "ops_core.cuh"), ("kJitPrelude", "jit_prelude.cuh"))
+JIT_INC = os.path.join(BUILD, "jit_sources.inc")
 
 
 def _nvcc():
@@ -39,9 +44,11 @@ def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     deps = [path] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".hpp", ".cuh"))]
     deps.append(os.path.join(INCLUDE, "hisvsim.h"))
+    if src == "jit.cpp":
+        deps.append(JIT_INC)
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
-    cmd = [_nvcc(), "-std=c++17", "-O3", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-c", path, "-o", obj]
+    cmd = [_nvcc(), "-std=c++17", "-O3", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", BUILD, "-c", path, "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ARCH + ["-lineinfo", "--expt-relaxed-constexpr"]
         if verbose:
@@ -56,11 +63,29 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
+def _write_jit_sources():
+    """The run-time compiler's headers as C++ raw string literals (rewritten
+    only when their text changes, so the dependency check stays exact)."""
+    text = "// generated by build.py from csrc/ops_core.cuh and csrc/jit_prelude.cuh\n"
+    for name, hdr in JIT_HEADERS:
+        with open(os.path.join(CSRC, hdr)) as f:
+            body = f.read()
+        assert ")HISVSRC" not in body
+        text += f'static const char *{name} = R"HISVSRC({body})HISVSRC";\n'
+    if os.path.exists(JIT_INC):
+        with open(JIT_INC) as f:
+            if f.read() == text:
+                return
+    with open(JIT_INC, "w") as f:
+        f.write(text)
+
+
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     if force:
         for f in os.listdir(BUILD):
             os.remove(os.path.join(BUILD, f))
+    _write_jit_sources()
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))

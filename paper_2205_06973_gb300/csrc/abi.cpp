@@ -279,8 +279,67 @@ sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int t, uint32_t flags, ui
     return SV_OK;
 }
 
+// The plan's specialised part kernels for (precision, tile, dense mode),
+// compiled and loaded on first use.
+static sv_status get_jit_program(sv_plan *p, bool fp64, int t, int dense, const Program *hp, JitProgram **out) {
+    std::lock_guard<std::recursive_mutex> lk(p->mu);
+    auto key = std::make_tuple(fp64, t, dense);
+    auto it = p->jit_progs.find(key);
+    if (it == p->jit_progs.end()) {
+        std::unique_ptr<JitProgram> jp(new JitProgram());
+        std::string err;
+        if (!jit_compile(*hp, *jp, err, true)) return fail(SV_ERR_CUDA, "specialised part kernels: " + err);
+        it = p->jit_progs.emplace(key, std::move(jp)).first;
+    }
+    *out = it->second.get();
+    return SV_OK;
+}
+
+sv_status sv_plan_specialise(sv_plan *p, sv_precision prec, int t, uint32_t flags, int load, double *compile_s) {
+    if (!p) return fail(SV_ERR_ARG, "plan is NULL");
+    const bool fp64 = prec == SV_C128;
+    if (t == 0) t = default_tile(fp64, p->max_part);
+    if (t < part_tmin() || t > part_tmax(fp64)) return fail(SV_ERR_ARG, "tile_qubits out of range");
+    const Program *hp = nullptr;
+    sv_status st = get_host_program(p, fp64, t, dense_mode(flags, fp64), &hp);
+    if (st != SV_OK) return st;
+    if (load) {
+        JitProgram *jp = nullptr;
+        st = get_jit_program(p, fp64, t, dense_mode(flags, fp64), hp, &jp);
+        if (st != SV_OK) return st;
+        if (compile_s) *compile_s = jp->compile_s;
+        return SV_OK;
+    }
+    JitProgram jp;
+    std::string err;
+    if (!jit_compile(*hp, jp, err, false)) return fail(SV_ERR_CUDA, "specialised part kernels: " + err);
+    if (compile_s) *compile_s = jp.compile_s;
+    return SV_OK;
+}
+
+sv_status sv_plan_source(sv_plan *p, sv_precision prec, int t, uint32_t flags, uint32_t part, char *buf, size_t cap,
+                         size_t *len) {
+    if (!p) return fail(SV_ERR_ARG, "plan is NULL");
+    const bool fp64 = prec == SV_C128;
+    if (t == 0) t = default_tile(fp64, p->max_part);
+    if (t < part_tmin() || t > part_tmax(fp64)) return fail(SV_ERR_ARG, "tile_qubits out of range");
+    const Program *hp = nullptr;
+    sv_status st = get_host_program(p, fp64, t, dense_mode(flags, fp64), &hp);
+    if (st != SV_OK) return st;
+    if (part >= hp->parts.size()) return fail(SV_ERR_ARG, "part index out of range");
+    const std::string src = jit_part_source(*hp, part);
+    if (len) *len = src.size();
+    if (buf && cap) {
+        const size_t m = std::min(cap - 1, src.size());
+        std::memcpy(buf, src.data(), m);
+        buf[m] = '\0';
+    }
+    return SV_OK;
+}
+
 sv_status sv_plan_destroy(sv_plan *p) {
     if (!p) return fail(SV_ERR_ARG, "plan is NULL");
+    for (auto &kv : p->jit_progs) jit_release(*kv.second);
     int cur = 0;
     cudaGetDevice(&cur);
     for (auto &kv : p->dev_progs) {   // no apply of the plan may be in flight
@@ -394,6 +453,11 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
         const DevProgram *dp = nullptr;
         st = get_dev_program(s, p, t, dense_mode(flags, fp64), &hp, &dp);
         if (st != SV_OK) return st;
+        JitProgram *jp = nullptr;
+        if ((flags & SV_FLAG_SPECIALISE) && !hp->parts.empty()) {
+            st = get_jit_program(p, fp64, t, dense_mode(flags, fp64), hp, &jp);
+            if (st != SV_OK) return st;
+        }
         if (!hp->dense.empty()) {
             const size_t need = hp->dense.size() + 1;
             if (s->dnorm_cap < need) {
@@ -412,7 +476,9 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
         for (size_t i = 0; i < hp->kind.size(); i++) {
             const uint32_t j = hp->index[i];
             cudaError_t e;
-            if (hp->kind[i] == 0)
+            if (hp->kind[i] == 0 && jp)
+                e = jit_launch(*jp, j, s->buf, hp->n_tiles[j], s->stream);
+            else if (hp->kind[i] == 0)
                 e = launch_part(fp64, hp->t, s->buf, hp->parts[j], dp->d_phases, dp->d_ops, dp->d_coefs,
                                 hp->n_tiles[j], s->stream);
             else
@@ -438,6 +504,12 @@ sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *nor
         CUDA_TRY(cudaStreamSynchronize(s->stream));
         *norm_out = s->h_norm;
     }
+    return SV_OK;
+}
+
+sv_status sv_alu_probe(int fp64, double *flops_per_s) {
+    if (!flops_per_s) return fail(SV_ERR_ARG, "flops_per_s is NULL");
+    CUDA_TRY(alu_probe(fp64 != 0, flops_per_s, nullptr));
     return SV_OK;
 }
 

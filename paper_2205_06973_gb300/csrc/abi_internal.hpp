@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/hisvsim.h"
+#include "jit.hpp"
 #include "partition.hpp"
 #include "planner.hpp"
 
@@ -65,6 +66,7 @@ struct sv_plan {
     std::map<std::tuple<bool, int, int>, std::unique_ptr<Program>> host_progs;   // (fp64, t, dense)
     std::map<std::tuple<int, bool, int, int>, DevProgram> dev_progs;             // (dev, fp64, t, dense)
     std::vector<std::vector<double>> mats;                                 // gatewise matrices
+    std::map<std::tuple<bool, int, int>, std::unique_ptr<hisv::JitProgram>> jit_progs;   // (fp64, t, dense)
     // the caches above are filled on first use; several host threads may
     // apply one plan (map nodes never move, so returned pointers stay valid)
     std::recursive_mutex mu;

@@ -511,6 +511,59 @@ cudaError_t launch_summary(bool fp64, const void *sv, int n, double *scratch, in
     return cudaGetLastError();
 }
 
+// ALU peak probe: 8 independent FMA chains per thread (enough to cover the
+// FMA latency), over a grid that fills every SM; the result is stored so the
+// chains are not removed.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(T *__restrict__ out, int iters, T b, T c) {
+    T x[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) x[j] = (T)(threadIdx.x + j);
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) x[j] = fma(x[j], b, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) s += x[j];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t alu_probe(bool fp64, double *flops_per_s, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = sms * 8, threads = 256;
+    void *out = nullptr;
+    e = cudaMallocAsync(&out, (size_t)blocks * threads * 8, st);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0.0;
+    int iters = 256;
+    for (int rep = 0; rep < 8 && e == cudaSuccess; rep++) {
+        cudaEventRecord(e0, st);
+        if (fp64) k_fma_probe<double><<<blocks, threads, 0, st>>>((double *)out, iters, 0.999999, 1e-7);
+        else k_fma_probe<float><<<blocks, threads, 0, st>>>((float *)out, iters, 0.999999f, 1e-7f);
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+        if (ms > 0.f) best = flops / (ms * 1e-3) > best ? flops / (ms * 1e-3) : best;
+        if (ms < 20.f && iters < (1 << 24)) iters *= 4;   // grow to a launch of tens of milliseconds
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(out, st);
+    if (e != cudaSuccess) return e;
+    *flops_per_s = best;
+    return cudaGetLastError();
+}
+
 template <typename Real>
 __global__ void k_set_one(typename CT<Real>::T *sv, uint64_t idx) {
     typename CT<Real>::T v;

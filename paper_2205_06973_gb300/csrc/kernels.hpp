@@ -31,6 +31,9 @@ cudaError_t launch_probs(bool fp64, const void *sv, int n, void *out, int out_fp
 // doubles, out 4 (out[3] holds the index's bits).
 cudaError_t launch_summary(bool fp64, const void *sv, int n, double *scratch, int nblocks, double *out,
                            cudaStream_t st);
+// FMA throughput of the CUDA cores in FP64 (fp64) or FP32, in FLOP/s (best of
+// a few timed launches over every SM; synchronises the stream).
+cudaError_t alu_probe(bool fp64, double *flops_per_s, cudaStream_t st);
 cudaError_t launch_set_basis(bool fp64, void *sv, int n, uint64_t idx, cudaStream_t st);
 
 }  // namespace hisv

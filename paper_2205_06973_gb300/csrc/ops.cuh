@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "ops_core.cuh"
 #include "program.hpp"
 
 namespace hisv {
@@ -18,107 +19,6 @@ namespace hisv {
 template <typename Real> struct CT;
 template <> struct CT<float> { typedef float2 T; };
 template <> struct CT<double> { typedef double2 T; };
-
-// ------------------------------------------------------------------------
-// register-bit operations; B, A are compile-time register bits
-// ------------------------------------------------------------------------
-// Hadamard without its 1/sqrt2: the planner folds the factor into the part's
-// store factor, so each H costs one add and one subtract per amplitude pair.
-template <int NR, int B, typename C>
-__device__ __forceinline__ void op_h(C (&a)[NR]) {
-#pragma unroll
-    for (int i = 0; i < NR; i++) {
-        if (i & (1 << B)) continue;
-        const int j = i | (1 << B);
-        const C x = a[i], y = a[j];
-        a[i].x = x.x + y.x; a[i].y = x.y + y.y;
-        a[j].x = x.x - y.x; a[j].y = x.y - y.y;
-    }
-}
-
-template <int NR, int B, typename C, typename Real>
-__device__ __forceinline__ void op_u2(C (&a)[NR], const Real *m) {
-    const Real m00r = m[0], m00i = m[1], m01r = m[2], m01i = m[3];
-    const Real m10r = m[4], m10i = m[5], m11r = m[6], m11i = m[7];
-#pragma unroll
-    for (int i = 0; i < NR; i++) {
-        if (i & (1 << B)) continue;
-        const int j = i | (1 << B);
-        const C x = a[i], y = a[j];
-        a[i].x = m00r * x.x - m00i * x.y + m01r * y.x - m01i * y.y;
-        a[i].y = m00r * x.y + m00i * x.x + m01r * y.y + m01i * y.x;
-        a[j].x = m10r * x.x - m10i * x.y + m11r * y.x - m11i * y.y;
-        a[j].y = m10r * x.y + m10i * x.x + m11r * y.y + m11i * y.x;
-    }
-}
-
-template <int NR, int B, typename C, typename Real>
-__device__ __forceinline__ void op_rx(C (&a)[NR], Real c, Real s) {
-#pragma unroll
-    for (int i = 0; i < NR; i++) {
-        if (i & (1 << B)) continue;
-        const int j = i | (1 << B);
-        const C x = a[i], y = a[j];
-        a[i].x = c * x.x + s * y.y; a[i].y = c * x.y - s * y.x;
-        a[j].x = s * x.y + c * y.x; a[j].y = c * y.y - s * x.x;
-    }
-}
-
-template <int NR, int B, typename C, typename Real>
-__device__ __forceinline__ void op_ry(C (&a)[NR], Real c, Real s) {
-#pragma unroll
-    for (int i = 0; i < NR; i++) {
-        if (i & (1 << B)) continue;
-        const int j = i | (1 << B);
-        const C x = a[i], y = a[j];
-        a[i].x = c * x.x - s * y.x; a[i].y = c * x.y - s * y.y;
-        a[j].x = s * x.x + c * y.x; a[j].y = s * x.y + c * y.y;
-    }
-}
-
-template <typename C, typename Real>
-__device__ __forceinline__ void cmul_in(C &v, Real dr, Real di) {
-    const Real x = v.x, y = v.y;
-    v.x = x * dr - y * di;
-    v.y = x * di + y * dr;
-}
-
-template <int NR, int B, typename C, typename Real>
-__device__ __forceinline__ void op_d(C (&a)[NR], Real d0r, Real d0i, Real d1r, Real d1i) {
-#pragma unroll
-    for (int i = 0; i < NR; i++) {
-        if (i & (1 << B)) cmul_in(a[i], d1r, d1i);
-        else cmul_in(a[i], d0r, d0i);
-    }
-}
-
-template <int NR, int B, typename C, typename Real>
-__device__ __forceinline__ void op_p(C (&a)[NR], Real dr, Real di) {
-#pragma unroll
-    for (int i = 0; i < NR; i++)
-        if (i & (1 << B)) cmul_in(a[i], dr, di);
-}
-
-template <int NR, int B, typename C>
-__device__ __forceinline__ void op_z(C (&a)[NR]) {
-#pragma unroll
-    for (int i = 0; i < NR; i++)
-        if (i & (1 << B)) { a[i].x = -a[i].x; a[i].y = -a[i].y; }
-}
-
-template <int NR, int A, int B, typename C, typename Real>
-__device__ __forceinline__ void op_cp(C (&a)[NR], Real dr, Real di) {
-#pragma unroll
-    for (int i = 0; i < NR; i++)
-        if ((i & (1 << A)) && (i & (1 << B))) cmul_in(a[i], dr, di);
-}
-
-template <int NR, int A, int B, typename C>
-__device__ __forceinline__ void op_cz(C (&a)[NR]) {
-#pragma unroll
-    for (int i = 0; i < NR; i++)
-        if ((i & (1 << A)) && (i & (1 << B))) { a[i].x = -a[i].x; a[i].y = -a[i].y; }
-}
 
 // Call f(integral_constant<int, b>) for a runtime register bit b < R.
 template <int R, int B = 0, typename F>
@@ -128,17 +28,6 @@ __device__ __forceinline__ void with_bit(int b, F &&f) {
         else with_bit<R, B + 1>(b, static_cast<F &&>(f));
     }
 }
-
-// Swizzled shared-memory index contribution of tile slot p. The swizzle XORs
-// the slot bits above the bank group into the low bits (linear over GF(2)),
-// so a warp whose lane bits sit on slots of distinct residues touches
-// distinct banks: 8-byte elements use 4-bit groups, 16-byte elements 3-bit.
-template <typename Real>
-__device__ __forceinline__ uint32_t swz(int p) {
-    if constexpr (sizeof(Real) == 4) return p < 4 ? (1u << p) : ((1u << p) | (1u << (p & 3)));
-    else return p < 3 ? (1u << p) : ((1u << p) | (1u << (p % 3)));
-}
-
 
 // Register permutations (X, Y, CX) go through shared memory: the thread
 // stores its amplitudes into its own slots of the tile buffer (slot of

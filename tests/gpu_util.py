@@ -20,7 +20,7 @@ def random_state(n, seed):
 
 
 def run_gpu(n, gates, method="dagp", k=8, precision="c64", tile=0, psi=None, basis=0, gatewise=False,
-            seed=0, tc=False):
+            seed=0, tc=False, jit=False):
     _, api = native()
     plan = api.Plan(gates, n, method if not gatewise else "none", k, seed=seed)
     st = api.State(n, precision, tile=tile)
@@ -29,7 +29,7 @@ def run_gpu(n, gates, method="dagp", k=8, precision="c64", tile=0, psi=None, bas
         st.upload(torch.from_numpy(np.ascontiguousarray(psi)).to(dt).pin_memory())
     else:
         st.set_basis(basis)
-    st.apply(plan, gatewise=gatewise, sync=True, tc=tc)
+    st.apply(plan, gatewise=gatewise, sync=True, tc=tc, jit=jit)
     out = st.copy_to_host().numpy().astype(np.complex128)
     st.close()
     plan.close()

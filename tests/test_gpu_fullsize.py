@@ -56,15 +56,15 @@ def _compare(ref, out, chunk=1 << 24):
     return mx, (d2 / r2) ** 0.5, fid, o2 ** 0.5
 
 
-def _check(api, n, g, ref, method, k, tc=False, gatewise=False, dfs_trials=16):
+def _check(api, n, g, ref, method, k, tc=False, gatewise=False, dfs_trials=16, jit=False):
     plan = api.Plan(g, n, method, k, dfs_trials=dfs_trials)
     st = api.State(n, "c64")
-    st.apply(plan, sync=True, tc=tc, gatewise=gatewise)
+    st.apply(plan, sync=True, tc=tc, gatewise=gatewise, jit=jit)
     stats = plan.stats("c64", 0, tc=tc)
     mx, rel, fid, nrm = _compare(ref, st.amplitudes())
     st.close()
     plan.close()
-    tag = f"{method} k={k} tc={tc} gatewise={gatewise} passes={stats['passes']} dense={stats['dense']}"
+    tag = f"{method} k={k} tc={tc} jit={jit} gatewise={gatewise} passes={stats['passes']} dense={stats['dense']}"
     assert mx <= MAX_ABS, f"{tag}: max-abs {mx:.3e}"
     assert rel <= REL_L2, f"{tag}: rel-L2 {rel:.3e}"
     assert fid >= FIDELITY, f"{tag}: fidelity {fid}"
@@ -79,18 +79,21 @@ def test_benchmark_plans_match_oracle(layered28):
     _, api = native()
     from paper_2205_06973_gb300.autotune import BEAM_WIDTH, STATE_CANDIDATES
     n, g, ref = layered28
-    for method, k, tc, _tile in STATE_CANDIDATES:
-        stats = _check(api, n, g, ref, method, k, tc=tc, dfs_trials=BEAM_WIDTH if method == "beam" else 16)
+    for method, k, tc, _tile, jit in STATE_CANDIDATES:
+        stats = _check(api, n, g, ref, method, k, tc=tc, dfs_trials=BEAM_WIDTH if method == "beam" else 16,
+                       jit=jit)
         if tc and k <= 6:
             assert stats["dense"] == stats["passes"]
 
 
 @pytest.mark.parametrize("method,k", [("dagp", 8), ("dagp", 10), ("dagp", 12), ("nat", 10), ("dfs", 10)])
 def test_paper_builders_match_oracle(layered28, method, k):
-    """The paper's three builders at the configured limits, gate-list kernel."""
+    """The paper's three builders at the configured limits, on the gate-list
+    interpreter kernel and on the plan's specialised kernels."""
     _, api = native()
     n, g, ref = layered28
     _check(api, n, g, ref, method, k)
+    _check(api, n, g, ref, method, k, jit=True)
 
 
 def test_gate_by_gate_matches_oracle(layered28):
