@@ -162,6 +162,24 @@ sv_status sv_plan_export(const sv_plan *p, uint32_t *part_of_gate, size_t n_gate
  * pointer may be NULL). Compiles on the host if needed; no device work. */
 sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int tile_qubits, uint32_t flags, uint32_t *passes,
                         uint32_t *phases, uint32_t *ops, uint32_t *dense);
+/* sv_plan_build_ml: multi-level partitioning (Sec. IV-B, "Multi-level
+ * partitioning"): the circuit is partitioned with builder m1 under the
+ * first-level limit k1 (one HBM pass per first-level part, as for
+ * sv_plan_build), then every first-level part, as a circuit of its own (its
+ * gates in their original order), is partitioned again with builder m2 under
+ * the second-level limit k2 <= k1. On the gate-list kernels each
+ * second-level part becomes one register phase of its pass (the register
+ * level is the tile's inner state vector), in place of the greedy phase
+ * split, so k2 must not exceed the register bits (5 for complex64, 4 for
+ * complex128; else sv_apply_parts reports SV_ERR_PARTITION). Same arguments
+ * and errors as sv_plan_build, plus SV_ERR_ARG for m2 = SV_PART_NONE or k2
+ * outside [1, k1] and SV_ERR_PARTITION for a gate wider than k2. Host only. */
+sv_status sv_plan_build_ml(const sv_gate *gates, size_t n_gates, int n_qubits, sv_method m1, int k1, sv_method m2,
+                           int k2, uint64_t seed, int dfs_trials, sv_plan **out);
+/* sv_plan_export_inner: the second-level part of every gate (numbered over
+ * the whole circuit: first-level parts in order, then each part's inner
+ * schedule) and their count; SV_ERR_ARG for a one-level plan. */
+sv_status sv_plan_export_inner(const sv_plan *p, uint32_t *inner_of_gate, size_t n_gates, uint32_t *n_inner);
 /* sv_plan_specialise: generate and compile the plan's specialised part
  * kernels (SV_FLAG_SPECIALISE) for the precision, tile (0 = default) and
  * flags (SV_FLAG_TC_DENSE: only the parts that stay on the gate-list kernel)

@@ -742,6 +742,28 @@ def partition(gates, n, method, k, seed=0, trials=16):
     raise ValueError(method)
 
 
+def multilevel(gates, n, m1, k1, m2, k2, seed=0, trials=16):
+    """Multi-level partitioning (Sec. IV-B): the circuit is partitioned with
+    builder m1 under the first-level limit k1; then each first-level part,
+    taken as a circuit of its own (its gates in their original order), is
+    partitioned again with builder m2 under the second-level limit k2.
+    Returns (outer, inner): the first-level part of every gate, and its
+    second-level part numbered over the whole circuit (first-level parts in
+    schedule order, then each part's own schedule)."""
+    outer = partition(gates, n, m1, k1, seed=seed, trials=trials)
+    P = (max(outer) + 1) if len(outer) else 0
+    inner = [0] * len(gates)
+    base = 0
+    for p in range(P):
+        ids = [g for g in range(len(gates)) if outer[g] == p]
+        sub = [gates[g] for g in ids]
+        sp = partition(sub, n, m2, k2, seed=seed, trials=trials)
+        for g, x in zip(ids, sp):
+            inner[g] = base + x
+        base += max(sp) + 1
+    return list(outer), inner
+
+
 # ---------------------------------------------------------- validation ----
 
 def check_partition(gates, n, k, pog):

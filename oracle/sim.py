@@ -6,6 +6,8 @@ Builds ``liborc.so`` next to the source with gcc on first use (or from
 * ``run(n, gates, state)``      - gate-by-gate simulation (Sec. II-B / III-A)
 * ``run_alg1(n, gates, part_of_gate, n_parts, state, order_mode)``
                                  - Algorithm 1 Gather-Execute-Scatter
+* ``run_alg1_nested(n, gates, outer, inner, state)``
+                                 - Algorithm 1 with nested parts (multi-level)
 * ``probs(state)``               - |a_x|^2 and their sum
 
 Gates are ``(name, qubits, theta)`` tuples as produced by ``synth``.
@@ -110,6 +112,42 @@ def run_alg1(n: int, gates, part_of_gate, n_parts: int, state=None, order_mode: 
                               enc.ctypes.data, len(enc), pog.ctypes.data, n_parts, order_mode)
     if rc:
         raise ValueError(f"oracle alg1 failed ({rc})")
+    return s
+
+
+def run_alg1_nested(n: int, gates, outer, inner, state=None):
+    """Algorithm 1 with nested parts (the multi-level execution of Sec. IV-B):
+    for every first-level part, in order, and every assignment of the qubits
+    outside it, gather the part's inner state vector (local bit j = the j-th
+    smallest qubit of the part), run Algorithm 1 of its second-level parts on
+    that vector with the gates' qubits renamed to local bits, and scatter it
+    back. outer / inner: first- and second-level part of every gate (inner
+    numbered over the circuit, each part's inner parts contiguous)."""
+    s = _prep(n, state)
+    outer = [int(x) for x in outer]
+    inner = [int(x) for x in inner]
+    P = (max(outer) + 1) if outer else 0
+    for p in range(P):
+        ids = [g for g in range(len(gates)) if outer[g] == p]
+        S = sorted({q for g in ids for q in gates[g][1]})
+        O = [q for q in range(n) if q not in S]
+        w = len(S)
+        local = {q: j for j, q in enumerate(S)}
+        sub = [(gates[g][0], tuple(local[q] for q in gates[g][1]), gates[g][2]) for g in ids]
+        first = min(inner[g] for g in ids)
+        sub_pog = [inner[g] - first for g in ids]
+        n_sub = max(sub_pog) + 1
+        y = np.arange(1 << w, dtype=np.int64)
+        idx_in = np.zeros(1 << w, dtype=np.int64)
+        for j, q in enumerate(S):
+            idx_in |= ((y >> j) & 1) << q
+        a = np.arange(1 << len(O), dtype=np.int64)
+        idx_out = np.zeros(1 << len(O), dtype=np.int64)
+        for j, q in enumerate(O):
+            idx_out |= ((a >> j) & 1) << q
+        for base in idx_out:
+            x = base | idx_in
+            s[x] = run_alg1(w, sub, sub_pog, n_sub, s[x])
     return s
 
 

@@ -66,6 +66,9 @@ _SIGS = {
     "sv_plan_build": ([_vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                        ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
     "sv_plan_export": ([_vp, _vp, ctypes.c_size_t, _u32p], ctypes.c_int),
+    "sv_plan_build_ml": ([_vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
+    "sv_plan_export_inner": ([_vp, _vp, ctypes.c_size_t, _u32p], ctypes.c_int),
     "sv_plan_stats": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p], ctypes.c_int),
     "sv_plan_destroy": ([_vp], ctypes.c_int),
     "sv_plan_specialise": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.c_int,

@@ -15,16 +15,31 @@ from . import _native as N
 class Plan:
     """sv_plan_build: DAG + partition (Sec. IV) of a circuit, host only."""
 
-    def __init__(self, gates, n, method="dagp", k=10, seed=0, dfs_trials=16):
+    def __init__(self, gates, n, method="dagp", k=10, seed=0, dfs_trials=16, inner=None):
+        """inner = (method2, k2): multi-level partitioning (sv_plan_build_ml),
+        every part re-partitioned with method2 under k2."""
         self.n = n
         self.G = len(gates)
         self.method = method
         self.k = k
+        self.inner = inner
         self._arr = N.encode_gates(gates)
         h = ctypes.c_void_p()
-        N.check(N.lib.sv_plan_build(ctypes.cast(self._arr, ctypes.c_void_p), self.G, n, N.METHODS[method],
-                                    k, seed, dfs_trials, ctypes.byref(h)))
+        if inner is None:
+            N.check(N.lib.sv_plan_build(ctypes.cast(self._arr, ctypes.c_void_p), self.G, n, N.METHODS[method],
+                                        k, seed, dfs_trials, ctypes.byref(h)))
+        else:
+            N.check(N.lib.sv_plan_build_ml(ctypes.cast(self._arr, ctypes.c_void_p), self.G, n, N.METHODS[method],
+                                           k, N.METHODS[inner[0]], inner[1], seed, dfs_trials, ctypes.byref(h)))
         self.h = h
+
+    def export_inner(self):
+        """Second-level part of every gate and their count (multi-level plans)."""
+        import numpy as np
+        inner = np.zeros(max(1, self.G), dtype=np.uint32)
+        P = ctypes.c_uint32()
+        N.check(N.lib.sv_plan_export_inner(self.h, inner.ctypes.data, self.G, ctypes.byref(P)))
+        return inner[: self.G], P.value
 
     def export(self):
         import numpy as np

@@ -231,6 +231,40 @@ sv_status sv_plan_build(const sv_gate *gates, size_t n_gates, int n, sv_method m
     return SV_OK;
 }
 
+sv_status sv_plan_build_ml(const sv_gate *gates, size_t n_gates, int n, sv_method m1, int k1, sv_method m2, int k2,
+                           uint64_t seed, int dfs_trials, sv_plan **out) {
+    if (!out) return fail(SV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (m1 == SV_PART_NONE || m2 < SV_PART_NAT || m2 > SV_PART_BEAM)
+        return fail(SV_ERR_ARG, "both levels need a part builder");
+    if (k2 < 1 || k2 > k1) return fail(SV_ERR_ARG, "k2 must be in [1, k1]");
+    sv_plan *p = nullptr;
+    sv_status st = sv_plan_build(gates, n_gates, n, m1, k1, seed, dfs_trials, &p);
+    if (st != SV_OK) return st;
+    std::unique_ptr<sv_plan> hold(p);
+    for (const GateRef &g : p->gates)
+        if (g.arity > k2) return fail(SV_ERR_PARTITION, "a gate has more qubits than k2");
+    std::vector<uint32_t> outer, inner;
+    std::string err;
+    if (!part_multilevel(p->gates, n, (int)m1, k1, (int)m2, k2, seed, dfs_trials, outer, inner, err))
+        return fail(SV_ERR_ARG, err);
+    if (outer != p->pog) return fail(SV_ERR_INTERNAL, "first-level partition differs from the plan's");
+    p->inner = std::move(inner);
+    for (uint32_t x : p->inner) p->n_inner = std::max(p->n_inner, x + 1);
+    p->k2 = k2;
+    *out = hold.release();
+    return SV_OK;
+}
+
+sv_status sv_plan_export_inner(const sv_plan *p, uint32_t *inner, size_t n_gates, uint32_t *n_inner) {
+    if (!p) return fail(SV_ERR_ARG, "plan is NULL");
+    if (n_gates != p->gates.size()) return fail(SV_ERR_ARG, "n_gates does not match the plan");
+    if (p->inner.empty() && n_gates) return fail(SV_ERR_ARG, "the plan has one level");
+    if (inner && n_gates) std::memcpy(inner, p->inner.data(), sizeof(uint32_t) * n_gates);
+    if (n_inner) *n_inner = p->n_inner;
+    return SV_OK;
+}
+
 sv_status sv_plan_export(const sv_plan *p, uint32_t *pog, size_t n_gates, uint32_t *n_parts) {
     if (!p) return fail(SV_ERR_ARG, "plan is NULL");
     if (n_gates != p->gates.size()) return fail(SV_ERR_ARG, "n_gates does not match the plan");
@@ -246,7 +280,8 @@ static sv_status get_host_program(sv_plan *p, bool fp64, int t, int dense, const
     if (it == p->host_progs.end()) {
         std::unique_ptr<Program> prog(new Program());
         std::string err;
-        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, fp64, t, part_R(fp64), dense, *prog, err))
+        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, fp64, t, part_R(fp64), dense, *prog, err,
+                             p->inner.empty() ? nullptr : &p->inner))
             return fail(SV_ERR_PARTITION, err);
         it = p->host_progs.emplace(key, std::move(prog)).first;
     }

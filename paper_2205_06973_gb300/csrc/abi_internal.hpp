@@ -63,6 +63,9 @@ struct sv_plan {
     std::vector<uint32_t> pog;
     uint32_t n_parts = 0;
     int max_part = 0;                                                      // qubits of the largest part
+    std::vector<uint32_t> inner;        // second-level part of each gate (multi-level plans), else empty
+    uint32_t n_inner = 0;
+    int k2 = 0;
     std::map<std::tuple<bool, int, int>, std::unique_ptr<Program>> host_progs;   // (fp64, t, dense)
     std::map<std::tuple<int, bool, int, int>, DevProgram> dev_progs;             // (dev, fp64, t, dense)
     std::vector<std::vector<double>> mats;                                 // gatewise matrices

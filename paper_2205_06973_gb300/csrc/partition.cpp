@@ -858,4 +858,51 @@ std::vector<uint32_t> part_beam(const Dag &dag, int k, int width) {
     return schedule_parts(dag, parts_to_pog(G, parts));
 }
 
+// One builder by its method code (1 Nat, 2 DFS, 3 dagP, 4 exact, 5 beam).
+bool run_builder(const Dag &dag, int method, int k, uint64_t seed, int trials, std::vector<uint32_t> &pog,
+                 std::string &err) {
+    switch (method) {
+    case 1: pog = part_nat(dag, k); return true;
+    case 2: pog = part_dfs(dag, k, seed, trials); return true;
+    case 3: pog = part_dagp(dag, k); return true;
+    case 4: return part_exact(dag, k, pog, err);
+    case 5: pog = part_beam(dag, k, trials); return true;
+    default: err = "bad builder"; return false;
+    }
+}
+
+// Multi-level partitioning (Sec. IV-B): the circuit is partitioned under the
+// first-level limit k1; then every first-level part, as a circuit of its own
+// (its gates in their original order, which its sub-DAG respects), is
+// partitioned again under the second-level limit k2. Inner parts are
+// numbered globally: the first-level parts in schedule order, and inside
+// each the inner parts in their own schedule order.
+bool part_multilevel(const std::vector<GateRef> &gates, int n, int m1, int k1, int m2, int k2, uint64_t seed,
+                     int trials, std::vector<uint32_t> &outer, std::vector<uint32_t> &inner, std::string &err) {
+    Dag dag;
+    if (!build_dag(gates, n, dag, err)) return false;
+    if (!run_builder(dag, m1, k1, seed, trials, outer, err)) return false;
+    uint32_t P = 0;
+    for (uint32_t x : outer) P = std::max(P, x + 1);
+    std::vector<std::vector<int>> members(P);
+    for (size_t g = 0; g < gates.size(); g++) members[outer[g]].push_back((int)g);
+    inner.assign(gates.size(), 0);
+    uint32_t base = 0;
+    for (uint32_t p = 0; p < P; p++) {
+        std::vector<GateRef> sub;
+        for (int g : members[p]) sub.push_back(gates[g]);
+        Dag sd;
+        if (!build_dag(sub, n, sd, err)) return false;
+        std::vector<uint32_t> sp;
+        if (!run_builder(sd, m2, k2, seed, trials, sp, err)) return false;
+        uint32_t q = 0;
+        for (size_t j = 0; j < sub.size(); j++) {
+            inner[members[p][j]] = base + sp[j];
+            q = std::max(q, sp[j] + 1);
+        }
+        base += q;
+    }
+    return true;
+}
+
 }  // namespace hisv

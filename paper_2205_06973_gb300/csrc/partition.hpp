@@ -42,5 +42,15 @@ bool part_exact(const Dag &dag, int k, std::vector<uint32_t> &pog, std::string &
 // circuit size); width <= 0: 16.
 std::vector<uint32_t> part_beam(const Dag &dag, int k, int width);
 std::vector<uint32_t> schedule_parts(const Dag &dag, const std::vector<uint32_t> &pog);
+// One builder by its method code (1 Nat, 2 DFS, 3 dagP, 4 exact, 5 beam;
+// trials = DFS trials or beam width).
+bool run_builder(const Dag &dag, int method, int k, uint64_t seed, int trials, std::vector<uint32_t> &pog,
+                 std::string &err);
+// Multi-level partitioning (Sec. IV-B): first level with builder m1 under
+// k1, then each first-level part re-partitioned with builder m2 under k2.
+// outer = first-level part of each gate (schedule order); inner = global
+// second-level part (first-level order, then each part's own schedule).
+bool part_multilevel(const std::vector<GateRef> &gates, int n, int m1, int k1, int m2, int k2, uint64_t seed,
+                     int trials, std::vector<uint32_t> &outer, std::vector<uint32_t> &inner, std::string &err);
 
 }  // namespace hisv

@@ -18,6 +18,7 @@
 #include "planner.hpp"
 
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstring>
 
@@ -191,7 +192,7 @@ void fused_unitary(const std::vector<GateRef> &gates, const std::vector<int> &id
 
 bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector<uint32_t> &pog,
                      uint32_t n_parts, bool fp64, int t_cfg, int R, int dense_mode, Program &prog,
-                     std::string &err) {
+                     std::string &err, const std::vector<uint32_t> *inner) {
     prog = Program();
     prog.fp64 = fp64;
     prog.R = R;
@@ -296,6 +297,27 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
             uint32_t Rset = 0;
             uint64_t blocked = 0;
             std::vector<int> sched, rest;
+            if (inner && !inner->empty()) {
+                // multi-level partitioning: the phase is the next second-level
+                // part (the smallest inner id left; its gates in order)
+                uint32_t next = UINT32_MAX;
+                for (int g : remaining) next = std::min(next, (*inner)[g]);
+                for (int g : remaining) {
+                    if ((*inner)[g] != next) {
+                        rest.push_back(g);
+                        continue;
+                    }
+                    const GateRef &gr = gates[g];
+                    Rset |= needed_slots(gr, sim_slot);
+                    sched.push_back(g);
+                    if (gr.kind == SV_GATE_SWAP) std::swap(sim_slot[gr.q[0]], sim_slot[gr.q[1]]);
+                }
+                if (popc(Rset) > R) {
+                    err = "a second-level part needs " + std::to_string(popc(Rset)) + " register qubits > " +
+                          std::to_string(R);
+                    return false;
+                }
+            } else
             for (int g : remaining) {
                 const GateRef &gr = gates[g];
                 if (gmask[g] & blocked) {

@@ -37,9 +37,13 @@ bool gate_is_two_qubit(int kind);
 // t_cfg qubits (t = min(n, t_cfg)) and R register bits.
 // dense_mode: 0 = gate lists only; 1 = every part of at most 6 qubits runs
 // as a dense tensor-core part (complex64, n >= 13).
+// inner (optional): the second-level part of every gate (multi-level
+// partitioning, Sec. IV-B); each becomes one register phase of its
+// first-level part instead of the greedy phase split (error if one needs
+// more than R register qubits).
 bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector<uint32_t> &pog,
                      uint32_t n_parts, bool fp64, int t_cfg, int R, int dense_mode, Program &prog,
-                     std::string &err);
+                     std::string &err, const std::vector<uint32_t> *inner = nullptr);
 
 // Fused unitary of gates acting on the qubits qs[0..k) (local bit j <-> qs[j]):
 // U = G_last ... G_first as a 2^k x 2^k row-major interleaved complex matrix.

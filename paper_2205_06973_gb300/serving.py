@@ -23,10 +23,13 @@ Admitted states stay on the device until their result is taken.
   micro-batch to the next without a host round trip. Requests that arrive
   meanwhile join the batch after.
 * Large requests get their own state and CUDA stream and run their part
-  passes (sv_apply_parts) beside the batches; at most ``large_running`` of
-  them at a time (each pass fills the GPU, so sharing it among many large
-  requests only stretches all their latencies). The batch streams have the
-  higher priority. Each large request runs the plan the cost model of
+  passes (sv_apply_parts) beside the batches, in two lanes: medium ones
+  (n <= mid_n, states up to 512 MiB) at most ``mid_running`` at a time, the
+  largest at most ``large_running`` at a time (each of their passes fills the
+  GPU, so sharing it among many only stretches all their latencies). Stream
+  priorities order the lanes: batches first, then medium requests, then the
+  largest, so a medium request's passes go between a large one's instead of
+  queueing behind it. Each large request runs the plan the cost model of
   ``autotune.choose_plan`` rates fastest: the tensor-core dense plan
   (beam-search parts, k = 6) or the gate-list plan (beam-search parts,
   k = 10). With ``tc=False`` large requests use ``method_large`` /
@@ -95,7 +98,7 @@ class Server:
     def __init__(self, budget_bytes=170e9, max_slots=4096, small_n=20, batch_max=512, k_small=9,
                  k_large=6, tc=True, method_small="beam", method_large="dagp", mode="parts",
                  keep_states=False, planners=8, large_planners=4, large_running=2, dense_min_qubits=13,
-                 small_budget=None):
+                 small_budget=None, mid_n=26, mid_running=4):
         self.budget = float(budget_bytes)
         self.small_budget = float(small_budget) if small_budget is not None else self.budget / 8
         self.max_slots = max_slots
@@ -109,12 +112,16 @@ class Server:
         self.mode = mode
         self.keep = keep_states
         self.large_running = max(1, large_running)
+        self.mid_n = mid_n
+        self.mid_running = max(1, mid_running)
         self.dense_min = dense_min_qubits if (tc and mode == "parts") else 0
         self.pool = cf.ThreadPoolExecutor(max_workers=planners)
         self.pool_large = cf.ThreadPoolExecutor(max_workers=large_planners)
         self.builder = cf.ThreadPoolExecutor(max_workers=1)
-        self.streams = [torch.cuda.Stream() for _ in range(self.large_running)]
         lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+        mid = max(hi, lo - 1) if hi < lo else lo   # one step above the lowest priority
+        self.streams = [torch.cuda.Stream(priority=lo) for _ in range(self.large_running)]
+        self.mid_streams = [torch.cuda.Stream(priority=mid) for _ in range(self.mid_running)]
         self.batch_streams = [torch.cuda.Stream(priority=hi) for _ in range(2)]
 
     @staticmethod
@@ -175,6 +182,7 @@ class Server:
         i = 0
         bsi = 0                               # next batch stream
         lsi = 0                               # next large-request stream
+        msi = 0                               # next medium-request stream
         host = {"batch_build_s": 0.0, "batches": 0, "batched_requests": 0, "large_tc": 0,
                 "admission_stalls": 0, "peak_used_bytes": 0.0}
         batch_times, batch_sizes, large_times = [], [], []
@@ -232,19 +240,27 @@ class Server:
                 admitted_at[r.rid] = now()
                 small_wait.append(r)
             host["peak_used_bytes"] = max(host["peak_used_bytes"], used)
-            # large requests start as running slots free up, once planned
+            # large requests start as running slots of their lane free up, once
+            # planned: medium ones (n <= mid_n) on their own higher-priority
+            # streams, so they do not queue behind the largest states
             j = 0
-            while j < len(large_wait) and len(running_large) < self.large_running:
+            while j < len(large_wait):
                 r = large_wait[j]
-                f = futures[r.rid]
-                if not f.done():
+                is_mid = r.n <= self.mid_n
+                lane_busy = sum((x[0].n <= self.mid_n) == is_mid for x in running_large)
+                if lane_busy >= (self.mid_running if is_mid else self.large_running) or not futures[r.rid].done():
                     j += 1
                     continue
                 large_wait.pop(j)
                 plan, tc = futures.pop(r.rid).result()
                 host["large_tc"] += int(tc)
-                st = self._new_state(r.n, self.streams[lsi % len(self.streams)])
-                lsi += 1
+                if is_mid:
+                    stream = self.mid_streams[msi % len(self.mid_streams)]
+                    msi += 1
+                else:
+                    stream = self.streams[lsi % len(self.streams)]
+                    lsi += 1
+                st = self._new_state(r.n, stream)
                 start = now()
                 st.apply(plan, gatewise=self.mode != "parts", tc=tc)
                 ev = torch.cuda.Event()

@@ -215,3 +215,42 @@ def test_new_builders_and_batch_entry_points_validate_arguments(native):
     n1, n2, n3 = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
     assert native.lib.sv_batch_dense_info(None, ctypes.byref(n1), ctypes.byref(n2), ctypes.byref(n3)) == \
         native.SV_ERR_ARG
+
+
+@pytest.mark.parametrize("m1,k1,m2,k2", [("nat", 8, "nat", 4), ("dagp", 10, "dagp", 5), ("dfs", 8, "dagp", 4),
+                                         ("dagp", 12, "beam", 5), ("beam", 10, "dfs", 5)])
+def test_multilevel_bit_exact(native, m1, k1, m2, k2):
+    """sv_plan_build_ml gives the oracle's two-level partition gate for gate
+    (both levels), on a random circuit and on the 28-qubit layered one."""
+    from paper_2205_06973_gb300.api import Plan
+    cases = [(12, _rand(12, 400, 77))]
+    if "beam" not in (m1, m2):     # the oracle's beam builder is slow at 2520 gates
+        cases.append(synth.layered_28q())
+    for n, g in cases:
+        p = Plan(g, n, m1, k1, inner=(m2, k2))
+        outer, P = p.export()
+        inner, Q = p.export_inner()
+        ro, ri = pt.multilevel(g, n, m1, k1, m2, k2)
+        assert list(outer) == ro and list(inner) == ri
+        assert P == max(ro) + 1 and Q == max(ri) + 1
+        pt.check_partition(g, n, k2, list(inner))
+        p.close()
+
+
+def test_multilevel_errors(native):
+    from paper_2205_06973_gb300.api import Plan
+    g = [("CX", (0, 1), 0.0), ("H", (2,), 0.0)]
+    with pytest.raises(native.SvError) as e:
+        Plan(g, 3, "dagp", 3, inner=("dagp", 4))      # k2 > k1
+    assert e.value.status == native.SV_ERR_ARG
+    with pytest.raises(native.SvError) as e:
+        Plan(g, 3, "dagp", 3, inner=("dagp", 1))      # a two-qubit gate under k2 = 1
+    assert e.value.status == native.SV_ERR_PARTITION
+    with pytest.raises(native.SvError) as e:
+        Plan(g, 3, "dagp", 3).export_inner()          # one-level plan
+    assert e.value.status == native.SV_ERR_ARG
+    p = Plan(synth.layered(14, 4, seed=2), 14, "dagp", 10, inner=("dagp", 6))
+    with pytest.raises(native.SvError) as e:          # second-level parts wider than the register bits
+        p.stats("c64")
+    assert e.value.status == native.SV_ERR_PARTITION
+    p.close()

@@ -87,3 +87,29 @@ def test_dense_and_specialised_mix():
     st = plan.stats("c64", 0, tc=True)
     assert 0 < st["dense"] < st["passes"], st
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_multilevel_plans(precision):
+    """Multi-level plans (Sec. IV-B): first-level parts as HBM passes, their
+    second-level parts as register phases, on the interpreter and on the
+    specialised kernels, against the oracle."""
+    _, api = native()
+    import torch
+    n = 16
+    _, g = synth.layered_28q(n=n, depth=14)
+    g = g + synth.qft(n)[:120]
+    psi = random_state(n, 31)
+    ref = sim.run(n, g, psi)
+    k2 = 5 if precision == "c64" else 4
+    dt = torch.complex128 if precision == "c128" else torch.complex64
+    for m1, k1, m2 in (("dagp", 10, "dagp"), ("beam", 12, "beam"), ("nat", 8, "nat"), ("dfs", 10, "dagp")):
+        plan = api.Plan(g, n, m1, k1, inner=(m2, k2))
+        for jit in (False, True):
+            st = api.State(n, precision)
+            st.upload(torch.from_numpy(np.ascontiguousarray(psi)).to(dt).pin_memory())
+            st.apply(plan, sync=True, jit=jit)
+            out = st.copy_to_host().numpy().astype(np.complex128)
+            st.close()
+            assert max_abs(out, ref) <= TOL[precision], (m1, k1, m2, jit)
+        plan.close()

@@ -4,10 +4,13 @@ minimum on tiny DAGs."""
 import json
 import os
 
+import numpy as np
 import pytest
 
 import synth
 from oracle import partition as pt
+from oracle import partition as P
+from oracle import sim
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "partition_examples.json")
 
@@ -179,3 +182,73 @@ def test_oracle_beam_valid_and_not_below_optimum():
             assert pt.check_partition(g, n, k, pog) >= opt
         hits += pt.check_partition(g, n, k, pt.beam(g, n, k, 16)) == opt
     assert hits >= 15, hits
+
+
+# ------------------------------------------------ multi-level (Sec. IV-B) ---
+
+ML_CASES = [("nat", 8, "nat", 4), ("dagp", 8, "dagp", 4), ("dfs", 7, "dagp", 3), ("dagp", 10, "beam", 5),
+            ("beam", 9, "nat", 5)]
+
+
+@pytest.mark.parametrize("m1,k1,m2,k2", ML_CASES)
+def test_multilevel_valid_at_both_levels(m1, k1, m2, k2):
+    """Both levels satisfy the conditions of Sec. IV-A: the first level under
+    k1; each first-level part's inner partition on its own sub-circuit under
+    k2; inner parts nest in first-level parts; and the inner parts in order
+    form one valid acyclic partition of the whole circuit under k2."""
+    n = 11
+    g = synth.layered(n, 5, seed=17, two_q=("CX", "CZ"))
+    outer, inner = P.multilevel(g, n, m1, k1, m2, k2)
+    assert P.check_partition(g, n, k1, outer) == max(outer) + 1
+    assert P.check_partition(g, n, k2, inner) == max(inner) + 1
+    for x in set(inner):
+        assert len({outer[i] for i in range(len(g)) if inner[i] == x}) == 1
+    for p in range(max(outer) + 1):
+        ids = [i for i in range(len(g)) if outer[i] == p]
+        first = min(inner[i] for i in ids)
+        P.check_partition([g[i] for i in ids], n, k2, [inner[i] - first for i in ids])
+    # the inner numbering follows the first level: part p's inner ids come
+    # after part p-1's
+    for i in range(len(g)):
+        for j in range(len(g)):
+            if outer[i] < outer[j]:
+                assert inner[i] < inner[j]
+
+
+def test_multilevel_with_equal_limits_is_one_level():
+    """k2 = k1 with the same builder: every first-level part already fits, so
+    its re-partition is the part itself and the two levels coincide."""
+    n = 10
+    g = synth.layered(n, 6, seed=3, two_q=("CX", "CZ"))
+    for m in ("nat", "dfs", "dagp"):
+        outer, inner = P.multilevel(g, n, m, 6, m, 6)
+        assert inner == outer, m
+
+
+@pytest.mark.parametrize("m1,k1,m2,k2", ML_CASES)
+def test_nested_algorithm1_equals_gate_by_gate(m1, k1, m2, k2):
+    """Algorithm 1 with nested parts (gather the first-level part's vector,
+    run its second-level parts by Algorithm 1 inside it, scatter) gives the
+    gate-by-gate state psi_out = U_G ... U_1 psi_in (Sec. II-B)."""
+    n = 10
+    g = synth.layered(n, 6, seed=5, two_q=("CX", "CZ")) + synth.qft(n)[:40]
+    psi = np.asarray(synth.random_amplitudes(n, 4))
+    psi = (psi[:, 0] + 1j * psi[:, 1]) / np.linalg.norm(psi[:, 0] + 1j * psi[:, 1])
+    outer, inner = P.multilevel(g, n, m1, k1, m2, k2)
+    ref = sim.run(n, g, psi)
+    out = sim.run_alg1_nested(n, g, outer, inner, psi)
+    assert np.abs(out - ref).max() <= 1e-13
+
+
+def test_nested_algorithm1_catches_a_misplaced_gate():
+    """The nested execution is sensitive to the inner order: moving one gate
+    into another second-level part against its dependencies changes the
+    state (the check above is not vacuous)."""
+    n = 6
+    g = [("H", (0,), 0.0), ("CX", (0, 1), 0.0), ("RX", (1,), 0.7), ("CZ", (1, 2), 0.0), ("RY", (2,), 1.1)]
+    outer = [0, 0, 0, 0, 0]
+    good = [0, 0, 1, 1, 1]
+    bad = [1, 0, 1, 1, 1]       # H after the CX that depends on it
+    ref = sim.run(n, g)
+    assert np.abs(sim.run_alg1_nested(n, g, outer, good) - ref).max() <= 1e-13
+    assert np.abs(sim.run_alg1_nested(n, g, outer, bad) - ref).max() > 1e-3
