@@ -107,6 +107,12 @@ typedef struct sv_plan sv_plan;
  * The amplitudes are the paper's state vector (Sec. II-B): 2^n entries. */
 sv_status sv_create(int n_qubits, sv_precision prec, void *dev_buf, size_t dev_buf_bytes,
                     void *stream, sv_state **out);
+/* sv_attach: a state handle over amplitudes already in dev_buf (required,
+ * same layout and size rules as sv_create), left as they are: for callers
+ * that own the amplitudes, e.g. one rank's slice of a distributed state
+ * (Sec. III-D), whose local steps run through sv_apply_parts. */
+sv_status sv_attach(int n_qubits, sv_precision prec, void *dev_buf, size_t dev_buf_bytes, void *stream,
+                    sv_state **out);
 sv_status sv_destroy(sv_state *s);
 /* Set the state to the basis state |index> (index < 2^n). Stream-ordered. */
 sv_status sv_set_basis(sv_state *s, uint64_t index);

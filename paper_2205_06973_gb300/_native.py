@@ -53,6 +53,7 @@ _u32p = ctypes.POINTER(ctypes.c_uint32)
 _SIGS = {
     "sv_create": ([ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
     "sv_destroy": ([_vp], ctypes.c_int),
+    "sv_attach": ([ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
     "sv_set_basis": ([_vp, ctypes.c_uint64], ctypes.c_int),
     "sv_upload": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "sv_copy_state": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),

@@ -103,6 +103,28 @@ class State:
         if tile:
             N.check(N.lib.sv_set_tile(self.h, tile))
 
+    @classmethod
+    def over(cls, amps, n, precision="c64", stream=None, tile=0):
+        """A state handle over an existing CUDA tensor of 2^n complex
+        amplitudes (sv_attach: the contents are kept, the tensor stays owned
+        by the caller)."""
+        self = cls.__new__(cls)
+        self.n = n
+        self.precision = precision
+        self.amp_bytes = 16 if precision == "c128" else 8
+        self.nbytes = self.amp_bytes << n
+        assert amps.is_cuda and amps.numel() * amps.element_size() == self.nbytes and amps.is_contiguous()
+        self.buf = amps
+        self.stream = stream if stream is not None else torch.cuda.current_stream(amps.device)
+        h = ctypes.c_void_p()
+        N.check(N.lib.sv_attach(n, N.SV_C128 if precision == "c128" else N.SV_C64,
+                                ctypes.c_void_p(amps.data_ptr()), self.nbytes,
+                                ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        if tile:
+            N.check(N.lib.sv_set_tile(self.h, tile))
+        return self
+
     # views of the amplitudes (no copy)
     def amplitudes(self):
         dt = torch.complex128 if self.precision == "c128" else torch.complex64

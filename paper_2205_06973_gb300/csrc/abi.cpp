@@ -61,7 +61,10 @@ extern "C" {
 const char *sv_last_error(void) { return g_err.c_str(); }
 const char *sv_version(void) { return "hisvsim-gb300 0.1 (sm_103a)"; }
 
-sv_status sv_create(int n, sv_precision prec, void *dev_buf, size_t dev_buf_bytes, void *stream, sv_state **out) {
+}  // extern "C"
+
+static sv_status create_state(int n, sv_precision prec, void *dev_buf, size_t dev_buf_bytes, void *stream, bool init,
+                              sv_state **out) {
     if (!out) return fail(SV_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > 36) return fail(SV_ERR_ARG, "n_qubits must be in [1, 36]");
@@ -95,7 +98,7 @@ sv_status sv_create(int n, sv_precision prec, void *dev_buf, size_t dev_buf_byte
         dev_free(s->d_err, s->stream);
         return fail(SV_ERR_OOM, std::string("scratch allocation: ") + cudaGetErrorString(e));
     }
-    e = launch_set_basis(is_fp64(s.get()), s->buf, n, 0, s->stream);
+    if (init) e = launch_set_basis(is_fp64(s.get()), s->buf, n, 0, s->stream);
     if (e != cudaSuccess) {
         if (s->owns) dev_free(s->buf, s->stream);
         dev_free(s->d_partials, s->stream);
@@ -104,6 +107,17 @@ sv_status sv_create(int n, sv_precision prec, void *dev_buf, size_t dev_buf_byte
     }
     *out = s.release();
     return SV_OK;
+}
+
+extern "C" {
+
+sv_status sv_create(int n, sv_precision prec, void *dev_buf, size_t dev_buf_bytes, void *stream, sv_state **out) {
+    return create_state(n, prec, dev_buf, dev_buf_bytes, stream, true, out);
+}
+
+sv_status sv_attach(int n, sv_precision prec, void *dev_buf, size_t dev_buf_bytes, void *stream, sv_state **out) {
+    if (!dev_buf) return fail(SV_ERR_ARG, "sv_attach needs dev_buf");
+    return create_state(n, prec, dev_buf, dev_buf_bytes, stream, false, out);
 }
 
 sv_status sv_destroy(sv_state *s) {
