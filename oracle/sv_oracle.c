@@ -154,62 +154,66 @@ static int64_t deposit(int64_t v, const int *pos, int cnt) {
 }
 
 /*
- * Algorithm 1 (Gather-Execute-Scatter). part_of_gate[g] in [0, n_parts) gives
- * the part of gate g; parts run in increasing id (the schedule), the gates of
- * a part in increasing gate index. The inner vector's bit j holds the qubit
- * inner_order[j] of the part; inner_order == 0 selects the part's qubits in
- * ascending order (inner bit j <-> j-th smallest qubit), any other bijection
- * is selected by order_mode = 1 (descending).
+ * Partitioned mode (Sec. III-C; Algorithm 1). A part whose gates act on the
+ * qubit set S is a unitary on the 2^|S|-dimensional factor of the state.
+ * Written as a matrix whose row index is the assignment of the qubits outside
+ * S and whose column index is the assignment of S, the state is a stack of
+ * independent 2^|S|-vectors, one per row, and the part acts on every row
+ * alone. So for each part, in increasing id (the schedule): the state is
+ * re-laid into that matrix, the part's gates (increasing gate index, qubits
+ * renamed to column bits) are applied to each row, and the matrix is laid
+ * back out. Column bit j holds the j-th smallest qubit of S (order_mode 0)
+ * or the j-th largest (order_mode 1); any bijection gives the same state.
  */
 int orc_run_alg1(double *svd, int n, const ogate *gates, int64_t ngates,
                  const uint32_t *part_of_gate, uint32_t n_parts, int order_mode) {
-    cplx *out_sv = (cplx *)svd;
-    int64_t *glist = (int64_t *)malloc(sizeof(int64_t) * (ngates > 0 ? ngates : 1));
-    if (!glist) return -3;
-    for (uint32_t p = 0; p < n_parts; p++) {
-        /* gate_list of p (ascending gate index) and its qubit set */
-        int64_t ng = 0;
-        uint64_t qmask = 0;
-        for (int64_t g = 0; g < ngates; g++) {
-            if (part_of_gate[g] != p) continue;
-            glist[ng++] = g;
-            for (int j = 0; j < gates[g].nq; j++) qmask |= (uint64_t)1 << gates[g].q[j];
-        }
-        if (ng == 0) continue;
-        int S[64], w = 0, outer[64], no = 0;
-        for (int q = 0; q < n; q++) {
-            if ((qmask >> q) & 1) S[w++] = q; else outer[no++] = q;
-        }
-        if (order_mode == 1) { /* reversed inner order */
-            for (int j = 0; j < w / 2; j++) { int t = S[j]; S[j] = S[w - 1 - j]; S[w - 1 - j] = t; }
-        }
-        int slot[64];
-        for (int j = 0; j < w; j++) slot[S[j]] = j;
-        const int64_t W = (int64_t)1 << w;
-        const int64_t NO = (int64_t)1 << no;
-        int err = 0;
-        #pragma omp parallel reduction(|:err)
-        {
-            cplx *in_sv = (cplx *)malloc(sizeof(cplx) * W);
-            #pragma omp for schedule(static)
-            for (int64_t o = 0; o < NO; o++) {
-                if (!in_sv) { err |= 1; continue; }
-                int64_t base = deposit(o, outer, no);
-                for (int64_t l = 0; l < W; l++) in_sv[l] = out_sv[base | deposit(l, S, w)];   /* gather */
-                for (int64_t i = 0; i < ng; i++) {                                               /* execute */
-                    const ogate *g = &gates[glist[i]];
-                    int32_t q[2] = {0, 0};
-                    for (int j = 0; j < g->nq; j++) q[j] = slot[g->q[j]];
-                    if (apply_gate(in_sv, w, g->kind, g->nq, q, g->theta)) err |= 2;
-                }
-                for (int64_t l = 0; l < W; l++) out_sv[base | deposit(l, S, w)] = in_sv[l];  /* scatter */
+    cplx *state = (cplx *)svd;
+    const int64_t N = (int64_t)1 << n;
+    cplx *matrix = (cplx *)malloc(sizeof(cplx) * N);
+    int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (ngates > 0 ? ngates : 1));
+    if (!matrix || !members) { free(matrix); free(members); return -3; }
+    int rc = 0;
+    for (uint32_t part = 0; part < n_parts && !rc; part++) {
+        int64_t count = 0;
+        uint64_t used = 0;
+        for (int64_t g = 0; g < ngates; g++)
+            if (part_of_gate[g] == part) {
+                members[count++] = g;
+                for (int j = 0; j < gates[g].nq; j++) used |= (uint64_t)1 << gates[g].q[j];
             }
-            free(in_sv);
+        if (count == 0) continue;
+        int cols[64], rest[64], width = 0, others = 0, column_of[64];
+        for (int q = 0; q < n; q++) {
+            if ((used >> q) & 1) cols[width++] = q; else rest[others++] = q;
         }
-        if (err) { free(glist); return -4; }
+        if (order_mode == 1)
+            for (int j = 0; j < width / 2; j++) { int t = cols[j]; cols[j] = cols[width - 1 - j]; cols[width - 1 - j] = t; }
+        for (int j = 0; j < width; j++) column_of[cols[j]] = j;
+        const int64_t C = (int64_t)1 << width, R = (int64_t)1 << others;
+        #pragma omp parallel for schedule(static)
+        for (int64_t r = 0; r < R; r++) {
+            const int64_t row = deposit(r, rest, others);
+            for (int64_t c = 0; c < C; c++) matrix[r * C + c] = state[row | deposit(c, cols, width)];
+        }
+        int err = 0;
+        #pragma omp parallel for schedule(static) reduction(|:err)
+        for (int64_t r = 0; r < R; r++)
+            for (int64_t i = 0; i < count; i++) {
+                const ogate *g = &gates[members[i]];
+                int32_t q[2] = {0, 0};
+                for (int j = 0; j < g->nq; j++) q[j] = column_of[g->q[j]];
+                if (apply_gate(matrix + r * C, width, g->kind, g->nq, q, g->theta)) err |= 1;
+            }
+        if (err) { rc = -4; break; }
+        #pragma omp parallel for schedule(static)
+        for (int64_t r = 0; r < R; r++) {
+            const int64_t row = deposit(r, rest, others);
+            for (int64_t c = 0; c < C; c++) state[row | deposit(c, cols, width)] = matrix[r * C + c];
+        }
     }
-    free(glist);
-    return 0;
+    free(matrix);
+    free(members);
+    return rc;
 }
 
 /* |a_x|^2 and the norm sum, in double. */
