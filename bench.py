@@ -437,6 +437,60 @@ def c128_section(n, gates, peak, fp64_peak):
             "fp64_peak_tflops": round(fp64_peak / 1e12, 3), "rows": rows, "norm": norm}
 
 
+def multilevel_section(peak):
+    """Multi-level partitioning (Sec. IV-B) against one level, on the
+    28-qubit layered circuit (complex64, 2 GiB) and the 33-qubit QFT
+    (complex64, 64 GiB): the same first-level parts (HBM passes), their
+    register phases from the greedy split (one level) or from a second
+    builder under k2 = 5 (two levels), on the specialised kernels."""
+    import synth
+    from paper_2205_06973_gb300 import api
+    out = []
+    n33, g33, x33 = synth.qft_basis(33)
+    for name, (n, g) in (("layered28", synth.layered_28q()), ("qft33", (n33, g33))):
+        st = api.State(n, "c64")
+        for m, k in (("dagp", 10), ("beam", 10), ("beam", 12)):
+            for inner in (None, ("dagp", 5), ("beam", 5)):
+                plan = api.Plan(g, n, m, k, inner=inner)
+                stt = plan.stats("c64")
+                cs = plan.specialise("c64")
+                ms = _timed(st, plan, jit=True, reps=2 if n < 30 else 1)
+                gbs = stt["passes"] * 2 * st.nbytes / (ms / 1e3) / 1e9
+                out.append({"circuit": name, "method": m, "k": k, "inner": "greedy" if inner is None else
+                            f"{inner[0]} k2={inner[1]}", "passes": stt["passes"], "phases": stt["phases"],
+                            "ops": stt["ops"], "ms": round(ms, 2), "GBs": round(gbs, 1),
+                            "frac": round(gbs / peak, 4), "compile_s": round(cs, 2)})
+                plan.close()
+        st.close()
+    return {"kernel": "specialised gate-list kernels", "rows": out}
+
+
+def qft33_section(peak):
+    """The 33-qubit QFT (577 gates) on the seeded basis state |x> (complex64,
+    64 GiB): the tensor-core plan (beam, k = 6) and the specialised
+    gate-list plans (beam, k = 10 and 12). (Its amplitudes are checked
+    against the closed form in tests/test_gpu_qft33.py.)"""
+    import synth
+    from paper_2205_06973_gb300 import api
+    n, g, x = synth.qft_basis(33)
+    st = api.State(n, "c64")
+    rows = []
+    for m, k, tc, jit in (("beam", 6, True, False), ("beam", 10, False, True), ("beam", 12, False, True)):
+        plan = api.Plan(g, n, m, k, dfs_trials=64 if k <= 6 else 16)
+        stt = plan.stats("c64", tc=tc)
+        cs = plan.specialise("c64", tc=tc) if jit else 0.0
+        st.set_basis(x)
+        ms = _timed(st, plan, tc=tc, jit=jit, reps=1)
+        gbs = stt["passes"] * 2 * st.nbytes / (ms / 1e3) / 1e9
+        rows.append({"method": m, "k": k, "tc": tc, "jit": jit, "passes": stt["passes"], "ms": round(ms, 1),
+                     "GBs": round(gbs, 1), "frac": round(gbs / peak, 4), "compile_s": round(cs, 2)})
+        plan.close()
+    norm = st.probs()
+    st.close()
+    return {"workload": "33-qubit QFT (577 gates) on a seeded basis state, complex64 (64 GiB)", "rows": rows,
+            "best": min(rows, key=lambda r: r["ms"]), "norm_after_last": norm}
+
+
 def run_ours(a):
     import torch
     ws, rank, local = dist_env()
@@ -559,12 +613,14 @@ def run_ours(a):
         cpu = cpu_baseline_oracle(n, gates, pog, P, max_parts=64, budget_s=20.0)
         cpu["sample"] += f" ({method} k={k} plan)"
 
-    grid = c128 = alu = None
+    grid = c128 = alu = ml = q33 = None
     if rank == 0 and not a.no_grid:
         alu = alu_peaks()
         grid = grid_section(n, gates, st, peak)
         c128 = c128_section(n, gates, peak, alu["fp64"])
         alu = {k: round(v / 1e12, 3) for k, v in alu.items()}
+        ml = multilevel_section(peak)
+        q33 = qft33_section(peak)
 
     batch = serving = None
     if rank == 0 and not a.no_batch:
@@ -584,7 +640,7 @@ def run_ours(a):
                            "l2": "state (2 GiB) larger than L2 (129 MB); no flush needed"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": passes * a.steps, "compare": compare, "norm": norm,
-                "grid": grid, "c128": c128, "alu_peak_tflops": alu,
+                "grid": grid, "c128": c128, "alu_peak_tflops": alu, "multilevel": ml, "qft33": q33,
                 "batch": batch, "serving": serving}
         print(json.dumps(line), flush=True)
     st.close()

@@ -7,8 +7,9 @@ Admitted states stay on the device until their result is taken.
 * Admission. Small requests (n <= small_n) and large ones queue apart, each
   in arrival order. A large request at the head of its queue that does not
   fit waits for memory to free up, without holding back the small requests
-  behind it; small states are admitted within a share of the budget
-  (``small_budget``, default 1/8), so they cannot starve the large head.
+  behind it; small and medium (n <= mid_n) requests queue apart too, and
+  while a large request waits each class is admitted only within its share
+  of the budget (``small_budget``, default 1/8), so they cannot starve it.
 * Planning never blocks the loop. Each request's plan is built on a worker
   thread as it arrives (small and large requests on separate pools, so small
   plans never queue behind the large requests' plan choice); a request joins
@@ -167,6 +168,7 @@ class Server:
         on the wall clock scaled by time_scale. Returns (results, stats)."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         pend_small = collections.deque()      # arrived, not admitted (arrival order)
+        pend_mid = collections.deque()
         pend_large = collections.deque()
         small_wait = collections.deque()      # admitted small requests not in a batch
         large_wait = []                       # admitted large requests not started
@@ -176,7 +178,7 @@ class Server:
         futures = {}
         admitted_at = {}
         used = 0.0
-        small_used = 0.0
+        class_used = [0.0, 0.0]               # small, medium
         slots = 0
         results = []
         i = 0
@@ -193,22 +195,24 @@ class Server:
             return (time.perf_counter() - t0) / time_scale
 
         def finish(r, start, done, norm, p0, am, pm, state):
-            nonlocal used, small_used, slots
+            nonlocal used, slots
             results.append(Result(r.rid, r.n, r.arrival, admitted_at.pop(r.rid), start, done, norm, p0, am, pm,
                                   state))
             used -= self.state_bytes(r.n)
             if self._small(r):
-                small_used -= self.state_bytes(r.n)
+                class_used[0] -= self.state_bytes(r.n)
+            elif r.n <= self.mid_n:
+                class_used[1] -= self.state_bytes(r.n)
             slots -= 1
 
-        while (i < len(reqs) or pend_small or pend_large or small_wait or large_wait or running_large
+        while (i < len(reqs) or pend_small or pend_mid or pend_large or small_wait or large_wait or running_large
                or building or in_flight):
             t = now()
             while i < len(reqs) and reqs[i].arrival <= t:
                 r = reqs[i]
                 small = self._small(r)
                 futures[r.rid] = (self.pool if small else self.pool_large).submit(self._plan, r)
-                (pend_small if small else pend_large).append(r)
+                (pend_small if small else pend_mid if r.n <= self.mid_n else pend_large).append(r)
                 i += 1
             # admission: large requests in arrival order while the head fits
             while pend_large:
@@ -225,20 +229,24 @@ class Server:
                 slots += 1
                 admitted_at[r.rid] = now()
                 large_wait.append(r)
-            # small requests in arrival order beside them, within a share of
-            # the budget (small_budget), so the memory finished large requests
-            # free always reaches a waiting large head
-            while pend_small:
-                r = pend_small[0]
-                b = self.state_bytes(r.n)
-                if slots >= self.max_slots or used + b > self.budget or small_used + b > self.small_budget:
-                    break
-                pend_small.popleft()
-                used += b
-                small_used += b
-                slots += 1
-                admitted_at[r.rid] = now()
-                small_wait.append(r)
+            # small and medium requests in arrival order beside them; while a
+            # large request waits, each class stays within its share of the
+            # budget (small_budget), so the memory finished large requests
+            # free reaches the waiting head
+            for pend, dest in ((pend_small, small_wait), (pend_mid, large_wait)):
+                while pend:
+                    r = pend[0]
+                    b = self.state_bytes(r.n)
+                    cls = 0 if dest is small_wait else 1
+                    if (slots >= self.max_slots or used + b > self.budget
+                            or (pend_large and class_used[cls] + b > self.small_budget)):
+                        break
+                    pend.popleft()
+                    used += b
+                    class_used[cls] += b
+                    slots += 1
+                    admitted_at[r.rid] = now()
+                    dest.append(r)
             host["peak_used_bytes"] = max(host["peak_used_bytes"], used)
             # large requests start as running slots of their lane free up, once
             # planned: medium ones (n <= mid_n) on their own higher-priority
@@ -323,7 +331,7 @@ class Server:
                            b.state_host(j) if self.keep else None)
                 b.close()
             idle = not (running_large or building or in_flight)
-            if idle and i < len(reqs) and not (pend_small or pend_large or small_wait or large_wait):
+            if idle and i < len(reqs) and not (pend_small or pend_mid or pend_large or small_wait or large_wait):
                 wait = reqs[i].arrival - now()
                 if wait > 0:
                     time.sleep(min(wait * time_scale, 0.01))

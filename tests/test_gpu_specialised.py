@@ -81,9 +81,9 @@ def test_dense_and_specialised_mix():
     psi = random_state(n, 21)
     ref = sim.run(n, g, psi)
     _, api = native()
-    out = run_gpu(n, g, method="beam", k=8, psi=psi, tc=True, jit=True)
+    out = run_gpu(n, g, method="dagp", k=7, psi=psi, tc=True, jit=True)
     assert max_abs(out, ref) <= 1e-5
-    plan = api.Plan(g, n, "beam", 8)
+    plan = api.Plan(g, n, "dagp", 7)
     st = plan.stats("c64", 0, tc=True)
     assert 0 < st["dense"] < st["passes"], st
     plan.close()
