@@ -412,28 +412,31 @@ def grid_section(n, gates, st, peak):
 
 def c128_section(n, gates, peak, fp64_peak):
     """The same circuit on a complex128 state (4 GiB, the paper's precision):
-    time per step, pass GB/s against the copy bandwidth and the circuit's
-    algorithmic FP64 flops (GATE_FLOPS) per second against the measured FP64
-    FMA rate, on the interpreter and on the specialised kernels."""
+    time per step, pass GB/s against the copy bandwidth, and the FP64 flops
+    the plan's kernels execute (sv_plan_flops) per second against the
+    measured FP64 FMA rate, on the interpreter and on the specialised
+    kernels. The gate model's count (GATE_FLOPS, general matrices) is given
+    beside it."""
     from paper_2205_06973_gb300 import api
     st = api.State(n, "c128")
-    flops = circuit_flops(n, gates)
+    model = circuit_flops(n, gates)
     rows = []
     for method, k, jit in (("dagp", 10, False), ("dagp", 10, True), ("beam", 10, True), ("beam", 12, True)):
         plan = api.Plan(gates, n, method, k, dfs_trials=16)
         passes = plan.stats("c128")["passes"]
+        flops = plan.flops("c128")[0]
         cs = plan.specialise("c128") if jit else 0.0
         ms = _timed(st, plan, jit=jit, reps=1)
         gbs = passes * 2 * st.nbytes / (ms / 1e3) / 1e9
         fl = flops / (ms / 1e3)
         rows.append({"method": method, "k": k, "kernel": "specialised" if jit else "interpreter", "passes": passes,
                      "ms": round(ms, 1), "GBs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
-                     "fp64_tflops": round(fl / 1e12, 3), "fp64_frac": round(fl / fp64_peak, 4),
-                     "compile_s": round(cs, 2)})
+                     "executed_fp64_flops": flops, "fp64_tflops": round(fl / 1e12, 3),
+                     "fp64_frac": round(fl / fp64_peak, 4), "compile_s": round(cs, 2)})
         plan.close()
     norm = st.probs()
     st.close()
-    return {"workload": "28-qubit layered circuit, complex128 state (4 GiB)", "algorithmic_fp64_flops": flops,
+    return {"workload": "28-qubit layered circuit, complex128 state (4 GiB)", "gate_model_fp64_flops": model,
             "fp64_peak_tflops": round(fp64_peak / 1e12, 3), "rows": rows, "norm": norm}
 
 
@@ -813,6 +816,32 @@ def partition_quality():
     r1, r2 = rows(rand), rows(fam)
     print(json.dumps({"partition_quality": {"random_small": summary(r1), "families": summary(r2),
                                             "family_cases": r2}}))
+    print(json.dumps({"exchange_plans": exchange_report()}))
+
+
+def exchange_report():
+    """Exchanges of the distributed state (Sec. III-D) planned from each
+    builder's first-level partition under L_m = l = n - p on 2^p ranks, for
+    the 28-qubit layered circuit and the 33-qubit QFT: parts, all-to-all
+    exchanges and qubits moved (host only)."""
+    import synth
+    from paper_2205_06973_gb300 import api
+    from paper_2205_06973_gb300 import distributed as D
+    rows = []
+    n33, g33, _ = synth.qft_basis(33)
+    for name, (n, g) in (("layered28", synth.layered_28q()), ("qft33", (n33, g33))):
+        for p in (1, 2, 3):
+            for m in ("nat", "dfs", "dagp", "beam"):
+                pl = api.Plan(g, n, m, n - p)
+                pog, P = pl.export()
+                pl.close()
+                qs = [set() for _ in range(P)]
+                for i, x in enumerate(pog):
+                    qs[x] |= set(g[i][1])
+                ex, moved = D.count_exchanges([sorted(q) for q in qs], n, p)
+                rows.append({"circuit": name, "ranks": 1 << p, "method": m, "parts": P, "exchanges": ex,
+                             "qubits_moved": moved})
+    return rows
 
 
 def main():

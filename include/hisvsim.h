@@ -204,6 +204,18 @@ sv_status sv_plan_specialise(sv_plan *p, sv_precision prec, int tile_qubits, uin
  * source length. Host only. */
 sv_status sv_plan_source(sv_plan *p, sv_precision prec, int tile_qubits, uint32_t flags, uint32_t part, char *buf,
                          size_t cap, size_t *len);
+/* sv_plan_flops: the floating-point operations one apply of the plan
+ * executes for the precision, tile and flags (host only): *alu_flops on the
+ * CUDA cores, counted per op of the compiled program as its arithmetic over
+ * the amplitudes it touches (an FMA counts two; H 2, RX/RY 6, a fused 2x2
+ * 14, a diagonal 6 on the amplitudes it scales; permutations and sign
+ * changes 0; gate by gate: 14 per one-qubit and 30 per two-qubit gate, the
+ * general matrices of Sec. III-A), and *tensor_flops on the tensor cores
+ * (1536 per amplitude per dense part: three split-BF16 products of the
+ * 128 x 128 real block form). Either pointer may be NULL. The basis of the
+ * ALU roofline of the complex128 path. */
+sv_status sv_plan_flops(sv_plan *p, sv_precision prec, int tile_qubits, uint32_t flags, double *alu_flops,
+                        double *tensor_flops);
 sv_status sv_plan_destroy(sv_plan *p);
 
 /* ---------------------------------------------------------------- apply ---

@@ -72,6 +72,8 @@ _SIGS = {
     "sv_plan_export_inner": ([_vp, _vp, ctypes.c_size_t, _u32p], ctypes.c_int),
     "sv_plan_stats": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, _u32p, _u32p, _u32p, _u32p], ctypes.c_int),
     "sv_plan_destroy": ([_vp], ctypes.c_int),
+    "sv_plan_flops": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "sv_plan_specialise": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.c_int,
                             ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "sv_plan_source": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_char_p,

@@ -55,6 +55,14 @@ class Plan:
                                     ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
         return {"passes": a.value, "phases": b.value, "ops": c.value, "dense": d.value}
 
+    def flops(self, precision="c64", tile=0, tc=False, gatewise=False):
+        """(CUDA-core flops, tensor-core flops) of one apply (sv_plan_flops)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        flags = (N.SV_FLAG_TC_DENSE if tc else 0) | (N.SV_FLAG_GATEWISE if gatewise else 0)
+        N.check(N.lib.sv_plan_flops(self.h, N.SV_C128 if precision == "c128" else N.SV_C64, tile, flags,
+                                    ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def specialise(self, precision="c64", tile=0, tc=False, load=True):
         """Generate and compile the plan's specialised part kernels
         (SV_FLAG_SPECIALISE) now; load=False only compiles (no device).

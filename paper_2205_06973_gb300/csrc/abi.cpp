@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/hisvsim.h).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -383,6 +384,28 @@ sv_status sv_plan_source(sv_plan *p, sv_precision prec, int t, uint32_t flags, u
         std::memcpy(buf, src.data(), m);
         buf[m] = '\0';
     }
+    return SV_OK;
+}
+
+sv_status sv_plan_flops(sv_plan *p, sv_precision prec, int t, uint32_t flags, double *alu_flops,
+                        double *tensor_flops) {
+    if (!p) return fail(SV_ERR_ARG, "plan is NULL");
+    const bool fp64 = prec == SV_C128;
+    if (t == 0) t = default_tile(fp64, p->max_part);
+    if (t < part_tmin() || t > part_tmax(fp64)) return fail(SV_ERR_ARG, "tile_qubits out of range");
+    double a = 0.0, b = 0.0;
+    if (p->method == SV_PART_NONE || p->n < part_tmin() || (flags & SV_FLAG_GATEWISE)) {
+        // one general matrix per gate: 14 flops per amplitude for a 2x2, 30 for a 4x4
+        for (const GateRef &g : p->gates) a += g.arity == 1 ? 14.0 : 30.0;
+    } else {
+        const Program *hp = nullptr;
+        sv_status st = get_host_program(p, fp64, t, dense_mode(flags, fp64), &hp);
+        if (st != SV_OK) return st;
+        program_flops(*hp, a, b);
+    }
+    const double N = std::ldexp(1.0, p->n);
+    if (alu_flops) *alu_flops = a * N;
+    if (tensor_flops) *tensor_flops = b * N;
     return SV_OK;
 }
 

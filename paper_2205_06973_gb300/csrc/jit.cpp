@@ -207,6 +207,13 @@ std::string jit_part_source(const Program &prog, size_t pi) {
                 for (int q = 0; q < 8; q++) o << (q ? ", " : "") << L_(c + q);
                 o << "}; op_u2<NR, " << A << ">(a, m); }";
                 break;
+            case OP_RXS: o << "op_rxs<NR, " << A << ", " << B << ">(a, " << L_(c) << ");"; break;
+            case OP_RYS: o << "op_rys<NR, " << A << ", " << B << ">(a, " << L_(c) << ");"; break;
+            case OP_U2S:
+                o << "op_u2s<NR, " << A << ", " << B << ">(a";
+                for (int q = 0; q < 6; q++) o << ", " << L_(c + q);
+                o << ");";
+                break;
             case OP_RX: o << "op_rx<NR, " << A << ">(a, " << L_(c) << ", " << L_(c + 1) << ");"; break;
             case OP_RY: o << "op_ry<NR, " << A << ">(a, " << L_(c) << ", " << L_(c + 1) << ");"; break;
             case OP_X: o << "op_x<" << A << ">(a);"; break;

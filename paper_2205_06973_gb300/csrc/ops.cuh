@@ -113,6 +113,23 @@ __device__ __forceinline__ void run_ops(typename CT<Real>::T (&a)[1 << R], const
             const Real c = cf[0], s = cf[1];
             with_bit<R>(op.a, [&](auto bc) { op_ry<NR, decltype(bc)::value>(a, c, s); });
         } break;
+        case OP_RXS: {
+            const Real t = cf[0];
+            if (op.b == 0) with_bit<R>(op.a, [&](auto bc) { op_rxs<NR, decltype(bc)::value, 0>(a, t); });
+            else with_bit<R>(op.a, [&](auto bc) { op_rxs<NR, decltype(bc)::value, 1>(a, t); });
+        } break;
+        case OP_RYS: {
+            const Real t = cf[0];
+            if (op.b == 0) with_bit<R>(op.a, [&](auto bc) { op_rys<NR, decltype(bc)::value, 0>(a, t); });
+            else with_bit<R>(op.a, [&](auto bc) { op_rys<NR, decltype(bc)::value, 1>(a, t); });
+        } break;
+        case OP_U2S: {
+            const Real ur = cf[0], ui = cf[1], vr = cf[2], vi = cf[3], wr = cf[4], wi = cf[5];
+            if (op.b == 0)
+                with_bit<R>(op.a, [&](auto bc) { op_u2s<NR, decltype(bc)::value, 0>(a, ur, ui, vr, vi, wr, wi); });
+            else
+                with_bit<R>(op.a, [&](auto bc) { op_u2s<NR, decltype(bc)::value, 1>(a, ur, ui, vr, vi, wr, wi); });
+        } break;
         case OP_D: {
             const Real d0r = cf[0], d0i = cf[1], d1r = cf[2], d1i = cf[3];
             with_bit<R>(op.a, [&](auto bc) { op_d<NR, decltype(bc)::value>(a, d0r, d0i, d1r, d1i); });

@@ -66,6 +66,60 @@ __device__ __forceinline__ void op_ry(C (&a)[NR], Real c, Real s) {
     }
 }
 
+// Scaled rotations: the gate divided by its largest entry (the factor is
+// applied once, with the part's store factor), so every output component is
+// one multiply-add. F = form (see OP_RXS / OP_RYS / OP_U2S in program.hpp).
+template <int NR, int B, int F, typename C, typename Real>
+__device__ __forceinline__ void op_rxs(C (&a)[NR], Real t) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        if (F == 0) {            // (x + (-it) y, y + (-it) x)
+            a[i].x = x.x + t * y.y; a[i].y = x.y - t * y.x;
+            a[j].x = y.x + t * x.y; a[j].y = y.y - t * x.x;
+        } else {                 // (y + (it) x, x + (it) y)
+            a[i].x = y.x - t * x.y; a[i].y = y.y + t * x.x;
+            a[j].x = x.x - t * y.y; a[j].y = x.y + t * y.x;
+        }
+    }
+}
+
+template <int NR, int B, int F, typename C, typename Real>
+__device__ __forceinline__ void op_rys(C (&a)[NR], Real t) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        if (F == 0) {            // (x - t y, y + t x)
+            a[i].x = x.x - t * y.x; a[i].y = x.y - t * y.y;
+            a[j].x = y.x + t * x.x; a[j].y = y.y + t * x.y;
+        } else {                 // (t x - y, x + t y)
+            a[i].x = t * x.x - y.x; a[i].y = t * x.y - y.y;
+            a[j].x = x.x + t * y.x; a[j].y = x.y + t * y.y;
+        }
+    }
+}
+
+template <int NR, int B, int F, typename C, typename Real>
+__device__ __forceinline__ void op_u2s(C (&a)[NR], Real ur, Real ui, Real vr, Real vi, Real wr, Real wi) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        if (F == 0) {            // (x + u y, v x + w y)
+            a[i].x = x.x + ur * y.x - ui * y.y; a[i].y = x.y + ur * y.y + ui * y.x;
+        } else {                 // (u x + y, v x + w y)
+            a[i].x = y.x + ur * x.x - ui * x.y; a[i].y = y.y + ur * x.y + ui * x.x;
+        }
+        a[j].x = vr * x.x - vi * x.y + wr * y.x - wi * y.y;
+        a[j].y = vr * x.y + vi * x.x + wr * y.y + wi * y.x;
+    }
+}
+
 template <typename C, typename Real>
 __device__ __forceinline__ void cmul_in(C &v, Real dr, Real di) {
     const Real x = v.x, y = v.y;

@@ -390,8 +390,21 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
                     break;
                 case SV_GATE_X: emit(OP_X, rb[s0], 0, 0, 0); break;
                 case SV_GATE_Y: emit(OP_Y, rb[s0], 0, 0, 0); break;
-                case SV_GATE_RX: emit(OP_RX, rb[s0], 0, 0, coef({std::cos(th / 2), std::sin(th / 2)})); break;
-                case SV_GATE_RY: emit(OP_RY, rb[s0], 0, 0, coef({std::cos(th / 2), std::sin(th / 2)})); break;
+                case SV_GATE_RX: case SV_GATE_RY: {
+                    // the largest entry joins the part factor: RX = c [[1, -it], [-it, 1]]
+                    // (t = s/c) or -is [[it, 1], [1, it]] (t = c/s); RY = c [[1, -t], [t, 1]]
+                    // or s [[t, -1], [1, t]], whichever keeps |t| <= 1
+                    const double c = std::cos(th / 2), sn = std::sin(th / 2);
+                    const bool rx = gr.kind == SV_GATE_RX;
+                    if (std::fabs(c) >= std::fabs(sn)) {
+                        fmul(c, 0.0);
+                        emit(rx ? OP_RXS : OP_RYS, rb[s0], 0, 0, coef({sn / c}));
+                    } else {
+                        if (rx) fmul(0.0, -sn);
+                        else fmul(sn, 0.0);
+                        emit(rx ? OP_RXS : OP_RYS, rb[s0], 1, 0, coef({c / sn}));
+                    }
+                } break;
                 case SV_GATE_Z: case SV_GATE_S: case SV_GATE_T: case SV_GATE_P: {
                     double ang = gr.kind == SV_GATE_Z ? M_PI : gr.kind == SV_GATE_S ? M_PI / 2 : gr.kind == SV_GATE_T ? M_PI / 4 : th;
                     double dr = gr.kind == SV_GATE_Z ? -1.0 : std::cos(ang), di = gr.kind == SV_GATE_Z ? 0.0 : std::sin(ang);
@@ -487,7 +500,23 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
                     err = "fused non-diagonal gate on a thread slot";
                     return false;
                 }
-                emit(OP_U2, rb[sq], 0, 0, coef({M[0], M[1], M[2], M[3], M[4], M[5], M[6], M[7]}));
+                // divide by the larger of m00 and m01 (the part factor takes it):
+                // [[1, u], [v, w]] or [[u, 1], [v, w]], entries of modulus <= 1
+                {
+                    const bool f1 = std::hypot(M[2], M[3]) > std::hypot(M[0], M[1]);
+                    const double pr = f1 ? M[2] : M[0], pi = f1 ? M[3] : M[1];
+                    const double den = pr * pr + pi * pi;
+                    auto div = [&](double xr, double xi, double &qr, double &qi) {
+                        qr = (xr * pr + xi * pi) / den;
+                        qi = (xi * pr - xr * pi) / den;
+                    };
+                    double ur, ui, vr, vi, wr, wi;
+                    div(f1 ? M[0] : M[2], f1 ? M[1] : M[3], ur, ui);
+                    div(M[4], M[5], vr, vi);
+                    div(M[6], M[7], wr, wi);
+                    fmul(pr, pi);
+                    emit(OP_U2S, rb[sq], f1 ? 1 : 0, 0, coef({ur, ui, vr, vi, wr, wi}));
+                }
                 return true;
             };
             std::vector<std::vector<int>> pend(n);
@@ -574,7 +603,8 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
                     // register bits the op acts on non-diagonally
                     uint32_t touch = 0;
                     switch (op.kind) {
-                    case OP_H: case OP_U2: case OP_RX: case OP_RY: case OP_X: case OP_Y: touch = 1u << op.a; break;
+                    case OP_H: case OP_U2: case OP_RX: case OP_RY: case OP_X: case OP_Y: case OP_RXS: case OP_RYS:
+                    case OP_U2S: touch = 1u << op.a; break;
                     case OP_CX: touch = (1u << op.a) | (1u << op.b); break;
                     case OP_CXT: touch = 1u << op.b; break;
                     default: touch = 0; break;   // thread-bit phases: diagonal, they commute
@@ -607,6 +637,44 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
         prog.n_tiles.push_back(1ull << (n - t));
     }
     return true;
+}
+
+// Real floating-point operations per amplitude of the whole state that the
+// program's kernels execute (an FMA counts two; sign changes, permutations
+// and shared-memory moves count none): per op of a gate-list part, the
+// arithmetic of its template in ops_core.cuh over the amplitudes it touches,
+// plus the store factor; per dense part, the split-BF16 products (3 x 128
+// real MACs per real output, 1536 per complex amplitude, tensor cores).
+void program_flops(const Program &prog, double &alu_per_amp, double &tensor_per_amp) {
+    alu_per_amp = 0.0;
+    tensor_per_amp = 0.0;
+    const int NR = 1 << prog.R;
+    for (size_t i = 0; i < prog.kind.size(); i++) {
+        if (prog.kind[i] == 1) {
+            tensor_per_amp += 2.0 * 3.0 * 2.0 * 128.0;
+            continue;
+        }
+        const PartLaunch &L = prog.parts[prog.index[i]];
+        for (uint32_t p = 0; p < L.n_phases; p++) {
+            const Phase &ph = prog.phases[L.phase_begin + p];
+            for (uint32_t k = 0; k < ph.op_count; k++) {
+                const Op &op = prog.ops[ph.op_begin + k];
+                switch (op.kind) {
+                case OP_H: alu_per_amp += 2.0; break;                 // a + b, a - b per component pair
+                case OP_RX: case OP_RY: alu_per_amp += 6.0; break;    // c x + s y per component
+                case OP_U2: alu_per_amp += 14.0; break;               // 2x2 complex matrix-vector
+                case OP_RXS: case OP_RYS: alu_per_amp += 4.0; break;  // one multiply-add per component
+                case OP_U2S: alu_per_amp += 11.0; break;              // x + u y (8), v x + w y (14) per pair
+                case OP_D: case OP_DIAG: case OP_TAPPLY: alu_per_amp += 6.0; break;   // complex product, all
+                case OP_P: case OP_CPT: alu_per_amp += 3.0; break;    // complex product on half
+                case OP_CP: alu_per_amp += 1.5; break;                // complex product on a quarter
+                default: break;                                       // X, Y, Z, CX, CZ, SWAP, thread phases
+                }
+            }
+        }
+        if (L.flags & PL_STORE_FACTOR) alu_per_amp += 6.0;
+        (void)NR;
+    }
 }
 
 }  // namespace hisv

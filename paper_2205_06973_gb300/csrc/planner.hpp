@@ -45,6 +45,10 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
                      uint32_t n_parts, bool fp64, int t_cfg, int R, int dense_mode, Program &prog,
                      std::string &err, const std::vector<uint32_t> *inner = nullptr);
 
+// Floating-point operations per state amplitude that the program's kernels
+// execute: CUDA-core arithmetic (alu) and tensor-core products (tensor).
+void program_flops(const Program &prog, double &alu_per_amp, double &tensor_per_amp);
+
 // Fused unitary of gates acting on the qubits qs[0..k) (local bit j <-> qs[j]):
 // U = G_last ... G_first as a 2^k x 2^k row-major interleaved complex matrix.
 void fused_unitary(const std::vector<GateRef> &gates, const std::vector<int> &ids, const int *qs, int k,

@@ -38,6 +38,11 @@ enum OpKind : uint8_t {
     OP_TP2,      // tb, b = second thread bit; coef: d: per-thread phase *= d if both set
     OP_TAPPLY,   // multiply the thread's amplitudes by its phase, reset the phase to 1
     OP_DIAG,     // coef: 2^R phases (re, im): register amplitude i *= phase i (merged diagonal gates)
+    // Rotations with their largest entry factored out into the part factor
+    // (one multiply-add per output component instead of two); b = form:
+    OP_RXS,      // a; coef t. b = 0: RX = c [[1, -it], [-it, 1]], t = s/c; b = 1: RX = -is [[it, 1], [1, it]], t = c/s
+    OP_RYS,      // a; coef t. b = 0: RY = c [[1, -t], [t, 1]], t = s/c;    b = 1: RY = s [[t, -1], [1, t]], t = c/s
+    OP_U2S,      // a; coef u, v, w (re, im). b = 0: m00 [[1, u], [v, w]]; b = 1: m01 [[u, 1], [v, w]]
     OP_COUNT
 };
 

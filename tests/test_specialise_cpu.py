@@ -27,7 +27,7 @@ def test_generated_source_compiles(precision):
     st = plan.stats(precision)
     src = "".join(plan.source(i, precision) for i in range(st["passes"]))
     # every op kind of the interpreter appears in the generated code
-    for name in ("op_h<", "op_u2<", "op_rx<", "op_ry<", "op_x<", "op_y<", "op_p<", "op_cx<", "op_cz<",
+    for name in ("op_h<", "op_u2s<", "op_rxs<", "op_rys<", "op_x<", "op_y<", "op_p<", "op_cx<", "op_cz<",
                  "op_cp<", "op_cxt<", "tmul(", "cmul_in("):
         assert name in src, name
     assert len(re.findall(r'extern "C" __global__', src)) == st["passes"]
