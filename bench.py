@@ -415,28 +415,38 @@ def c128_section(n, gates, peak, fp64_peak):
     time per step, pass GB/s against the copy bandwidth, and the FP64 flops
     the plan's kernels execute (sv_plan_flops) per second against the
     measured FP64 FMA rate, on the interpreter and on the specialised
-    kernels. The gate model's count (GATE_FLOPS, general matrices) is given
-    beside it."""
+    kernels in FP64 and in double-float arithmetic (SV_C128DF: the same
+    operations on FP32 pipes, so the rate is FP64-equivalent operations per
+    second and may exceed the FP64 peak). The gate model's count
+    (GATE_FLOPS, general matrices) is given beside it."""
     from paper_2205_06973_gb300 import api
     st = api.State(n, "c128")
     model = circuit_flops(n, gates)
     rows = []
-    for method, k, jit in (("dagp", 10, False), ("dagp", 10, True), ("beam", 10, True), ("beam", 12, True)):
+    sdf = api.State(n, "c128df")
+    for method, k, jit, prec in (("dagp", 10, False, "c128"), ("dagp", 10, True, "c128"), ("beam", 10, True, "c128"),
+                                 ("beam", 10, True, "c128df"), ("beam", 8, True, "c128df"),
+                                 ("dagp", 10, True, "c128df")):
         plan = api.Plan(gates, n, method, k, dfs_trials=16)
         passes = plan.stats("c128")["passes"]
         flops = plan.flops("c128")[0]
-        cs = plan.specialise("c128") if jit else 0.0
-        ms = _timed(st, plan, jit=jit, reps=1)
+        cs = plan.specialise(prec) if jit else 0.0
+        ms = _timed(st if prec == "c128" else sdf, plan, jit=jit, reps=1)
         gbs = passes * 2 * st.nbytes / (ms / 1e3) / 1e9
         fl = flops / (ms / 1e3)
-        rows.append({"method": method, "k": k, "kernel": "specialised" if jit else "interpreter", "passes": passes,
+        rows.append({"method": method, "k": k, "precision": prec,
+                     "arithmetic": "double-float on FP32 pipes" if prec == "c128df" else "FP64",
+                     "kernel": "specialised" if jit else "interpreter", "passes": passes,
                      "ms": round(ms, 1), "GBs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
                      "executed_fp64_flops": flops, "fp64_tflops": round(fl / 1e12, 3),
                      "fp64_frac": round(fl / fp64_peak, 4), "compile_s": round(cs, 2)})
         plan.close()
     norm = st.probs()
+    norm_df = sdf.probs()
     st.close()
+    sdf.close()
     return {"workload": "28-qubit layered circuit, complex128 state (4 GiB)", "gate_model_fp64_flops": model,
+            "norm_df": norm_df,
             "fp64_peak_tflops": round(fp64_peak / 1e12, 3), "rows": rows, "norm": norm}
 
 

@@ -11,7 +11,16 @@
  * Conventions shared by every entry point
  *   - Amplitude x of an n-qubit state is stored at index x = sum_q b_q 2^q
  *     (little-endian, Sec. II-B / Fig. 1), interleaved (re, im):
- *     SV_C64 = two floats (8 bytes), SV_C128 = two doubles (16 bytes).
+ *     SV_C64 = two floats (8 bytes), SV_C128 = two doubles (16 bytes),
+ *     SV_C128DF = complex128 held as double-float pairs: each of the real and
+ *     imaginary parts is the unevaluated sum hi + lo of two floats (Dekker's
+ *     double-float format, about 48 significant bits), stored as (re.hi,
+ *     re.lo, im.hi, im.lo), 16 bytes. Its arithmetic runs on the FP32 pipes
+ *     (the FP64 rate of the GPU is a small fraction of its FP32 rate);
+ *     sv_upload / sv_copy_state / sv_download / sv_export_c128 take and give
+ *     double2 amplitudes, converted on the device; its parts always run on the
+ *     plan's specialised kernels (SV_FLAG_SPECIALISE implied; no gate-by-gate
+ *     or tensor-core path).
  *   - Handles (sv_state, sv_plan, sv_batch) are opaque, created and destroyed
  *     by the caller, and not thread-safe: one thread uses a handle at a time.
  *   - Device work is stream-ordered on the state's CUDA stream and the call
@@ -42,7 +51,7 @@ typedef enum {
     SV_ERR_INTERNAL = 7
 } sv_status;
 
-typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_precision;
+typedef enum { SV_C64 = 0, SV_C128 = 1, SV_C128DF = 2 } sv_precision;
 
 /* Part builders of Sec. IV-B; SV_PART_NONE runs gate by gate (one pass per gate).
  * SV_PART_EXACT: the minimum number of parts over all acyclic partitions with
@@ -128,6 +137,11 @@ sv_status sv_copy_state(sv_state *s, void *host_dst, size_t bytes);
  * copy asynchronous, so a caller can overlap one state's transfers with
  * another state's passes. bytes = state size. */
 sv_status sv_download(sv_state *s, void *host_dst, size_t bytes);
+/* sv_export_c128: the state's amplitudes as 2^n double2 values into the
+ * caller's device buffer dev_dst (bytes = 16 * 2^n), stream-ordered: a copy
+ * for SV_C128, the conversion hi + lo (exact in FP64) for SV_C128DF;
+ * SV_ERR_ARG for SV_C64. */
+sv_status sv_export_c128(sv_state *s, void *dev_dst, size_t bytes);
 /* Device address of the amplitudes and the number of bytes they occupy. */
 sv_status sv_device_ptr(sv_state *s, void **ptr, size_t *bytes);
 /* Synchronise the state's stream and report any pending device error; a

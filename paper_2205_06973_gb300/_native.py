@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhisvsim.so")
 
 SV_OK, SV_ERR_ARG, SV_ERR_OOM, SV_ERR_CUDA, SV_ERR_PARTITION, SV_ERR_TIMEOUT, SV_ERR_BUSY, SV_ERR_INTERNAL = range(8)
-SV_C64, SV_C128 = 0, 1
+SV_C64, SV_C128, SV_C128DF = 0, 1, 2
+PRECISIONS = {"c64": SV_C64, "c128": SV_C128, "c128df": SV_C128DF}
 SV_PART_NONE, SV_PART_NAT, SV_PART_DFS, SV_PART_DAGP, SV_PART_EXACT, SV_PART_BEAM = 0, 1, 2, 3, 4, 5
 METHODS = {"none": SV_PART_NONE, "nat": SV_PART_NAT, "dfs": SV_PART_DFS, "dagp": SV_PART_DAGP,
            "exact": SV_PART_EXACT, "beam": SV_PART_BEAM}
@@ -61,6 +62,7 @@ _SIGS = {
     "sv_batch_hold_last_item": ([_vp, ctypes.c_int], ctypes.c_int),
     "sv_qasm_parse": ([ctypes.c_char_p, _vp, _vp, _vp], ctypes.c_int),
     "sv_free_gates": ([_vp], None),
+    "sv_export_c128": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "sv_device_ptr": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "sv_sync": ([_vp], ctypes.c_int),
     "sv_set_tile": ([_vp, ctypes.c_int], ctypes.c_int),

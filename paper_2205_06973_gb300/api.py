@@ -50,7 +50,7 @@ class Plan:
 
     def stats(self, precision="c64", tile=0, tc=False):
         a, b, c, d = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
-        N.check(N.lib.sv_plan_stats(self.h, N.SV_C128 if precision == "c128" else N.SV_C64, tile,
+        N.check(N.lib.sv_plan_stats(self.h, N.PRECISIONS[precision], tile,
                                     N.SV_FLAG_TC_DENSE if tc else 0,
                                     ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
         return {"passes": a.value, "phases": b.value, "ops": c.value, "dense": d.value}
@@ -59,7 +59,7 @@ class Plan:
         """(CUDA-core flops, tensor-core flops) of one apply (sv_plan_flops)."""
         a, b = ctypes.c_double(), ctypes.c_double()
         flags = (N.SV_FLAG_TC_DENSE if tc else 0) | (N.SV_FLAG_GATEWISE if gatewise else 0)
-        N.check(N.lib.sv_plan_flops(self.h, N.SV_C128 if precision == "c128" else N.SV_C64, tile, flags,
+        N.check(N.lib.sv_plan_flops(self.h, N.PRECISIONS[precision], tile, flags,
                                     ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
@@ -68,14 +68,14 @@ class Plan:
         (SV_FLAG_SPECIALISE) now; load=False only compiles (no device).
         Returns the compile time in seconds."""
         s = ctypes.c_double()
-        N.check(N.lib.sv_plan_specialise(self.h, N.SV_C128 if precision == "c128" else N.SV_C64, tile,
+        N.check(N.lib.sv_plan_specialise(self.h, N.PRECISIONS[precision], tile,
                                          N.SV_FLAG_TC_DENSE if tc else 0, 1 if load else 0, ctypes.byref(s)))
         return s.value
 
     def source(self, part, precision="c64", tile=0, tc=False):
         """Generated CUDA source of gate-list part ``part``."""
         n = ctypes.c_size_t()
-        args = (self.h, N.SV_C128 if precision == "c128" else N.SV_C64, tile, N.SV_FLAG_TC_DENSE if tc else 0, part)
+        args = (self.h, N.PRECISIONS[precision], tile, N.SV_FLAG_TC_DENSE if tc else 0, part)
         N.check(N.lib.sv_plan_source(*args, None, 0, ctypes.byref(n)))
         buf = ctypes.create_string_buffer(n.value + 1)
         N.check(N.lib.sv_plan_source(*args, buf, n.value + 1, ctypes.byref(n)))
@@ -97,14 +97,16 @@ class State:
     """sv_create over a torch-owned device buffer on the current stream."""
 
     def __init__(self, n, precision="c64", device="cuda", stream=None, tile=0):
+        """precision: "c64", "c128", or "c128df" (complex128 held as
+        double-float pairs, computed on the FP32 pipes; see SV_C128DF)."""
         self.n = n
         self.precision = precision
-        self.amp_bytes = 16 if precision == "c128" else 8
+        self.amp_bytes = 8 if precision == "c64" else 16
         self.nbytes = self.amp_bytes << n
         self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.buf.device)
         h = ctypes.c_void_p()
-        N.check(N.lib.sv_create(n, N.SV_C128 if precision == "c128" else N.SV_C64,
+        N.check(N.lib.sv_create(n, N.PRECISIONS[precision],
                                 ctypes.c_void_p(self.buf.data_ptr()), self.nbytes,
                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
         self.h = h
@@ -119,13 +121,13 @@ class State:
         self = cls.__new__(cls)
         self.n = n
         self.precision = precision
-        self.amp_bytes = 16 if precision == "c128" else 8
+        self.amp_bytes = 8 if precision == "c64" else 16
         self.nbytes = self.amp_bytes << n
         assert amps.is_cuda and amps.numel() * amps.element_size() == self.nbytes and amps.is_contiguous()
         self.buf = amps
         self.stream = stream if stream is not None else torch.cuda.current_stream(amps.device)
         h = ctypes.c_void_p()
-        N.check(N.lib.sv_attach(n, N.SV_C128 if precision == "c128" else N.SV_C64,
+        N.check(N.lib.sv_attach(n, N.PRECISIONS[precision],
                                 ctypes.c_void_p(amps.data_ptr()), self.nbytes,
                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
         self.h = h
@@ -135,8 +137,20 @@ class State:
 
     # views of the amplitudes (no copy)
     def amplitudes(self):
+        """The amplitudes as a complex tensor view (complex64 / complex128
+        states; a double-float state gives a complex128 copy, export_c128)."""
+        if self.precision == "c128df":
+            return self.export_c128()
         dt = torch.complex128 if self.precision == "c128" else torch.complex64
         return self.buf.view(dt)
+
+    def export_c128(self, out=None):
+        """Complex128 device tensor of the amplitudes (sv_export_c128,
+        stream-ordered on the state's stream)."""
+        if out is None:
+            out = torch.empty(1 << self.n, dtype=torch.complex128, device=self.buf.device)
+        N.check(N.lib.sv_export_c128(self.h, ctypes.c_void_p(out.data_ptr()), out.numel() * 16))
+        return out
 
     def set_basis(self, x):
         N.check(N.lib.sv_set_basis(self.h, x))
@@ -147,7 +161,7 @@ class State:
         N.check(N.lib.sv_upload(self.h, ctypes.c_void_p(t.data_ptr()), self.nbytes))
 
     def copy_to_host(self, out=None):
-        dt = torch.complex128 if self.precision == "c128" else torch.complex64
+        dt = torch.complex64 if self.precision == "c64" else torch.complex128
         if out is None:
             out = torch.empty(1 << self.n, dtype=dt)
         N.check(N.lib.sv_copy_state(self.h, ctypes.c_void_p(out.data_ptr()), self.nbytes))

@@ -94,7 +94,7 @@ def tune_state(workload, n, gates, precision="c64", candidates=STATE_CANDIDATES,
     for cand in candidates:
         method, k, tc, tile = cand[:4]
         jit = cand[4] if len(cand) > 4 else False
-        if precision == "c128" and tc:
+        if precision != "c64" and tc:
             continue
         if k > n:
             continue
@@ -178,36 +178,52 @@ def tune_batch(workload, circuits, method="dfs", candidates=BATCH_CANDIDATES, sa
 
 
 # Cost model of one apply, from measurements on GB300 (complex64): a part
-# pass moves 2 x 8 x 2^n bytes at ~6.3 TB/s on either kernel; the gate-list
-# kernel adds ~2.6e-13 s per interpreter op and amplitude (28-qubit layered
-# circuit at k = 10: 245 ms for 91 passes and 2420 ops; 33-qubit QFT: 1656 ms
-# for 31 passes and 475 ops).
+# pass moves 2 x 8 x 2^n bytes at ~6.3 TB/s on any kernel; the gate-list
+# interpreter adds ~2.6e-13 s per op and amplitude (28-qubit layered circuit
+# at k = 10: 245 ms for 91 passes and 2420 ops; 33-qubit QFT: 1656 ms for 31
+# passes and 475 ops), the plan's specialised kernels ~1.6e-14 s (beam k = 8:
+# 74 ms for 94 passes and ~2400 ops).
 PASS_BYTES_PER_S = 6.3e12
 OP_S_PER_AMP = 2.6e-13
+OP_S_PER_AMP_JIT = 1.6e-14
 
 
-def estimate_s(n, stats, tc):
+def estimate_s(n, stats, tc, jit=False):
     """Estimated seconds of one apply of a plan with these statistics."""
     t = stats["passes"] * 2 * 8 * (1 << n) / PASS_BYTES_PER_S
     if not tc or stats["dense"] < stats["passes"]:
-        t += stats["ops"] * (1 << n) * OP_S_PER_AMP
+        t += stats["ops"] * (1 << n) * (OP_S_PER_AMP_JIT if jit else OP_S_PER_AMP)
     return t
 
 
-def choose_plan(gates, n, candidates=(("beam", 6, True), ("beam", 10, False))):
+# (builder, k, tensor-core dense parts, specialised kernels, smallest n)
+PLAN_CANDIDATES = (("beam", 6, True, False, 0), ("beam", 10, False, False, 0), ("beam", 8, False, True, 29),
+                   ("beam", 10, False, True, 29))
+
+
+def choose_plan(gates, n, candidates=PLAN_CANDIDATES):
     """Build each candidate plan and keep the one the cost model rates
-    fastest; returns (plan, tc, estimates). The other plans are closed."""
+    fastest; returns (plan, tc, estimates, jit). Specialised candidates
+    (compiled for the plan with NVRTC, ~0.3-3 s of host time, at its first
+    apply or by Plan.specialise) are tried only for states large enough that
+    their passes save more than the compilation costs. The other plans are
+    closed."""
     from . import api
     best = None
     est = []
-    for method, k, tc in candidates:
+    for cand in candidates:
+        method, k, tc = cand[:3]
+        jit = cand[3] if len(cand) > 3 else False
+        if len(cand) > 4 and n < cand[4]:
+            continue
         plan = api.Plan(gates, n, method, min(k, n), dfs_trials=16)
-        e = estimate_s(n, plan.stats("c64", 0, tc=tc), tc)
-        est.append({"method": method, "k": k, "tc": tc, "est_s": e})
+        e = estimate_s(n, plan.stats("c64", 0, tc=tc), tc, jit)
+        est.append({"method": method, "k": k, "tc": tc, "jit": jit, "est_s": e})
         if best is None or e < best[2]:
             if best is not None:
                 best[0].close()
-            best = (plan, tc, e)
+            best = (plan, tc, e, jit)
         else:
             plan.close()
-    return best[0], best[1], est
+    plan, tc, _, jit = best
+    return plan, tc, est, jit

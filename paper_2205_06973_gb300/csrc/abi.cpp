@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/hisvsim.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,8 +47,11 @@ namespace hisv {
 void set_last_error(const std::string &msg) { g_err = msg; }
 }
 
-static size_t amp_bytes(sv_precision p) { return p == SV_C128 ? 16 : 8; }
-static bool is_fp64(const sv_state *s) { return s->prec == SV_C128; }
+static size_t amp_bytes(sv_precision p) { return p == SV_C64 ? 8 : 16; }
+// complex128 and its double-float form share the FP64 program (tile, register bits)
+static bool is_fp64(const sv_state *s) { return s->prec != SV_C64; }
+static bool is_df(const sv_state *s) { return s->prec == SV_C128DF; }
+constexpr uint64_t kStageAmps = 1ull << 21;   // 32 MiB of double2 per staged download chunk
 
 // Default tile: 2^12 complex64 / 2^11 complex128 amplitudes per CTA (two
 // 64 KiB shared buffers, three CTAs per SM), grown to the plan's largest part.
@@ -69,7 +73,7 @@ static sv_status create_state(int n, sv_precision prec, void *dev_buf, size_t de
     if (!out) return fail(SV_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > 36) return fail(SV_ERR_ARG, "n_qubits must be in [1, 36]");
-    if (prec != SV_C64 && prec != SV_C128) return fail(SV_ERR_ARG, "bad precision");
+    if (prec != SV_C64 && prec != SV_C128 && prec != SV_C128DF) return fail(SV_ERR_ARG, "bad precision");
     const size_t bytes = amp_bytes(prec) << n;
     if (dev_buf && dev_buf_bytes < bytes) return fail(SV_ERR_ARG, "dev_buf smaller than 2^n amplitudes");
     if (dev_buf && (reinterpret_cast<uintptr_t>(dev_buf) & 15)) return fail(SV_ERR_ARG, "dev_buf must be 16-byte aligned");
@@ -99,7 +103,7 @@ static sv_status create_state(int n, sv_precision prec, void *dev_buf, size_t de
         dev_free(s->d_err, s->stream);
         return fail(SV_ERR_OOM, std::string("scratch allocation: ") + cudaGetErrorString(e));
     }
-    if (init) e = launch_set_basis(is_fp64(s.get()), s->buf, n, 0, s->stream);
+    if (init) e = launch_set_basis(is_fp64(s.get()), s->buf, n, 0, s->stream, is_df(s.get()));
     if (e != cudaSuccess) {
         if (s->owns) dev_free(s->buf, s->stream);
         dev_free(s->d_partials, s->stream);
@@ -128,6 +132,7 @@ sv_status sv_destroy(sv_state *s) {
     dev_free(s->d_partials, s->stream);
     dev_free(s->d_err, s->stream);
     dev_free(s->d_dnorm, s->stream);
+    dev_free(s->d_stage, s->stream);
     delete s;
     if (e != cudaSuccess) return fail(SV_ERR_CUDA, std::string("pending work failed: ") + cudaGetErrorString(e));
     return SV_OK;
@@ -136,7 +141,7 @@ sv_status sv_destroy(sv_state *s) {
 sv_status sv_set_basis(sv_state *s, uint64_t index) {
     if (!s) return fail(SV_ERR_ARG, "state is NULL");
     if (index >> s->n) return fail(SV_ERR_ARG, "basis index >= 2^n");
-    CUDA_TRY(launch_set_basis(is_fp64(s), s->buf, s->n, index, s->stream));
+    CUDA_TRY(launch_set_basis(is_fp64(s), s->buf, s->n, index, s->stream, is_df(s)));
     return SV_OK;
 }
 
@@ -144,13 +149,40 @@ sv_status sv_upload(sv_state *s, const void *src, size_t bytes) {
     if (!s || !src) return fail(SV_ERR_ARG, "NULL argument");
     if (bytes != s->bytes) return fail(SV_ERR_ARG, "bytes must equal the state size");
     CUDA_TRY(cudaMemcpyAsync(s->buf, src, bytes, cudaMemcpyHostToDevice, s->stream));
+    if (is_df(s)) CUDA_TRY(launch_to_df(s->buf, 1ull << s->n, s->stream));   // double2 -> hi + lo, in place
+    return SV_OK;
+}
+
+// Device -> host copy of the state (stream-ordered). A double-float state
+// goes through a staging buffer in chunks, each converted to double2 first.
+static sv_status copy_out(sv_state *s, void *dst) {
+    if (!is_df(s)) {
+        CUDA_TRY(cudaMemcpyAsync(dst, s->buf, s->bytes, cudaMemcpyDeviceToHost, s->stream));
+        return SV_OK;
+    }
+    const uint64_t N = 1ull << s->n, chunk = std::min<uint64_t>(N, kStageAmps);
+    if (!s->d_stage) {
+        cudaError_t e = dev_alloc(&s->d_stage, 16 * chunk, s->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->d_stage = nullptr;
+            return fail(SV_ERR_OOM, std::string("download staging: ") + cudaGetErrorString(e));
+        }
+    }
+    for (uint64_t i = 0; i < N; i += chunk) {
+        const uint64_t m = std::min(chunk, N - i);
+        CUDA_TRY(launch_from_df(static_cast<char *>(s->buf) + 16 * i, s->d_stage, m, s->stream));
+        CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(dst) + 16 * i, s->d_stage, 16 * m, cudaMemcpyDeviceToHost,
+                                 s->stream));
+    }
     return SV_OK;
 }
 
 sv_status sv_copy_state(sv_state *s, void *dst, size_t bytes) {
     if (!s || !dst) return fail(SV_ERR_ARG, "NULL argument");
     if (bytes != s->bytes) return fail(SV_ERR_ARG, "bytes must equal the state size");
-    CUDA_TRY(cudaMemcpyAsync(dst, s->buf, bytes, cudaMemcpyDeviceToHost, s->stream));
+    sv_status st = copy_out(s, dst);
+    if (st != SV_OK) return st;
     CUDA_TRY(cudaStreamSynchronize(s->stream));
     return SV_OK;
 }
@@ -158,7 +190,15 @@ sv_status sv_copy_state(sv_state *s, void *dst, size_t bytes) {
 sv_status sv_download(sv_state *s, void *dst, size_t bytes) {
     if (!s || !dst) return fail(SV_ERR_ARG, "NULL argument");
     if (bytes != s->bytes) return fail(SV_ERR_ARG, "bytes must equal the state size");
-    CUDA_TRY(cudaMemcpyAsync(dst, s->buf, bytes, cudaMemcpyDeviceToHost, s->stream));
+    return copy_out(s, dst);
+}
+
+sv_status sv_export_c128(sv_state *s, void *dev_dst, size_t bytes) {
+    if (!s || !dev_dst) return fail(SV_ERR_ARG, "NULL argument");
+    if (s->prec == SV_C64) return fail(SV_ERR_ARG, "sv_export_c128 needs a complex128 state");
+    if (bytes != s->bytes) return fail(SV_ERR_ARG, "bytes must equal the state size");
+    if (is_df(s)) CUDA_TRY(launch_from_df(s->buf, dev_dst, 1ull << s->n, s->stream));
+    else CUDA_TRY(cudaMemcpyAsync(dev_dst, s->buf, bytes, cudaMemcpyDeviceToDevice, s->stream));
     return SV_OK;
 }
 
@@ -309,7 +349,7 @@ static int dense_mode(uint32_t flags, bool fp64) { return ((flags & SV_FLAG_TC_D
 sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int t, uint32_t flags, uint32_t *passes, uint32_t *phases,
                         uint32_t *ops, uint32_t *dense) {
     if (!p) return fail(SV_ERR_ARG, "plan is NULL");
-    const bool fp64 = prec == SV_C128;
+    const bool fp64 = prec != SV_C64;
     if (t == 0) t = default_tile(fp64, p->max_part);
     if (t < part_tmin() || t > part_tmax(fp64)) return fail(SV_ERR_ARG, "tile_qubits out of range");
     if (p->method == SV_PART_NONE || p->n < part_tmin() || (flags & SV_FLAG_GATEWISE)) {
@@ -331,14 +371,16 @@ sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int t, uint32_t flags, ui
 
 // The plan's specialised part kernels for (precision, tile, dense mode),
 // compiled and loaded on first use.
-static sv_status get_jit_program(sv_plan *p, bool fp64, int t, int dense, const Program *hp, JitProgram **out) {
+static sv_status get_jit_program(sv_plan *p, sv_precision prec, int t, int dense, const Program *hp,
+                                 JitProgram **out) {
     std::lock_guard<std::recursive_mutex> lk(p->mu);
-    auto key = std::make_tuple(fp64, t, dense);
+    auto key = std::make_tuple((int)prec, t, dense);
     auto it = p->jit_progs.find(key);
     if (it == p->jit_progs.end()) {
         std::unique_ptr<JitProgram> jp(new JitProgram());
         std::string err;
-        if (!jit_compile(*hp, *jp, err, true)) return fail(SV_ERR_CUDA, "specialised part kernels: " + err);
+        if (!jit_compile(*hp, *jp, err, true, prec == SV_C128DF))
+            return fail(SV_ERR_CUDA, "specialised part kernels: " + err);
         it = p->jit_progs.emplace(key, std::move(jp)).first;
     }
     *out = it->second.get();
@@ -347,7 +389,7 @@ static sv_status get_jit_program(sv_plan *p, bool fp64, int t, int dense, const 
 
 sv_status sv_plan_specialise(sv_plan *p, sv_precision prec, int t, uint32_t flags, int load, double *compile_s) {
     if (!p) return fail(SV_ERR_ARG, "plan is NULL");
-    const bool fp64 = prec == SV_C128;
+    const bool fp64 = prec != SV_C64;
     if (t == 0) t = default_tile(fp64, p->max_part);
     if (t < part_tmin() || t > part_tmax(fp64)) return fail(SV_ERR_ARG, "tile_qubits out of range");
     const Program *hp = nullptr;
@@ -355,14 +397,15 @@ sv_status sv_plan_specialise(sv_plan *p, sv_precision prec, int t, uint32_t flag
     if (st != SV_OK) return st;
     if (load) {
         JitProgram *jp = nullptr;
-        st = get_jit_program(p, fp64, t, dense_mode(flags, fp64), hp, &jp);
+        st = get_jit_program(p, prec, t, dense_mode(flags, fp64), hp, &jp);
         if (st != SV_OK) return st;
         if (compile_s) *compile_s = jp->compile_s;
         return SV_OK;
     }
     JitProgram jp;
     std::string err;
-    if (!jit_compile(*hp, jp, err, false)) return fail(SV_ERR_CUDA, "specialised part kernels: " + err);
+    if (!jit_compile(*hp, jp, err, false, prec == SV_C128DF))
+        return fail(SV_ERR_CUDA, "specialised part kernels: " + err);
     if (compile_s) *compile_s = jp.compile_s;
     return SV_OK;
 }
@@ -370,14 +413,14 @@ sv_status sv_plan_specialise(sv_plan *p, sv_precision prec, int t, uint32_t flag
 sv_status sv_plan_source(sv_plan *p, sv_precision prec, int t, uint32_t flags, uint32_t part, char *buf, size_t cap,
                          size_t *len) {
     if (!p) return fail(SV_ERR_ARG, "plan is NULL");
-    const bool fp64 = prec == SV_C128;
+    const bool fp64 = prec != SV_C64;
     if (t == 0) t = default_tile(fp64, p->max_part);
     if (t < part_tmin() || t > part_tmax(fp64)) return fail(SV_ERR_ARG, "tile_qubits out of range");
     const Program *hp = nullptr;
     sv_status st = get_host_program(p, fp64, t, dense_mode(flags, fp64), &hp);
     if (st != SV_OK) return st;
     if (part >= hp->parts.size()) return fail(SV_ERR_ARG, "part index out of range");
-    const std::string src = jit_part_source(*hp, part);
+    const std::string src = jit_part_source(*hp, part, prec == SV_C128DF);
     if (len) *len = src.size();
     if (buf && cap) {
         const size_t m = std::min(cap - 1, src.size());
@@ -390,7 +433,7 @@ sv_status sv_plan_source(sv_plan *p, sv_precision prec, int t, uint32_t flags, u
 sv_status sv_plan_flops(sv_plan *p, sv_precision prec, int t, uint32_t flags, double *alu_flops,
                         double *tensor_flops) {
     if (!p) return fail(SV_ERR_ARG, "plan is NULL");
-    const bool fp64 = prec == SV_C128;
+    const bool fp64 = prec != SV_C64;
     if (t == 0) t = default_tile(fp64, p->max_part);
     if (t < part_tmin() || t > part_tmax(fp64)) return fail(SV_ERR_ARG, "tile_qubits out of range");
     double a = 0.0, b = 0.0;
@@ -516,6 +559,11 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
     if (!s || !p) return fail(SV_ERR_ARG, "NULL argument");
     if (p->n != s->n) return fail(SV_ERR_ARG, "plan and state qubit counts differ");
     sv_status st = SV_OK;
+    if (is_df(s)) {
+        if ((flags & SV_FLAG_GATEWISE) || p->method == SV_PART_NONE || s->n < part_tmin())
+            return fail(SV_ERR_ARG, "a double-float state runs parts of a partitioned plan (n >= 10) only");
+        flags = (flags | SV_FLAG_SPECIALISE) & ~SV_FLAG_TC_DENSE;
+    }
     if ((flags & SV_FLAG_GATEWISE) || p->method == SV_PART_NONE || s->n < part_tmin()) {
         st = apply_gatewise(s, p);
     } else {
@@ -527,7 +575,7 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
         if (st != SV_OK) return st;
         JitProgram *jp = nullptr;
         if ((flags & SV_FLAG_SPECIALISE) && !hp->parts.empty()) {
-            st = get_jit_program(p, fp64, t, dense_mode(flags, fp64), hp, &jp);
+            st = get_jit_program(p, s->prec, t, dense_mode(flags, fp64), hp, &jp);
             if (st != SV_OK) return st;
         }
         if (!hp->dense.empty()) {
@@ -570,7 +618,8 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
 sv_status sv_measure_probs(sv_state *s, void *dev_out, int out_fp64, double *norm_out) {
     if (!s) return fail(SV_ERR_ARG, "state is NULL");
     double *d_norm = s->d_partials + kProbBlocks;
-    CUDA_TRY(launch_probs(is_fp64(s), s->buf, s->n, dev_out, out_fp64, s->d_partials, kProbBlocks, d_norm, s->stream));
+    CUDA_TRY(launch_probs(is_fp64(s), s->buf, s->n, dev_out, out_fp64, s->d_partials, kProbBlocks, d_norm, s->stream,
+                          is_df(s)));
     if (norm_out) {
         CUDA_TRY(cudaMemcpyAsync(&s->h_norm, d_norm, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
         CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -589,7 +638,7 @@ sv_status sv_measure_summary(sv_state *s, double *norm_out, double *p0_out, uint
                              double *pmax_out) {
     if (!s) return fail(SV_ERR_ARG, "state is NULL");
     double *scratch = s->d_partials + kSummaryAt, *d_out = scratch + 3 * kProbBlocks;
-    CUDA_TRY(launch_summary(is_fp64(s), s->buf, s->n, scratch, kProbBlocks, d_out, s->stream));
+    CUDA_TRY(launch_summary(is_fp64(s), s->buf, s->n, scratch, kProbBlocks, d_out, s->stream, is_df(s)));
     double h[4];
     CUDA_TRY(cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));

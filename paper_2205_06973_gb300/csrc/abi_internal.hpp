@@ -53,6 +53,7 @@ struct sv_state {
     int *d_err = nullptr;           // device error word of bounded waits (0 = none)
     double *d_dnorm = nullptr;      // norm accumulators of one apply's dense passes
     size_t dnorm_cap = 0;           // (1 + dense parts), grown on demand
+    void *d_stage = nullptr;        // double2 staging of double-float downloads (allocated on first use)
 };
 
 struct sv_plan {
@@ -69,7 +70,7 @@ struct sv_plan {
     std::map<std::tuple<bool, int, int>, std::unique_ptr<Program>> host_progs;   // (fp64, t, dense)
     std::map<std::tuple<int, bool, int, int>, DevProgram> dev_progs;             // (dev, fp64, t, dense)
     std::vector<std::vector<double>> mats;                                 // gatewise matrices
-    std::map<std::tuple<bool, int, int>, std::unique_ptr<hisv::JitProgram>> jit_progs;   // (fp64, t, dense)
+    std::map<std::tuple<int, int, int>, std::unique_ptr<hisv::JitProgram>> jit_progs;   // (precision, t, dense)
     // the caches above are filled on first use; several host threads may
     // apply one plan (map nodes never move, so returned pointers stay valid)
     std::recursive_mutex mu;

@@ -69,10 +69,16 @@ Nvrtc &nvrtc() {
 
 // Exact literal of a coefficient in the kernel's precision (hexadecimal
 // floating point: the value the interpreter would read, rounded to nearest).
-std::string lit(double v, bool fp64) {
-    char b[64];
-    if (fp64) std::snprintf(b, sizeof(b), "(%a)", v);
-    else std::snprintf(b, sizeof(b), "(%af)", (double)(float)v);
+// Literal in one of the kernel's number formats: 0 float (v rounded to
+// nearest), 1 double, 2 double-float (hi = v rounded to float, lo = the rest
+// rounded to float).
+std::string lit(double v, int mode) {
+    char b[96];
+    if (mode == 1) std::snprintf(b, sizeof(b), "(%a)", v);
+    else if (mode == 2) {
+        const float hi = (float)v, lo = (float)(v - (double)hi);
+        std::snprintf(b, sizeof(b), "(df(%af, %af))", (double)hi, (double)lo);
+    } else std::snprintf(b, sizeof(b), "(%af)", (double)(float)v);
     return b;
 }
 
@@ -107,9 +113,10 @@ bool jit_available(std::string *why) {
     return n.ok;
 }
 
-std::string jit_part_source(const Program &prog, size_t pi) {
+std::string jit_part_source(const Program &prog, size_t pi, bool df) {
     const PartLaunch &L = prog.parts[pi];
     const bool fp64 = prog.fp64;
+    const int mode = df ? 2 : fp64 ? 1 : 0;
     const int t = prog.t, R = prog.R, TB = t - R, NT = 1 << TB, NRr = 1 << R;
     const size_t smem = 2 * ((size_t)(fp64 ? 16 : 8) << t);
     std::ostringstream o;
@@ -187,7 +194,7 @@ std::string jit_part_source(const Program &prog, size_t pi) {
       << "        Real tpr = 1, tpi = 0;\n"
       << "        (void)tpr; (void)tpi;\n";
     const std::vector<double> &cf = prog.coefs;
-    auto L_ = [&](uint32_t at) { return lit(cf[at], fp64); };
+    auto L_ = [&](uint32_t at) { return lit(cf[at], mode); };
     for (uint32_t p = 0; p < nph; p++) {
         const Phase &ph = prog.phases[L.phase_begin + p];
         if (p > 0)
@@ -268,11 +275,11 @@ std::string jit_part_source(const Program &prog, size_t pi) {
         }
     }
     if (L.flags & PL_STORE_FACTOR) {
-        o << "        { const Real gr = " << lit(L.gr, fp64) << ", gi = " << lit(L.gi, fp64) << ";\n"
+        o << "        { const Real gr = " << lit(L.gr, mode) << ", gi = " << lit(L.gi, mode) << ";\n"
           << "          const Real fr = gr * tpr - gi * tpi, fi = gr * tpi + gi * tpr;\n"
           << "#pragma unroll\n          for (int i = 0; i < NR; i++) cmul_in(a[i], fr, fi); }\n";
     }
-    o << "#pragma unroll\n        for (int i = 0; i < NR; i++) __stcs(sv + (base | st_thr | SG[i]), a[i]);\n"
+    o << "#pragma unroll\n        for (int i = 0; i < NR; i++) st_amp(sv + (base | st_thr | SG[i]), a[i]);\n"
       << "        base = nbase;\n"
       << "    }\n"
       << "    cp_wait0();\n"
@@ -280,7 +287,7 @@ std::string jit_part_source(const Program &prog, size_t pi) {
     return o.str();
 }
 
-bool jit_compile(const Program &prog, JitProgram &out, std::string &err, bool load) {
+bool jit_compile(const Program &prog, JitProgram &out, std::string &err, bool load, bool df) {
     Nvrtc &n = nvrtc();
     if (!n.ok) {
         err = "run-time compiler unavailable: " + n.why;
@@ -301,10 +308,11 @@ bool jit_compile(const Program &prog, JitProgram &out, std::string &err, bool lo
     std::vector<std::vector<char>> cubins(nchunks);
     std::vector<std::string> errs(nchunks);
     const std::string defs_fp = std::string("-DHISV_FP64=") + (prog.fp64 ? "1" : "0");
+    const std::string defs_df = std::string("-DHISV_DF=") + (df ? "1" : "0");
     const std::string defs_r = "-DHISV_R=" + std::to_string(prog.R);
     auto work = [&](size_t ci) {
         std::string src = "#include \"jit_prelude.cuh\"\n";
-        for (size_t i = ci; i < P; i += nchunks) src += jit_part_source(prog, i);
+        for (size_t i = ci; i < P; i += nchunks) src += jit_part_source(prog, i, df);
         const char *hdrs[2] = {kJitOpsCore, kJitPrelude};
         const char *hnames[2] = {"ops_core.cuh", "jit_prelude.cuh"};
         nvrtcProgram pr = nullptr;
@@ -313,8 +321,9 @@ bool jit_compile(const Program &prog, JitProgram &out, std::string &err, bool lo
             errs[ci] = std::string("nvrtcCreateProgram: ") + n.errstr(r);
             return;
         }
-        const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", defs_fp.c_str(), defs_r.c_str()};
-        r = n.compile(pr, 4, opts);
+        const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", defs_fp.c_str(), defs_r.c_str(),
+                              defs_df.c_str()};
+        r = n.compile(pr, 5, opts);
         if (r != NVRTC_SUCCESS) {
             size_t ls = 0;
             n.log_size(pr, &ls);

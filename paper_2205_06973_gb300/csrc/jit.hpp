@@ -26,14 +26,15 @@ struct JitProgram {
 };
 
 // CUDA source of gate-list part i of prog (one extern "C" kernel named
-// hisv_part_<i>); exposed for the host tests.
-std::string jit_part_source(const Program &prog, size_t i);
+// hisv_part_<i>); df: the complex128 program in double-float arithmetic on
+// double-float amplitudes (16 bytes each, like complex128).
+std::string jit_part_source(const Program &prog, size_t i, bool df = false);
 
 // Generate and compile every gate-list part of prog (chunks compiled in
 // parallel host threads) and, with load, load the code on the current
 // device's context (without load nothing touches a device). On failure
 // returns false with the compiler's log or the loader's error in err.
-bool jit_compile(const Program &prog, JitProgram &out, std::string &err, bool load);
+bool jit_compile(const Program &prog, JitProgram &out, std::string &err, bool load, bool df = false);
 
 // Launch part i of a compiled program on the stream (grid: resident CTAs per
 // SM times the SMs, at most one CTA per tile).

@@ -1,8 +1,8 @@
 // Prelude of the part kernels that are generated for one plan and compiled
 // at run time (NVRTC, sm_103a). Self-contained: only ops_core.cuh, which the
 // library hands to the compiler as an in-memory header. HISV_FP64 selects
-// complex128 (1) or complex64 (0) amplitudes; HISV_R the register bits per
-// thread.
+// complex128 (1) or complex64 (0) amplitudes, HISV_DF = 1 complex128 held as
+// double-float pairs; HISV_R the register bits per thread.
 //
 // A generated kernel is the part kernel of Algorithm 1 (Gather - Execute -
 // Scatter) with everything known at plan time folded in: the tile's qubits
@@ -15,7 +15,45 @@
 
 namespace hisv {
 
-#if HISV_FP64
+#if HISV_DF
+// Double-float arithmetic: a real is the unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi) / 2 (about 48 significant bits; Dekker 1971).
+// Sums use Knuth's error-free TwoSum of the high parts (TAOCP vol. 2, 4.2.2)
+// plus the low parts, renormalised by Dekker's FastTwoSum; products use the
+// error-free product of the high parts through one FMA, plus the cross terms.
+// The absolute error of an operation stays within a few units of 2^-48 of
+// its operands' magnitude.
+struct df {
+    float hi, lo;
+    df() = default;
+    __device__ __forceinline__ constexpr df(float h, float l) : hi(h), lo(l) {}
+    __device__ __forceinline__ df(int v) : hi((float)v), lo(0.f) {}
+};
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return df(s, b - (s - a));
+}
+__device__ __forceinline__ df operator+(df a, df b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return df_fast_two_sum(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+struct __align__(16) cdf {
+    df x, y;
+};
+typedef df Real;
+typedef cdf C;
+#elif HISV_FP64
 typedef double Real;
 typedef double2 C;
 #else
@@ -36,6 +74,15 @@ __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Streaming (evict-first) store of one amplitude.
+__device__ __forceinline__ void st_amp(C *p, const C &v) {
+#if HISV_DF
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo));
+#else
+    __stcs(p, v);
+#endif
+}
 
 // Deposit the bits of v, lowest first, into the set bits of mask.
 __device__ __forceinline__ u64 deposit64(u64 v, u64 mask) {

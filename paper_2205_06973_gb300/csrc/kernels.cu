@@ -352,15 +352,31 @@ cudaError_t launch_gate2(bool fp64, void *sv, int n, int q0, int q1, const doubl
 // ------------------------------------------------------------------------
 // probabilities and norm
 // ------------------------------------------------------------------------
-template <typename Real, typename Out>
-__global__ void __launch_bounds__(256) k_probs(const typename CT<Real>::T *__restrict__ sv, uint64_t N,
+// Real and imaginary part of a stored amplitude, in FP64: complex64
+// (float2), complex128 (double2) or double-float complex128 (float4: re.hi,
+// re.lo, im.hi, im.lo; each part is the sum of its two floats).
+__device__ __forceinline__ void amp_parts(const float2 &v, double &re, double &im) {
+    re = (double)v.x;
+    im = (double)v.y;
+}
+__device__ __forceinline__ void amp_parts(const double2 &v, double &re, double &im) {
+    re = v.x;
+    im = v.y;
+}
+__device__ __forceinline__ void amp_parts(const float4 &v, double &re, double &im) {
+    re = (double)v.x + (double)v.y;
+    im = (double)v.z + (double)v.w;
+}
+
+template <typename E, typename Out>
+__global__ void __launch_bounds__(256) k_probs(const E *__restrict__ sv, uint64_t N,
                                                 Out *__restrict__ out, double *__restrict__ partials) {
-    typedef typename CT<Real>::T C;
     __shared__ double red[8];
     double acc = 0.0;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
-        const C v = __ldcs(sv + i);
-        const double re = (double)v.x, im = (double)v.y;
+        const E v = __ldcs(sv + i);
+        double re, im;
+        amp_parts(v, re, im);
         const double p = re * re + im * im;
         if (out) out[i] = (Out)p;
         acc += p;
@@ -390,17 +406,20 @@ __global__ void k_sum(const double *__restrict__ partials, int nb, double *__res
 }
 
 cudaError_t launch_probs(bool fp64, const void *sv, int n, void *out, int out_fp64, double *partials,
-                         int nblocks, double *d_norm, cudaStream_t st) {
+                         int nblocks, double *d_norm, cudaStream_t st, bool df) {
     const uint64_t N = 1ull << n;
     uint64_t need = (N + 255) / 256;
     int nb = (int)(need < (uint64_t)nblocks ? need : (uint64_t)nblocks);
     if (nb < 1) nb = 1;
-    if (!fp64) {
-        if (out_fp64) k_probs<float, double><<<nb, 256, 0, st>>>((const float2 *)sv, N, (double *)out, partials);
-        else k_probs<float, float><<<nb, 256, 0, st>>>((const float2 *)sv, N, (float *)out, partials);
+    if (df) {
+        if (out_fp64) k_probs<float4, double><<<nb, 256, 0, st>>>((const float4 *)sv, N, (double *)out, partials);
+        else k_probs<float4, float><<<nb, 256, 0, st>>>((const float4 *)sv, N, (float *)out, partials);
+    } else if (!fp64) {
+        if (out_fp64) k_probs<float2, double><<<nb, 256, 0, st>>>((const float2 *)sv, N, (double *)out, partials);
+        else k_probs<float2, float><<<nb, 256, 0, st>>>((const float2 *)sv, N, (float *)out, partials);
     } else {
-        if (out_fp64) k_probs<double, double><<<nb, 256, 0, st>>>((const double2 *)sv, N, (double *)out, partials);
-        else k_probs<double, float><<<nb, 256, 0, st>>>((const double2 *)sv, N, (float *)out, partials);
+        if (out_fp64) k_probs<double2, double><<<nb, 256, 0, st>>>((const double2 *)sv, N, (double *)out, partials);
+        else k_probs<double2, float><<<nb, 256, 0, st>>>((const double2 *)sv, N, (float *)out, partials);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -418,18 +437,18 @@ __device__ __forceinline__ void better(double &p, uint64_t &i, double q, uint64_
     }
 }
 
-template <typename Real>
-__global__ void __launch_bounds__(256) k_summary(const typename CT<Real>::T *__restrict__ sv, uint64_t N,
+template <typename E>
+__global__ void __launch_bounds__(256) k_summary(const E *__restrict__ sv, uint64_t N,
                                                   double *__restrict__ sums, double *__restrict__ maxs,
                                                   uint64_t *__restrict__ idxs) {
-    typedef typename CT<Real>::T C;
     __shared__ double rs[8], rm[8];
     __shared__ uint64_t ri[8];
     double acc = 0.0, best = -1.0;
     uint64_t bi = ~0ull;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
-        const C v = __ldcs(sv + i);
-        const double re = (double)v.x, im = (double)v.y;
+        const E v = __ldcs(sv + i);
+        double re, im;
+        amp_parts(v, re, im);
         const double p = re * re + im * im;
         acc += p;
         better(best, bi, p, i);
@@ -461,8 +480,8 @@ __global__ void __launch_bounds__(256) k_summary(const typename CT<Real>::T *__r
 }
 
 // out[0] = sum |a|^2, out[1] = |a_0|^2, out[2] = max |a_x|^2, out[3] = its index (bits)
-template <typename Real>
-__global__ void k_summary_final(const typename CT<Real>::T *__restrict__ sv, const double *__restrict__ sums,
+template <typename E>
+__global__ void k_summary_final(const E *__restrict__ sv, const double *__restrict__ sums,
                                 const double *__restrict__ maxs, const uint64_t *__restrict__ idxs, int nb,
                                 double *__restrict__ out) {
     __shared__ double rs[256], rm[256];
@@ -485,7 +504,8 @@ __global__ void k_summary_final(const typename CT<Real>::T *__restrict__ sv, con
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double re = (double)sv[0].x, im = (double)sv[0].y;
+        double re, im;
+        amp_parts(sv[0], re, im);
         out[0] = rs[0];
         out[1] = re * re + im * im;
         out[2] = rm[0];
@@ -494,19 +514,22 @@ __global__ void k_summary_final(const typename CT<Real>::T *__restrict__ sv, con
 }
 
 cudaError_t launch_summary(bool fp64, const void *sv, int n, double *scratch, int nblocks, double *out,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool df) {
     const uint64_t N = 1ull << n;
     uint64_t need = (N + 255) / 256;
     int nb = (int)(need < (uint64_t)nblocks ? need : (uint64_t)nblocks);
     if (nb < 1) nb = 1;
     double *sums = scratch, *maxs = scratch + nblocks;
     uint64_t *idxs = reinterpret_cast<uint64_t *>(scratch + 2 * nblocks);
-    if (fp64) {
-        k_summary<double><<<nb, 256, 0, st>>>((const double2 *)sv, N, sums, maxs, idxs);
-        k_summary_final<double><<<1, 256, 0, st>>>((const double2 *)sv, sums, maxs, idxs, nb, out);
+    if (df) {
+        k_summary<float4><<<nb, 256, 0, st>>>((const float4 *)sv, N, sums, maxs, idxs);
+        k_summary_final<float4><<<1, 256, 0, st>>>((const float4 *)sv, sums, maxs, idxs, nb, out);
+    } else if (fp64) {
+        k_summary<double2><<<nb, 256, 0, st>>>((const double2 *)sv, N, sums, maxs, idxs);
+        k_summary_final<double2><<<1, 256, 0, st>>>((const double2 *)sv, sums, maxs, idxs, nb, out);
     } else {
-        k_summary<float><<<nb, 256, 0, st>>>((const float2 *)sv, N, sums, maxs, idxs);
-        k_summary_final<float><<<1, 256, 0, st>>>((const float2 *)sv, sums, maxs, idxs, nb, out);
+        k_summary<float2><<<nb, 256, 0, st>>>((const float2 *)sv, N, sums, maxs, idxs);
+        k_summary_final<float2><<<1, 256, 0, st>>>((const float2 *)sv, sums, maxs, idxs, nb, out);
     }
     return cudaGetLastError();
 }
@@ -572,12 +595,47 @@ __global__ void k_set_one(typename CT<Real>::T *sv, uint64_t idx) {
     sv[idx] = v;
 }
 
-cudaError_t launch_set_basis(bool fp64, void *sv, int n, uint64_t idx, cudaStream_t st) {
-    const size_t bytes = (fp64 ? 16ull : 8ull) << n;
+__global__ void k_set_one_df(float4 *sv, uint64_t idx) { sv[idx] = make_float4(1.f, 0.f, 0.f, 0.f); }
+
+cudaError_t launch_set_basis(bool fp64, void *sv, int n, uint64_t idx, cudaStream_t st, bool df) {
+    const size_t bytes = (fp64 || df ? 16ull : 8ull) << n;
     cudaError_t e = cudaMemsetAsync(sv, 0, bytes, st);
     if (e != cudaSuccess) return e;
-    if (fp64) k_set_one<double><<<1, 1, 0, st>>>((double2 *)sv, idx);
+    if (df) k_set_one_df<<<1, 1, 0, st>>>((float4 *)sv, idx);
+    else if (fp64) k_set_one<double><<<1, 1, 0, st>>>((double2 *)sv, idx);
     else k_set_one<float><<<1, 1, 0, st>>>((float2 *)sv, idx);
+    return cudaGetLastError();
+}
+
+// Double-float representation (Dekker 1971): a double d is held as the
+// unevaluated sum hi + lo of two floats, hi = d rounded to float and lo =
+// (d - hi) rounded to float (d - hi is exact in FP64). In place: each element
+// is read before it is written.
+__global__ void __launch_bounds__(256) k_to_df(double2 *__restrict__ sv, uint64_t N) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+        const double2 v = sv[i];
+        const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+        const float rl = __double2float_rn(v.x - (double)rh), il = __double2float_rn(v.y - (double)ih);
+        reinterpret_cast<float4 *>(sv)[i] = make_float4(rh, rl, ih, il);
+    }
+}
+
+// hi + lo back to FP64 (exact: lo lies below hi's last bit, the sum fits 53 bits).
+__global__ void __launch_bounds__(256) k_from_df(const float4 *__restrict__ src, double2 *__restrict__ dst,
+                                                 uint64_t N) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float4 v = src[i];
+        dst[i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
+}
+
+cudaError_t launch_to_df(void *sv, uint64_t n_amps, cudaStream_t st) {
+    k_to_df<<<grid_for(n_amps, 256), 256, 0, st>>>((double2 *)sv, n_amps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_df(const void *src, void *dst, uint64_t n_amps, cudaStream_t st) {
+    k_from_df<<<grid_for(n_amps, 256), 256, 0, st>>>((const float4 *)src, (double2 *)dst, n_amps);
     return cudaGetLastError();
 }
 

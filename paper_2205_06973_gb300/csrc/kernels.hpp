@@ -24,16 +24,22 @@ cudaError_t launch_gate2(bool fp64, void *sv, int n, int q0, int q1, const doubl
 // p[x] = |a_x|^2 (float or double out, may be null) and FP64 block partial sums
 // of the norm reduced into *d_norm. partials has nblocks doubles.
 cudaError_t launch_probs(bool fp64, const void *sv, int n, void *out, int out_fp64, double *partials,
-                         int nblocks, double *d_norm, cudaStream_t st);
+                         int nblocks, double *d_norm, cudaStream_t st, bool df = false);
 
 // Norm, |a_0|^2 and the largest |a_x|^2 with its index (ties to the smaller
 // index), FP64, without a probability vector: scratch holds 3 * nblocks
 // doubles, out 4 (out[3] holds the index's bits).
 cudaError_t launch_summary(bool fp64, const void *sv, int n, double *scratch, int nblocks, double *out,
-                           cudaStream_t st);
+                           cudaStream_t st, bool df = false);
 // FMA throughput of the CUDA cores in FP64 (fp64) or FP32, in FLOP/s (best of
 // a few timed launches over every SM; synchronises the stream).
 cudaError_t alu_probe(bool fp64, double *flops_per_s, cudaStream_t st);
-cudaError_t launch_set_basis(bool fp64, void *sv, int n, uint64_t idx, cudaStream_t st);
+cudaError_t launch_set_basis(bool fp64, void *sv, int n, uint64_t idx, cudaStream_t st, bool df = false);
+// Double-float complex128 (df = true above): each part of an amplitude is the
+// sum hi + lo of two floats, stored (re.hi, re.lo, im.hi, im.lo).
+// launch_to_df converts n_amps double2 amplitudes in place; launch_from_df
+// writes the double2 values of n_amps double-float amplitudes to dst.
+cudaError_t launch_to_df(void *sv, uint64_t n_amps, cudaStream_t st);
+cudaError_t launch_from_df(const void *src, void *dst, uint64_t n_amps, cudaStream_t st);
 
 }  // namespace hisv

@@ -46,7 +46,7 @@ extern "C" sv_status sv_probs_noalloc(const void *dev_state, int n_qubits, sv_pr
     if (n_qubits < 1 || n_qubits > 36) {
         return noalloc_fail(SV_ERR_ARG, "n_qubits must be in [1, 36]");
     }
-    if (prec != SV_C64 && prec != SV_C128) {
+    if (prec != SV_C64 && prec != SV_C128 && prec != SV_C128DF) {
         return noalloc_fail(SV_ERR_ARG, "bad precision");
     }
     if (n_blocks == 0) n_blocks = SV_NOALLOC_DEFAULT_BLOCKS;
@@ -90,8 +90,8 @@ extern "C" sv_status sv_probs_noalloc(const void *dev_state, int n_qubits, sv_pr
     }
     double *partials = static_cast<double *>(scratch);
     double *norm = dev_norm ? dev_norm : partials + SV_NOALLOC_MAX_BLOCKS;
-    e = hisv::launch_probs(prec == SV_C128, dev_state, n_qubits, dev_probs, out_fp64, partials, n_blocks, norm,
-                           reinterpret_cast<cudaStream_t>(stream));
+    e = hisv::launch_probs(prec != SV_C64, dev_state, n_qubits, dev_probs, out_fp64, partials, n_blocks, norm,
+                           reinterpret_cast<cudaStream_t>(stream), prec == SV_C128DF);
     if (e != cudaSuccess) {
         return noalloc_fail(SV_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     }

@@ -32,8 +32,9 @@ Admitted states stay on the device until their result is taken.
   largest, so a medium request's passes go between a large one's instead of
   queueing behind it. Each large request runs the plan the cost model of
   ``autotune.choose_plan`` rates fastest: the tensor-core dense plan
-  (beam-search parts, k = 6) or the gate-list plan (beam-search parts,
-  k = 10). With ``tc=False`` large requests use ``method_large`` /
+  (beam-search parts, k = 6), the gate-list plan (beam-search parts,
+  k = 10), or, for states of 29 qubits and more, the plan's specialised
+  kernels (k = 8 or 10, compiled on the planner thread). With ``tc=False`` large requests use ``method_large`` /
   ``k_large`` on the gate-list kernel.
 
 A request's result is a summary of its probability distribution (Sec. II-A):
@@ -133,17 +134,20 @@ class Server:
         return r.n <= self.small_n and self.mode == "parts"
 
     def _plan(self, r):
-        """Built on a worker thread: (plan, tc)."""
+        """Built on a worker thread: (plan, tc, jit)."""
         if self.mode != "parts":
-            return Plan(r.gates, r.n, "none", min(self.k_large, r.n)), False
+            return Plan(r.gates, r.n, "none", min(self.k_large, r.n)), False, False
         if self._small(r):
             if self.dense_min and r.n >= self.dense_min:
-                return Plan(r.gates, r.n, "beam", 6, dfs_trials=4), True
+                return Plan(r.gates, r.n, "beam", 6, dfs_trials=4), True, False
             return Plan(r.gates, r.n, self.method_small, min(self.k_small, r.n),
-                        dfs_trials=4 if self.method_small == "beam" else 16), False
+                        dfs_trials=4 if self.method_small == "beam" else 16), False, False
         if not self.tc:
-            return Plan(r.gates, r.n, self.method_large, min(self.k_large, r.n)), False
-        return autotune.choose_plan(r.gates, r.n)[:2]
+            return Plan(r.gates, r.n, self.method_large, min(self.k_large, r.n)), False, False
+        plan, tc, _, jit = autotune.choose_plan(r.gates, r.n)
+        if jit:
+            plan.specialise("c64", 0, tc=tc)   # compiled here, on the planner thread
+        return plan, tc, jit
 
     def _build_batch(self, take, plans, stream):
         """Built on the builder thread: the micro-batch with its graph captured."""
@@ -185,7 +189,7 @@ class Server:
         bsi = 0                               # next batch stream
         lsi = 0                               # next large-request stream
         msi = 0                               # next medium-request stream
-        host = {"batch_build_s": 0.0, "batches": 0, "batched_requests": 0, "large_tc": 0,
+        host = {"batch_build_s": 0.0, "batches": 0, "batched_requests": 0, "large_tc": 0, "large_jit": 0,
                 "admission_stalls": 0, "peak_used_bytes": 0.0}
         batch_times, batch_sizes, large_times = [], [], []
         stalled = False
@@ -260,8 +264,9 @@ class Server:
                     j += 1
                     continue
                 large_wait.pop(j)
-                plan, tc = futures.pop(r.rid).result()
+                plan, tc, jit = futures.pop(r.rid).result()
                 host["large_tc"] += int(tc)
+                host["large_jit"] += int(jit)
                 if is_mid:
                     stream = self.mid_streams[msi % len(self.mid_streams)]
                     msi += 1
@@ -270,7 +275,7 @@ class Server:
                     lsi += 1
                 st = self._new_state(r.n, stream)
                 start = now()
-                st.apply(plan, gatewise=self.mode != "parts", tc=tc)
+                st.apply(plan, gatewise=self.mode != "parts", tc=tc, jit=jit)
                 ev = torch.cuda.Event()
                 ev.record(st.stream)
                 running_large.append((r, st, plan, ev, start))

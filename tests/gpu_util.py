@@ -25,7 +25,7 @@ def run_gpu(n, gates, method="dagp", k=8, precision="c64", tile=0, psi=None, bas
     plan = api.Plan(gates, n, method if not gatewise else "none", k, seed=seed)
     st = api.State(n, precision, tile=tile)
     if psi is not None:
-        dt = torch.complex128 if precision == "c128" else torch.complex64
+        dt = torch.complex64 if precision == "c64" else torch.complex128
         st.upload(torch.from_numpy(np.ascontiguousarray(psi)).to(dt).pin_memory())
     else:
         st.set_basis(basis)
@@ -40,4 +40,4 @@ def max_abs(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max())
 
 
-TOL = {"c64": 1e-5, "c128": 1e-12}
+TOL = {"c64": 1e-5, "c128": 1e-12, "c128df": 1e-12}

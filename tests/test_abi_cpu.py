@@ -182,13 +182,19 @@ def test_cost_model_picks_kernel_per_circuit(native):
     from paper_2205_06973_gb300 import autotune
     n = 24
     ring = [("CZ", (q, (q + 1) % n), 0.0) for q in range(n)] * 3
-    plan, tc, est = autotune.choose_plan(ring, n)
-    assert not tc and len(est) == 2 and est[1]["est_s"] < est[0]["est_s"]
+    plan, tc, est, jit = autotune.choose_plan(ring, n)
+    assert not tc and not jit and len(est) == 2 and est[1]["est_s"] < est[0]["est_s"]
     plan.close()
     for n, g in (synth.layered_28q(n=24, depth=30), synth.qft_basis(26)[:2]):
-        plan, tc, est = autotune.choose_plan(g, n)
-        assert tc and est[0]["est_s"] < est[1]["est_s"]
+        plan, tc, est, jit = autotune.choose_plan(g, n)
+        assert tc and not jit and est[0]["est_s"] < est[1]["est_s"]
         plan.close()
+    # specialised candidates only from 29 qubits on (their compilation is
+    # host time that a smaller state's passes do not repay); choose_plan
+    # estimates them without compiling
+    plan, tc, est, jit = autotune.choose_plan(synth.qft_basis(30)[1], 30)
+    assert len(est) == 4 and any(e["jit"] for e in est)
+    plan.close()
 
 
 def test_new_builders_and_batch_entry_points_validate_arguments(native):

@@ -100,3 +100,21 @@ def test_gate_by_gate_matches_oracle(layered28):
     _, api = native()
     n, g, ref = layered28
     _check(api, n, g, ref, "dagp", 10, gatewise=True)
+
+
+def test_complex128_paths_match_oracle(layered28):
+    """The 28-qubit circuit in complex128, the paper's precision, on the FP64
+    interpreter kernel and on the plan's specialised kernels in FP64 and in
+    double-float arithmetic (SV_C128DF): max-abs <= 1e-12 against the oracle."""
+    _, api = native()
+    n, g, ref = layered28
+    plan = api.Plan(g, n, "beam", 10, dfs_trials=16)
+    for precision, jit in (("c128", False), ("c128", True), ("c128df", True)):
+        st = api.State(n, precision)
+        st.apply(plan, sync=True, jit=jit)
+        out = st.amplitudes() if precision == "c128" else st.export_c128()
+        mx = float(max((out[s:s + (1 << 24)] - ref[s:s + (1 << 24)]).abs().max() for s in range(0, 1 << n, 1 << 24)))
+        del out
+        st.close()
+        assert mx <= 1e-12, (precision, jit, mx)
+    plan.close()

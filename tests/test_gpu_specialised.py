@@ -15,7 +15,7 @@ from tests.test_gpu_parity import _all_kinds
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("precision", ["c64", "c128", "c128df"])
 @pytest.mark.parametrize("n", [10, 11, 13, 15])
 def test_all_gate_kinds(precision, n):
     g = _all_kinds(n, 300, 40 + n)
@@ -27,7 +27,8 @@ def test_all_gate_kinds(precision, n):
 
 
 @pytest.mark.parametrize("precision,tile", [("c64", 10), ("c64", 11), ("c64", 12), ("c64", 13),
-                                            ("c128", 10), ("c128", 11), ("c128", 12)])
+                                            ("c128", 10), ("c128", 11), ("c128", 12),
+                                            ("c128df", 10), ("c128df", 11), ("c128df", 12)])
 def test_tiles(precision, tile):
     n = 17
     _, g = synth.layered_28q(n=n, depth=12)
@@ -38,7 +39,7 @@ def test_tiles(precision, tile):
         assert max_abs(out, ref) <= TOL[precision], (method, k, tile)
 
 
-@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("precision", ["c64", "c128", "c128df"])
 def test_qft_and_long_runs(precision):
     """Diagonal-heavy parts (QFT: merged phase-vector ops) and long runs of
     one-qubit gates (fused 2x2 ops), with the thread-bit controls."""
@@ -113,3 +114,36 @@ def test_multilevel_plans(precision):
             st.close()
             assert max_abs(out, ref) <= TOL[precision], (m1, k1, m2, jit)
         plan.close()
+
+
+def test_double_float_state_io_and_reductions():
+    """A double-float complex128 state: upload and download round trip
+    (double -> hi + lo -> double keeps 48 bits: within 2^-47 relative), the
+    basis state, norm and summary reductions, the device export, and the
+    paths it has no kernels for refused."""
+    import torch
+    _, api = native()
+    N = api.N
+    n = 12
+    psi = random_state(n, 44)
+    st = api.State(n, "c128df")
+    st.upload(torch.from_numpy(psi).pin_memory())
+    back = st.copy_to_host().numpy()
+    assert np.abs(back - psi).max() <= 2.0 ** -47
+    dev = st.export_c128()
+    assert np.abs(dev.cpu().numpy() - back).max() == 0.0
+    assert abs(st.probs() - 1.0) <= 1e-12
+    norm, p0, am, pm = st.summary()
+    p = np.abs(back) ** 2
+    assert abs(norm - 1.0) <= 1e-12 and abs(p0 - p[0]) <= 1e-15 and am == int(np.argmax(p))
+    st.set_basis(77)
+    out = st.copy_to_host().numpy()
+    assert out[77] == 1.0 and np.count_nonzero(out) == 1
+    plan = api.Plan(synth.qft(n), n, "dagp", 8)
+    with pytest.raises(N.SvError):
+        st.apply(plan, gatewise=True)
+    st.apply(plan, sync=True)
+    ref = cf.qft_basis_amplitude(n, 77, np.arange(1 << n))
+    assert max_abs(st.copy_to_host().numpy(), ref) <= 1e-12
+    plan.close()
+    st.close()

@@ -18,7 +18,7 @@ def _api():
     return N, api
 
 
-@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("precision", ["c64", "c128", "c128df"])
 def test_generated_source_compiles(precision):
     N, api = _api()
     n = 13
