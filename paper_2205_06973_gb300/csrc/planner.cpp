@@ -628,6 +628,24 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
         L.n_phases = (uint32_t)prog.phases.size() - L.phase_begin;
         L.op_end = (uint32_t)prog.ops.size();
         L.coef_end = (uint32_t)prog.coefs.size();
+        // the part factor is one complex scalar: any op that multiplies every
+        // amplitude by a per-index phase (a merged diagonal) takes it into its
+        // coefficients, which saves the multiply at the store unless the last
+        // phase also left a per-thread phase to apply there
+        if (!last_tphase && (fr != 1.0 || fi != 0.0)) {
+            for (uint32_t o = L.op_begin; o < (uint32_t)prog.ops.size(); o++) {
+                if (prog.ops[o].kind != OP_DIAG) continue;
+                double *c = prog.coefs.data() + prog.ops[o].coef;
+                for (int i = 0; i < (1 << R); i++) {
+                    const double x = c[2 * i], y = c[2 * i + 1];
+                    c[2 * i] = x * fr - y * fi;
+                    c[2 * i + 1] = x * fi + y * fr;
+                }
+                fr = 1.0;
+                fi = 0.0;
+                break;
+            }
+        }
         L.gr = fr;
         L.gi = fi;
         L.flags = (last_tphase || fr != 1.0 || fi != 0.0) ? PL_STORE_FACTOR : 0u;
