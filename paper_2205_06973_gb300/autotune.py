@@ -76,7 +76,7 @@ STATE_CANDIDATES = (
     ("dagp", 10, False, 0, False), ("beam", 12, False, 0, False), ("dagp", 8, False, 0, False),
     ("beam", 8, False, 0, True), ("beam", 10, False, 0, True), ("beam", 12, False, 0, True),
     ("dagp", 10, False, 0, True), ("beam", 8, True, 0, True), ("beam", 10, False, 13, True),
-    ("beam", 8, False, 13, True),
+    ("beam", 8, False, 13, True), ("beam", 9, False, 0, True), ("beam", 11, False, 13, True),
 )
 BEAM_WIDTH = 64   # beam builder width for the tuned plans (0.3 s for 2520 gates)
 

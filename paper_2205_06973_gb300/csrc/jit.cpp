@@ -208,14 +208,20 @@ std::string jit_part_source(const Program &prog, size_t pi, bool df) {
             const int A = op.a, B = op.b;
             o << "        ";
             switch (op.kind) {
-            case OP_H: o << "op_h<NR, " << A << ">(a);"; break;
+            case OP_H:
+                if (mode == 0) o << "op_h2<" << A << ">(a);";   // packed f32x2
+                else o << "op_h<NR, " << A << ">(a);";
+                break;
             case OP_U2:
                 o << "{ const Real m[8] = {";
                 for (int q = 0; q < 8; q++) o << (q ? ", " : "") << L_(c + q);
                 o << "}; op_u2<NR, " << A << ">(a, m); }";
                 break;
             case OP_RXS: o << "op_rxs<NR, " << A << ", " << B << ">(a, " << L_(c) << ");"; break;
-            case OP_RYS: o << "op_rys<NR, " << A << ", " << B << ">(a, " << L_(c) << ");"; break;
+            case OP_RYS:
+                if (mode == 0) o << "op_rys2<" << A << ", " << B << ">(a, " << L_(c) << ");";
+                else o << "op_rys<NR, " << A << ", " << B << ">(a, " << L_(c) << ");";
+                break;
             case OP_U2S:
                 o << "op_u2s<NR, " << A << ", " << B << ">(a";
                 for (int q = 0; q < 6; q++) o << ", " << L_(c + q);

@@ -96,6 +96,66 @@ __device__ __forceinline__ u64 deposit64(u64 v, u64 mask) {
     return out;
 }
 
+#if !HISV_FP64 && !HISV_DF
+// Packed pairs of floats (sm_100+ f32x2 arithmetic): a complex64 amplitude is
+// one 64-bit register pair, so a complex sum or a real-scaled complex
+// multiply-add is one instruction.
+__device__ __forceinline__ unsigned long long pk(float2 v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+// t * b + c with the real t on both halves
+__device__ __forceinline__ float2 fma2(float t, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(make_float2(t, t))), "l"(pk(b)), "l"(pk(c)));
+    return upk(d);
+}
+// H without its 1/sqrt2 (x + y, x - y) and the scaled RY, packed.
+template <int B>
+__device__ __forceinline__ void op_h2(C (&a)[NR]) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        a[i] = add2(x, y);
+        a[j] = sub2(x, y);
+    }
+}
+template <int B, int F>
+__device__ __forceinline__ void op_rys2(C (&a)[NR], float t) {
+#pragma unroll
+    for (int i = 0; i < NR; i++) {
+        if (i & (1 << B)) continue;
+        const int j = i | (1 << B);
+        const C x = a[i], y = a[j];
+        if (F == 0) {            // (x - t y, y + t x)
+            a[i] = fma2(-t, y, x);
+            a[j] = fma2(t, x, y);
+        } else {                 // (t x - y, x + t y)
+            a[i] = fma2(t, x, make_float2(-y.x, -y.y));
+            a[j] = fma2(t, y, x);
+        }
+    }
+}
+#endif
+
 // X on register bit B: exchange the halves (a renaming).
 template <int B>
 __device__ __forceinline__ void op_x(C (&a)[NR]) {

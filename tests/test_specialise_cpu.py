@@ -27,7 +27,8 @@ def test_generated_source_compiles(precision):
     st = plan.stats(precision)
     src = "".join(plan.source(i, precision) for i in range(st["passes"]))
     # every op kind of the interpreter appears in the generated code
-    for name in ("op_h<", "op_u2s<", "op_rxs<", "op_rys<", "op_x<", "op_y<", "op_p<", "op_cx<", "op_cz<",
+    h = ("op_h2<", "op_rys2<") if precision == "c64" else ("op_h<", "op_rys<")
+    for name in h + ("op_u2s<", "op_rxs<", "op_x<", "op_y<", "op_p<", "op_cx<", "op_cz<",
                  "op_cp<", "op_cxt<", "tmul(", "cmul_in("):
         assert name in src, name
     assert len(re.findall(r'extern "C" __global__', src)) == st["passes"]
