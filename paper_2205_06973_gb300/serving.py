@@ -11,9 +11,9 @@ Admitted states stay on the device until their result is taken.
   while a large request waits each class is admitted only within its share
   of the budget (``small_budget``, default 1/8), so they cannot starve it.
 * Planning never blocks the loop. Each request's plan is built on a worker
-  thread as it arrives (small and large requests on separate pools, so small
-  plans never queue behind the large requests' plan choice); a request joins
-  a micro-batch, or starts, only once its plan is ready.
+  thread as it arrives (small, medium and large requests on separate pools,
+  so no class's plans queue behind another's); a request joins a
+  micro-batch, or starts, only once its plan is ready.
 * Small requests run in micro-batches on the batched persistent launch
   (sv_batch_*): the circuits of >= 13 qubits on the batched tensor-core
   kernel (beam-search parts of <= 6 qubits), the others on the gate-list
@@ -32,9 +32,12 @@ Admitted states stay on the device until their result is taken.
   largest, so a medium request's passes go between a large one's instead of
   queueing behind it. Each large request runs the plan the cost model of
   ``autotune.choose_plan`` rates fastest: the tensor-core dense plan
-  (beam-search parts, k = 6), the gate-list plan (beam-search parts,
-  k = 10), or, for states of 29 qubits and more, the plan's specialised
-  kernels (k = 8 or 10, compiled on the planner thread). With ``tc=False`` large requests use ``method_large`` /
+  (beam-search parts, k = 6) or the gate-list plan (beam-search parts,
+  k = 10); with ``jit_large`` also, for states of 29 qubits and more, the
+  plan's specialised kernels (k = 8 or 10), compiled on the planner thread
+  (off by default: a compilation takes 1-3 s of host time per request, which
+  under a stream of thousands of large requests holds the planners up more
+  than the kernels save). With ``tc=False`` large requests use ``method_large`` /
   ``k_large`` on the gate-list kernel.
 
 A request's result is a summary of its probability distribution (Sec. II-A):
@@ -100,7 +103,7 @@ class Server:
     def __init__(self, budget_bytes=170e9, max_slots=4096, small_n=20, batch_max=512, k_small=9,
                  k_large=6, tc=True, method_small="beam", method_large="dagp", mode="parts",
                  keep_states=False, planners=8, large_planners=4, large_running=2, dense_min_qubits=13,
-                 small_budget=None, mid_n=26, mid_running=4):
+                 small_budget=None, mid_n=26, mid_running=4, mid_planners=4, jit_large=False):
         self.budget = float(budget_bytes)
         self.small_budget = float(small_budget) if small_budget is not None else self.budget / 8
         self.max_slots = max_slots
@@ -119,6 +122,8 @@ class Server:
         self.dense_min = dense_min_qubits if (tc and mode == "parts") else 0
         self.pool = cf.ThreadPoolExecutor(max_workers=planners)
         self.pool_large = cf.ThreadPoolExecutor(max_workers=large_planners)
+        self.pool_mid = cf.ThreadPoolExecutor(max_workers=mid_planners)
+        self.jit_large = jit_large
         self.builder = cf.ThreadPoolExecutor(max_workers=1)
         lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
         mid = max(hi, lo - 1) if hi < lo else lo   # one step above the lowest priority
@@ -144,7 +149,9 @@ class Server:
                         dfs_trials=4 if self.method_small == "beam" else 16), False, False
         if not self.tc:
             return Plan(r.gates, r.n, self.method_large, min(self.k_large, r.n)), False, False
-        plan, tc, _, jit = autotune.choose_plan(r.gates, r.n)
+        cands = autotune.PLAN_CANDIDATES if self.jit_large else tuple(
+            c for c in autotune.PLAN_CANDIDATES if not (len(c) > 3 and c[3]))
+        plan, tc, _, jit = autotune.choose_plan(r.gates, r.n, candidates=cands)
         if jit:
             plan.specialise("c64", 0, tc=tc)   # compiled here, on the planner thread
         return plan, tc, jit
@@ -215,7 +222,8 @@ class Server:
             while i < len(reqs) and reqs[i].arrival <= t:
                 r = reqs[i]
                 small = self._small(r)
-                futures[r.rid] = (self.pool if small else self.pool_large).submit(self._plan, r)
+                pool = self.pool if small else self.pool_mid if r.n <= self.mid_n else self.pool_large
+                futures[r.rid] = pool.submit(self._plan, r)
                 (pend_small if small else pend_mid if r.n <= self.mid_n else pend_large).append(r)
                 i += 1
             # admission: large requests in arrival order while the head fits
@@ -373,5 +381,5 @@ class Server:
         return stats
 
     def close(self):
-        for p in (self.pool, self.pool_large, self.builder):
+        for p in (self.pool, self.pool_mid, self.pool_large, self.builder):
             p.shutdown(wait=True)
