@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--tc", type=int, default=0, help="with --k: run parts of <= 6 qubits on the tensor cores")
     ap.add_argument("--jit", type=int, default=0, help="with --k: gate-list parts on the plan's specialised kernels")
+    ap.add_argument("--regbits", type=int, default=0, help="with --jit: register bits per thread (0 = default)")
     ap.add_argument("--no-grid", action="store_true", help="skip the builder x k grid and the complex128 line")
     ap.add_argument("--n", type=int, default=28)
     ap.add_argument("--no-e2e", action="store_true")
@@ -372,14 +373,14 @@ def alu_peaks():
     return out
 
 
-def _timed(st, plan, tc=False, jit=False, reps=2):
+def _timed(st, plan, tc=False, jit=False, reps=2, regbits=0):
     import torch
-    st.apply(plan, sync=True, tc=tc, jit=jit)
+    st.apply(plan, sync=True, tc=tc, jit=jit, regbits=regbits)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st.stream)
     for _ in range(reps):
-        st.apply(plan, tc=tc, jit=jit)
+        st.apply(plan, tc=tc, jit=jit, regbits=regbits)
     e1.record(st.stream)
     e1.synchronize()
     st.sync()
@@ -518,25 +519,27 @@ def run_ours(a):
     n, gates = synth.layered_28q(n=a.n)
     st = api.State(n, "c64", tile=a.tile)
     if a.k:
-        choice = {"method": a.method, "k": a.k, "tc": bool(a.tc), "tile": a.tile, "jit": bool(a.jit), "trials": []}
+        choice = {"method": a.method, "k": a.k, "tc": bool(a.tc), "tile": a.tile, "jit": bool(a.jit),
+                  "regbits": a.regbits, "trials": []}
     else:
         from paper_2205_06973_gb300 import autotune
         choice = autotune.tune_state(f"layered{n}", n, gates, "c64", state=st, use_cache=False)
     k, tc, method = choice["k"], bool(choice["tc"]), choice["method"]
     jit = bool(choice.get("jit"))
+    regbits = int(choice.get("regbits") or 0)
     if choice.get("tile"):
         st = api.State(n, "c64", tile=choice["tile"])
     from paper_2205_06973_gb300.autotune import BEAM_WIDTH
     plan = api.Plan(gates, n, method, k, dfs_trials=BEAM_WIDTH if method == "beam" else 16)
-    stats = plan.stats("c64", choice.get("tile", 0), tc=tc)
+    stats = plan.stats("c64", choice.get("tile", 0), tc=tc, regbits=regbits)
     if jit:
-        plan.specialise("c64", choice.get("tile", 0), tc=tc)
+        plan.specialise("c64", choice.get("tile", 0), tc=tc, regbits=regbits)
     passes = stats["passes"]
     bytes_per_pass = 2 * st.nbytes
     bytes_per_step = passes * bytes_per_pass
 
     for _ in range(max(a.warmup, 3)):
-        st.apply(plan, tc=tc, jit=jit)
+        st.apply(plan, tc=tc, jit=jit, regbits=regbits)
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
@@ -546,7 +549,7 @@ def run_ours(a):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st.stream)
     for _ in range(a.steps):
-        st.apply(plan, tc=tc, jit=jit)
+        st.apply(plan, tc=tc, jit=jit, regbits=regbits)
     e1.record(st.stream)
     torch.cuda.synchronize()
     barrier(ws)
@@ -562,7 +565,7 @@ def run_ours(a):
     achieved = bytes_per_pass / (launch_ms / 1e3) / 1e9
     kernel = "k_dense6" if (tc and stats["dense"] * 2 >= passes) else ("hisv_part" if jit else "k_part")
     wkey = (f"layered{n}_{method}_k{k}_c64_{'tc' if tc else 't' + str(choice.get('tile') or 'auto')}"
-            f"{'_jit' if jit else ''}")
+            f"{'_jit' if jit else ''}{'_r' + str(regbits) if regbits else ''}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                 "traffic": traffic_from_profile(kernel, wkey), "kernel": kernel,
@@ -579,7 +582,7 @@ def run_ours(a):
         host_out = [torch.empty(1 << n, dtype=torch.complex64).pin_memory() for _ in range(2)]
         for i in range(2):
             sts[i].upload(host_in)
-            sts[i].apply(plan, tc=tc, jit=jit)
+            sts[i].apply(plan, tc=tc, jit=jit, regbits=regbits)
             sts[i].download(host_out[i])
         for x in sts:
             x.sync()
@@ -591,7 +594,7 @@ def run_ours(a):
             if i >= 2:
                 x.sync()          # its step i-2 result has reached host memory
             x.upload(host_in)
-            x.apply(plan, tc=tc, jit=jit)
+            x.apply(plan, tc=tc, jit=jit, regbits=regbits)
             x.download(host_out[i % 2])
         for x in sts:
             x.sync()
@@ -647,6 +650,8 @@ def run_ours(a):
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_TC if tc else DTYPE_FP32, "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_qubits": n, "gates": len(gates), "method": method,
                            "k": k, "tensor_core_dense_parts": stats["dense"], "passes": passes,
+                           "specialised_kernels": jit, "tile": choice.get("tile") or "default",
+                           "register_bits": regbits or "default",
                            "phases": stats["phases"], "ops": stats["ops"],
                            "autotune_trials": choice.get("trials", []),
                            "state_bytes": st.nbytes, "parallelism": f"replicas x{ws}",

@@ -97,6 +97,12 @@ typedef struct sv_plan sv_plan;
 #define SV_FLAG_TC_DENSE 0x4u   /* complex64, n >= 13: parts of at most 6 qubits run as one fused
                                    64x64 unitary on the tensor cores (split BF16, FP32
                                    accumulation); other parts keep the gate-list kernel */
+/* Register bits per thread of the gate-list part kernels (amplitudes per
+ * thread = 2^r, the register level of the tile): r in [3, 6] with
+ * SV_FLAG_SPECIALISE (the tile must keep at least 2^5 threads, t - r >= 5);
+ * 0 = the default (5 for complex64, 4 for complex128). The interpreter runs
+ * the default only (SV_ERR_ARG otherwise). */
+#define SV_FLAG_REGBITS(r) (((uint32_t)(r) & 0xFu) << 8)
 #define SV_FLAG_SPECIALISE 0x8u /* gate-list parts run as kernels generated for this plan, with
                                    the tile layout, register phases and every gate (with its
                                    coefficients) compiled in (NVRTC, sm_103a); compiled at the

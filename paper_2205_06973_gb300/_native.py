@@ -22,6 +22,12 @@ SV_FLAG_GATEWISE = 0x1
 SV_FLAG_SYNC = 0x2
 SV_FLAG_TC_DENSE = 0x4
 SV_FLAG_SPECIALISE = 0x8
+
+
+def SV_FLAG_REGBITS(r):
+    return (int(r) & 0xF) << 8
+
+
 SV_NOALLOC_MAX_BLOCKS = 4096
 
 GATE_KINDS = ("H", "X", "Y", "Z", "S", "T", "RX", "RY", "RZ", "P", "CX", "CZ", "CP", "SWAP")

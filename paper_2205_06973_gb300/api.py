@@ -48,10 +48,10 @@ class Plan:
         N.check(N.lib.sv_plan_export(self.h, pog.ctypes.data, self.G, ctypes.byref(P)))
         return pog[: self.G], P.value
 
-    def stats(self, precision="c64", tile=0, tc=False):
+    def stats(self, precision="c64", tile=0, tc=False, regbits=0):
         a, b, c, d = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
         N.check(N.lib.sv_plan_stats(self.h, N.PRECISIONS[precision], tile,
-                                    N.SV_FLAG_TC_DENSE if tc else 0,
+                                    (N.SV_FLAG_TC_DENSE if tc else 0) | N.SV_FLAG_REGBITS(regbits),
                                     ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
         return {"passes": a.value, "phases": b.value, "ops": c.value, "dense": d.value}
 
@@ -63,19 +63,22 @@ class Plan:
                                     ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
-    def specialise(self, precision="c64", tile=0, tc=False, load=True):
+    def specialise(self, precision="c64", tile=0, tc=False, load=True, regbits=0):
         """Generate and compile the plan's specialised part kernels
         (SV_FLAG_SPECIALISE) now; load=False only compiles (no device).
-        Returns the compile time in seconds."""
+        regbits: amplitudes per thread 2^regbits (0 = default). Returns the
+        compile time in seconds."""
         s = ctypes.c_double()
         N.check(N.lib.sv_plan_specialise(self.h, N.PRECISIONS[precision], tile,
-                                         N.SV_FLAG_TC_DENSE if tc else 0, 1 if load else 0, ctypes.byref(s)))
+                                         (N.SV_FLAG_TC_DENSE if tc else 0) | N.SV_FLAG_REGBITS(regbits),
+                                         1 if load else 0, ctypes.byref(s)))
         return s.value
 
-    def source(self, part, precision="c64", tile=0, tc=False):
+    def source(self, part, precision="c64", tile=0, tc=False, regbits=0):
         """Generated CUDA source of gate-list part ``part``."""
         n = ctypes.c_size_t()
-        args = (self.h, N.PRECISIONS[precision], tile, N.SV_FLAG_TC_DENSE if tc else 0, part)
+        args = (self.h, N.PRECISIONS[precision], tile,
+                (N.SV_FLAG_TC_DENSE if tc else 0) | N.SV_FLAG_REGBITS(regbits), part)
         N.check(N.lib.sv_plan_source(*args, None, 0, ctypes.byref(n)))
         buf = ctypes.create_string_buffer(n.value + 1)
         N.check(N.lib.sv_plan_source(*args, buf, n.value + 1, ctypes.byref(n)))
@@ -173,9 +176,10 @@ class State:
         N.check(N.lib.sv_download(self.h, ctypes.c_void_p(out.data_ptr()), self.nbytes))
         return out
 
-    def apply(self, plan: Plan, gatewise=False, sync=False, tc=False, jit=False):
+    def apply(self, plan: Plan, gatewise=False, sync=False, tc=False, jit=False, regbits=0):
         flags = ((N.SV_FLAG_GATEWISE if gatewise else 0) | (N.SV_FLAG_SYNC if sync else 0)
-                 | (N.SV_FLAG_TC_DENSE if tc else 0) | (N.SV_FLAG_SPECIALISE if jit else 0))
+                 | (N.SV_FLAG_TC_DENSE if tc else 0) | (N.SV_FLAG_SPECIALISE if jit else 0)
+                 | N.SV_FLAG_REGBITS(regbits))
         N.check(N.lib.sv_apply_parts(self.h, plan.h, flags))
 
     def probs(self, out=None, fp64=False):

@@ -55,13 +55,13 @@ def cached_k(workload, method, precision):
     return None
 
 
-def _time_apply(st, plan, tc, reps, jit=False):
-    st.apply(plan, sync=True, tc=tc, jit=jit)
+def _time_apply(st, plan, tc, reps, jit=False, regbits=0):
+    st.apply(plan, sync=True, tc=tc, jit=jit, regbits=regbits)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st.stream)
     for _ in range(reps):
-        st.apply(plan, tc=tc, jit=jit)
+        st.apply(plan, tc=tc, jit=jit, regbits=regbits)
     e1.record(st.stream)
     e1.synchronize()
     st.sync()
@@ -69,7 +69,7 @@ def _time_apply(st, plan, tc, reps, jit=False):
 
 
 # (part builder, k, tensor-core dense parts, tile (0 = default), specialised
-# gate-list kernels)
+# gate-list kernels, register bits per thread (0 = default; specialised only))
 STATE_CANDIDATES = (
     ("beam", 6, True, 0, False), ("dagp", 6, True, 0, False), ("beam", 5, True, 0, False),
     ("dfs", 6, True, 0, False), ("beam", 8, True, 0, False), ("beam", 10, False, 0, False),
@@ -77,6 +77,7 @@ STATE_CANDIDATES = (
     ("beam", 8, False, 0, True), ("beam", 10, False, 0, True), ("beam", 12, False, 0, True),
     ("dagp", 10, False, 0, True), ("beam", 8, True, 0, True), ("beam", 10, False, 13, True),
     ("beam", 8, False, 13, True), ("beam", 9, False, 0, True), ("beam", 11, False, 13, True),
+    ("beam", 9, False, 0, True, 4), ("beam", 10, False, 13, True, 4), ("beam", 9, False, 13, True, 4),
 )
 BEAM_WIDTH = 64   # beam builder width for the tuned plans (0.3 s for 2520 gates)
 
@@ -95,6 +96,7 @@ def tune_state(workload, n, gates, precision="c64", candidates=STATE_CANDIDATES,
     for cand in candidates:
         method, k, tc, tile = cand[:4]
         jit = cand[4] if len(cand) > 4 else False
+        regbits = cand[5] if len(cand) > 5 else 0
         if precision != "c64" and tc:
             continue
         if k > n:
@@ -108,9 +110,9 @@ def tune_state(workload, n, gates, precision="c64", candidates=STATE_CANDIDATES,
                 from . import _native as N
                 N.check(N.lib.sv_set_tile(st.h, tile))
             if jit:
-                compile_s = plan.specialise(precision, tile, tc=tc)
-            ms = _time_apply(st, plan, tc, reps, jit=jit)
-            stats = plan.stats(precision, tile, tc=tc)
+                compile_s = plan.specialise(precision, tile, tc=tc, regbits=regbits)
+            ms = _time_apply(st, plan, tc, reps, jit=jit, regbits=regbits)
+            stats = plan.stats(precision, tile, tc=tc, regbits=regbits)
         except Exception as e:   # a configuration the library rejects (tile too small, no NVRTC)
             if log:
                 log(f"tune: skip {method} k={k} tc={tc} tile={tile} jit={jit}: {e}")
@@ -120,7 +122,8 @@ def tune_state(workload, n, gates, precision="c64", candidates=STATE_CANDIDATES,
             if tile:
                 from . import _native as N
                 N.lib.sv_set_tile(st.h, 0)
-        trials.append({"method": method, "k": k, "tc": tc, "tile": tile, "jit": jit, "ms": round(ms, 3),
+        trials.append({"method": method, "k": k, "tc": tc, "tile": tile, "jit": jit, "regbits": regbits,
+                       "ms": round(ms, 3),
                        "passes": stats["passes"], "plan_s": round(plan_s, 3), "compile_s": round(compile_s, 2)})
         plan.close()
     if own:

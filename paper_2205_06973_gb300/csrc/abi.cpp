@@ -335,7 +335,8 @@ static sv_status get_host_program(sv_plan *p, bool fp64, int t, int dense, const
     if (it == p->host_progs.end()) {
         std::unique_ptr<Program> prog(new Program());
         std::string err;
-        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, fp64, t, part_R(fp64), dense, *prog, err,
+        const int R = (dense >> 4) ? (dense >> 4) : part_R(fp64);
+        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, fp64, t, R, dense & 1, *prog, err,
                              p->inner.empty() ? nullptr : &p->inner))
             return fail(SV_ERR_PARTITION, err);
         it = p->host_progs.emplace(key, std::move(prog)).first;
@@ -344,7 +345,11 @@ static sv_status get_host_program(sv_plan *p, bool fp64, int t, int dense, const
     return SV_OK;
 }
 
-static int dense_mode(uint32_t flags, bool fp64) { return ((flags & SV_FLAG_TC_DENSE) && !fp64) ? 1 : 0; }
+// Program variant of the flags: bit 0 = tensor-core dense parts (complex64
+// only), bits 4-7 = register bits per thread when not the precision's default.
+static int dense_mode(uint32_t flags, bool fp64) {
+    return (((flags & SV_FLAG_TC_DENSE) && !fp64) ? 1 : 0) | (int)(((flags >> 8) & 0xFu) << 4);
+}
 
 sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int t, uint32_t flags, uint32_t *passes, uint32_t *phases,
                         uint32_t *ops, uint32_t *dense) {
@@ -574,6 +579,8 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
         st = get_dev_program(s, p, t, dense_mode(flags, fp64), &hp, &dp);
         if (st != SV_OK) return st;
         JitProgram *jp = nullptr;
+        if (((flags >> 8) & 0xFu) && !(flags & SV_FLAG_SPECIALISE))
+            return fail(SV_ERR_ARG, "register bits other than the default need SV_FLAG_SPECIALISE");
         if ((flags & SV_FLAG_SPECIALISE) && !hp->parts.empty()) {
             st = get_jit_program(p, s->prec, t, dense_mode(flags, fp64), hp, &jp);
             if (st != SV_OK) return st;

@@ -56,15 +56,16 @@ def _compare(ref, out, chunk=1 << 24):
     return mx, (d2 / r2) ** 0.5, fid, o2 ** 0.5
 
 
-def _check(api, n, g, ref, method, k, tc=False, gatewise=False, dfs_trials=16, jit=False):
+def _check(api, n, g, ref, method, k, tc=False, gatewise=False, dfs_trials=16, jit=False, regbits=0, tile=0):
     plan = api.Plan(g, n, method, k, dfs_trials=dfs_trials)
-    st = api.State(n, "c64")
-    st.apply(plan, sync=True, tc=tc, gatewise=gatewise, jit=jit)
-    stats = plan.stats("c64", 0, tc=tc)
+    st = api.State(n, "c64", tile=tile)
+    st.apply(plan, sync=True, tc=tc, gatewise=gatewise, jit=jit, regbits=regbits)
+    stats = plan.stats("c64", tile, tc=tc, regbits=regbits)
     mx, rel, fid, nrm = _compare(ref, st.amplitudes())
     st.close()
     plan.close()
-    tag = f"{method} k={k} tc={tc} jit={jit} gatewise={gatewise} passes={stats['passes']} dense={stats['dense']}"
+    tag = (f"{method} k={k} tc={tc} jit={jit} tile={tile} regbits={regbits} gatewise={gatewise} "
+           f"passes={stats['passes']} dense={stats['dense']}")
     assert mx <= MAX_ABS, f"{tag}: max-abs {mx:.3e}"
     assert rel <= REL_L2, f"{tag}: rel-L2 {rel:.3e}"
     assert fid >= FIDELITY, f"{tag}: fidelity {fid}"
@@ -79,9 +80,11 @@ def test_benchmark_plans_match_oracle(layered28):
     _, api = native()
     from paper_2205_06973_gb300.autotune import BEAM_WIDTH, STATE_CANDIDATES
     n, g, ref = layered28
-    for method, k, tc, _tile, jit in STATE_CANDIDATES:
+    for cand in STATE_CANDIDATES:
+        method, k, tc, tile, jit = cand[:5]
+        regbits = cand[5] if len(cand) > 5 else 0
         stats = _check(api, n, g, ref, method, k, tc=tc, dfs_trials=BEAM_WIDTH if method == "beam" else 16,
-                       jit=jit)
+                       jit=jit, regbits=regbits, tile=tile)
         if tc and k <= 6:
             assert stats["dense"] == stats["passes"]
 

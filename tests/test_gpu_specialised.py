@@ -147,3 +147,25 @@ def test_double_float_state_io_and_reductions():
     assert max_abs(st.copy_to_host().numpy(), ref) <= 1e-12
     plan.close()
     st.close()
+
+
+@pytest.mark.parametrize("precision,regbits,tile", [("c64", 4, 12), ("c64", 6, 12), ("c64", 4, 13),
+                                                    ("c128", 3, 11), ("c128df", 3, 11)])
+def test_register_bits(precision, regbits, tile):
+    """2^r amplitudes per thread (SV_FLAG_REGBITS) against the oracle."""
+    _, api = native()
+    import torch
+    n = 16
+    g = _all_kinds(n, 300, 71) + synth.qft(n)[:80]
+    psi = random_state(n, 72)
+    ref = sim.run(n, g, psi)
+    dt = torch.complex64 if precision == "c64" else torch.complex128
+    for method, k in (("dagp", 8), ("beam", 10)):
+        plan = api.Plan(g, n, method, k)
+        st = api.State(n, precision, tile=tile)
+        st.upload(torch.from_numpy(np.ascontiguousarray(psi)).to(dt).pin_memory())
+        st.apply(plan, sync=True, jit=True, regbits=regbits)
+        out = st.copy_to_host().numpy().astype(np.complex128)
+        st.close()
+        plan.close()
+        assert max_abs(out, ref) <= TOL[precision], (method, k)

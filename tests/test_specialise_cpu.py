@@ -49,3 +49,20 @@ def test_source_layout_and_errors():
     with pytest.raises(N.SvError):
         plan.source(10 ** 6, "c64")                    # no such part
     plan.close()
+
+
+def test_register_bits_variants():
+    """SV_FLAG_REGBITS: 2^r amplitudes per thread in the specialised kernels
+    (r = 4 and 6 for complex64, 3 for complex128): the programs compile with
+    NVRTC, the CTA has 2^(t - r) threads, and out-of-range choices fail."""
+    N, api = _api()
+    n, g = synth.layered_28q(n=16, depth=6)
+    plan = api.Plan(g, n, "beam", 9)
+    for prec, r, t in (("c64", 4, 12), ("c64", 6, 12), ("c64", 4, 13), ("c128", 3, 11)):
+        src = plan.source(0, prec, tile=t, regbits=r)
+        assert f"__launch_bounds__({1 << (t - r)}," in src, (prec, r, t)
+        assert plan.specialise(prec, tile=t, load=False, regbits=r) > 0.0
+    assert plan.stats("c64", 12, regbits=4)["phases"] >= plan.stats("c64", 12)["phases"]
+    with pytest.raises(N.SvError):
+        plan.stats("c64", 10, regbits=6)            # 2^4 threads: less than a warp
+    plan.close()
