@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
     ap.add_argument("--serving-window", type=float, default=3.0,
                     help="seconds of the request stream's arrivals served in the serving section")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="only the serving section (what the benchmark runs in a child process), one JSON line")
     ap.add_argument("--serving-full", action="store_true",
                     help="serve the whole 20000-request stream (60 s of arrivals, then drain; minutes), "
                          "one JSON line, then exit")
@@ -323,6 +325,22 @@ def serving_section(window_s=3.0):
     sp["throughput_vs_gate_by_gate"] = round(sp["parts"]["circuits_per_s"] / sp["gatewise"]["circuits_per_s"], 2)
     sp["p99_vs_gate_by_gate"] = round(sp["gatewise"]["p99_s"] / sp["parts"]["p99_s"], 2)
     return out
+
+
+def serving_child(window_s):
+    """serving_section in a child process on the same GPU: the serving loop
+    runs many streams and host threads at once, and a device fault there
+    must not take the benchmark's own context (and its JSON line) down with
+    it."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--serving-only", "--serving-window", str(window_s)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    for line in reversed(r.stdout.strip().splitlines()):
+        if line.startswith("{"):
+            try:
+                return json.loads(line)["serving"]
+            except (ValueError, KeyError):
+                break
+    return {"error": f"serving child exited {r.returncode}: " + " | ".join(r.stderr.strip().splitlines()[-3:])}
 
 
 def serving_full():
@@ -642,7 +660,7 @@ def run_ours(a):
     if rank == 0 and not a.no_batch:
         batch = batch_section(a.batch_circuits)
     if rank == 0 and not a.no_serving:
-        serving = serving_section(a.serving_window)
+        serving = serving_child(a.serving_window)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
@@ -868,6 +886,10 @@ def main():
         partition_quality()
     elif a.serving_full:
         serving_full()
+    elif a.serving_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"serving": serving_section(a.serving_window)}), flush=True)
     elif a.impl == "reference" and a.oracle_report:
         oracle_report()
     elif a.impl == "reference":
