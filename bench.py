@@ -405,28 +405,36 @@ def _timed(st, plan, tc=False, jit=False, reps=2, regbits=0):
     return e0.elapsed_time(e1) / reps
 
 
-def grid_section(n, gates, st, peak):
+def grid_section(n, gates, st, peak, fp32_peak=None):
     """The paper's three builders at k in {8, 10, 12} on the complex64 state:
     passes, time per step and pass GB/s (fraction of the measured copy
     bandwidth) on the interpreter kernel and on the plan's specialised
-    kernels."""
+    kernels, and the FP32 flops the plan's program executes (sv_plan_flops)
+    per second against the measured FP32 FMA rate: the second bound, which
+    takes over as the gates per pass grow with k."""
     from paper_2205_06973_gb300 import api
     rows = []
     for method in ("nat", "dfs", "dagp"):
         for k in (8, 10, 12):
             plan = api.Plan(gates, n, method, k)
             passes = plan.stats("c64")["passes"]
-            row = {"method": method, "k": k, "passes": passes}
+            flops = plan.flops("c64")[0]
+            row = {"method": method, "k": k, "passes": passes, "executed_fp32_flops": flops}
             for name, jit in (("interpreter", False), ("specialised", True)):
                 if jit:
                     row["compile_s"] = round(plan.specialise("c64"), 2)
                 ms = _timed(st, plan, jit=jit)
                 gbs = passes * 2 * st.nbytes / (ms / 1e3) / 1e9
                 row[name] = {"ms": round(ms, 2), "GBs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+                if fp32_peak:
+                    fl = flops / (ms / 1e3)
+                    row[name]["fp32_tflops"] = round(fl / 1e12, 2)
+                    row[name]["fp32_frac"] = round(fl / fp32_peak, 4)
             plan.close()
             rows.append(row)
     return {"workload": "28-qubit layered circuit, complex64 state (2 GiB), gate-list parts",
-            "peak_GBs": peak, "rows": rows}
+            "peak_GBs": peak, "fp32_fma_peak_tflops": round(fp32_peak / 1e12, 2) if fp32_peak else None,
+            "rows": rows}
 
 
 def c128_section(n, gates, peak, fp64_peak):
@@ -650,7 +658,7 @@ def run_ours(a):
     grid = c128 = alu = ml = q33 = None
     if rank == 0 and not a.no_grid:
         alu = alu_peaks()
-        grid = grid_section(n, gates, st, peak)
+        grid = grid_section(n, gates, st, peak, alu["fp32"])
         c128 = c128_section(n, gates, peak, alu["fp64"])
         alu = {k: round(v / 1e12, 3) for k, v in alu.items()}
         ml = multilevel_section(peak)
@@ -660,6 +668,12 @@ def run_ours(a):
     if rank == 0 and not a.no_batch:
         batch = batch_section(a.batch_circuits)
     if rank == 0 and not a.no_serving:
+        # the child gets the device to itself: return the blocks this process
+        # cached for the sections above (the 64 GiB QFT state and others)
+        import gc
+        gc.collect()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
         serving = serving_child(a.serving_window)
 
     if rank == 0:

@@ -34,8 +34,11 @@ struct sv_batch {
     std::vector<uint64_t> off;           // first amplitude per circuit
     uint64_t total = 0;                  // amplitudes in all states
     std::vector<sv_plan *> plans;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // the caller's stream: graph launches, probabilities, frees
     bool own_stream = false;
+    cudaStream_t prep = nullptr;         // private: allocations, uploads and the graph capture, so that
+                                         // building a batch never enqueues on (or captures) a stream that
+                                         // another thread uses for earlier batches
     int warps = 8;                       // warps per CTA
     int chunk = 16;                      // tiles per queue item
     bool hold_last = false;              // testing: the last item waits for tiles that never complete
@@ -63,6 +66,7 @@ struct sv_batch {
 };
 
 static void drop_program(sv_batch *b) {
+    if (b->prep) cudaStreamSynchronize(b->prep);   // no upload into the program is still in flight
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
     b->gexec = nullptr;
@@ -94,31 +98,45 @@ sv_status sv_batch_create(uint32_t n_circuits, const int *n_qubits, void *stream
     b->plans.assign(n_circuits, nullptr);
     b->h_norms.assign(n_circuits, 0.0);
     b->stream = reinterpret_cast<cudaStream_t>(stream);
-    if (!b->stream) {   // graph capture needs a non-legacy stream
+    if (!b->stream) {   // graph launches need a non-legacy stream
         BCUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
         b->own_stream = true;
     }
-    cudaStream_t st = b->stream;
+    {
+        cudaError_t pe = cudaStreamCreateWithFlags(&b->prep, cudaStreamNonBlocking);
+        if (pe != cudaSuccess) {
+            if (b->own_stream) cudaStreamDestroy(b->stream);
+            return bfail(SV_ERR_CUDA, std::string("batch stream: ") + cudaGetErrorString(pe));
+        }
+    }
+    // allocated and initialised on the private stream, which is synchronised
+    // before the batch is returned: the buffers are ready for any stream
+    cudaStream_t st = b->prep;
     cudaError_t e = dev_alloc(reinterpret_cast<void **>(&b->sv), sizeof(float2) * b->total, st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_off), sizeof(uint64_t) * n_circuits, st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_nq), sizeof(uint32_t) * n_circuits, st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_done), sizeof(uint32_t) * (n_circuits + 2), st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_err), sizeof(int) * DENSE_BATCH_ERR_WORDS, st);
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&b->d_norms), sizeof(double) * n_circuits, st);
+    std::vector<uint32_t> nq32(b->nq.begin(), b->nq.end());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_off, b->off.data(), sizeof(uint64_t) * n_circuits, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_nq, nq32.data(), sizeof(uint32_t) * n_circuits, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int) * DENSE_BATCH_ERR_WORDS, st);
+    if (e == cudaSuccess) e = launch_batch_reset(b->sv, b->d_off, n_circuits, b->total, st);
+    cudaError_t se = cudaStreamSynchronize(st);   // also: the host vectors above go out of scope
+    if (e == cudaSuccess) e = se;
     if (e != cudaSuccess) {
         cudaGetLastError();
         dev_free(b->sv, st); dev_free(b->d_off, st); dev_free(b->d_nq, st); dev_free(b->d_done, st);
         dev_free(b->d_err, st); dev_free(b->d_norms, st);
         cudaStreamSynchronize(st);
+        cudaStreamDestroy(b->prep);
         if (b->own_stream) cudaStreamDestroy(b->stream);
-        return bfail(SV_ERR_OOM, std::string("batch allocation: ") + cudaGetErrorString(e));
+        return bfail(e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA,
+                     std::string("batch allocation: ") + cudaGetErrorString(e));
     }
-    std::vector<uint32_t> nq32(b->nq.begin(), b->nq.end());
-    BCUDA(cudaMemcpyAsync(b->d_off, b->off.data(), sizeof(uint64_t) * n_circuits, cudaMemcpyHostToDevice, b->stream));
-    BCUDA(cudaMemcpyAsync(b->d_nq, nq32.data(), sizeof(uint32_t) * n_circuits, cudaMemcpyHostToDevice, b->stream));
-    BCUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int) * DENSE_BATCH_ERR_WORDS, b->stream));
-    BCUDA(launch_batch_reset(b->sv, b->d_off, n_circuits, b->total, b->stream));
-    BCUDA(cudaStreamSynchronize(b->stream));   // the host vectors above go out of scope
     *out = b.release();
     return SV_OK;
 }
@@ -225,13 +243,12 @@ static sv_status build_program(sv_batch *b) {
     dense_layout(b, D);
     char *dd = nullptr;
     if (D.n_circ) {
-        cudaError_t e = dev_alloc(reinterpret_cast<void **>(&dd), D.s_items + D.s_parts + D.s_img + D.s_dn, b->stream);
+        cudaError_t e = dev_alloc(reinterpret_cast<void **>(&dd), D.s_items + D.s_parts + D.s_img + D.s_dn, b->prep);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return bfail(SV_ERR_OOM, std::string("dense batch program: ") + cudaGetErrorString(e));
         }
         b->d_dprog = dd;
-        BCUDA(cudaStreamSynchronize(b->stream));   // the allocation exists before the workers copy into it
     }
     int dev = 0;
     BCUDA(cudaGetDevice(&dev));
@@ -274,8 +291,10 @@ static sv_status build_program(sv_batch *b) {
                 std::memcpy(P.col_q, L.col_q, DENSE_COLS);
                 P.n = (uint8_t)b->nq[c];
             }
-            cudaError_t e = cudaMemcpy(dd + D.s_items + D.s_parts + (size_t)D.base[c] * DENSE_A_BYTES, pr.a_img.data(),
-                                       (size_t)D.npass[c] * DENSE_A_BYTES, cudaMemcpyHostToDevice);
+            // a pageable source is staged before the call returns: pr may go
+            cudaError_t e = cudaMemcpyAsync(dd + D.s_items + D.s_parts + (size_t)D.base[c] * DENSE_A_BYTES,
+                                            pr.a_img.data(), (size_t)D.npass[c] * DENSE_A_BYTES,
+                                            cudaMemcpyHostToDevice, b->prep);
             if (e != cudaSuccess) errs[c] = std::string("R image upload: ") + cudaGetErrorString(e);
         }
     };
@@ -286,10 +305,15 @@ static sv_status build_program(sv_batch *b) {
     work();
     for (auto &t : th) t.join();
     for (uint32_t c = 0; c < b->n; c++)
-        if (!errs[c].empty()) return bfail(SV_ERR_PARTITION, errs[c]);
+        if (!errs[c].empty()) {
+            cudaStreamSynchronize(b->prep);   // no upload into the program is left in flight when it is freed
+            return bfail(SV_ERR_PARTITION, errs[c]);
+        }
     if (D.n_circ) {
-        BCUDA(cudaMemcpy(dd, D.items.data(), D.items.size() * sizeof(DenseBatchItem), cudaMemcpyHostToDevice));
-        BCUDA(cudaMemcpy(dd + D.s_items, dparts.data(), dparts.size() * sizeof(DenseBatchPart), cudaMemcpyHostToDevice));
+        BCUDA(cudaMemcpyAsync(dd, D.items.data(), D.items.size() * sizeof(DenseBatchItem), cudaMemcpyHostToDevice,
+                              b->prep));
+        BCUDA(cudaMemcpyAsync(dd + D.s_items, dparts.data(), dparts.size() * sizeof(DenseBatchPart),
+                              cudaMemcpyHostToDevice, b->prep));
         b->n_dense_items = (uint32_t)D.items.size();
         b->n_dense_parts = D.n_parts;
         b->n_dense_circ = D.n_circ;
@@ -349,7 +373,7 @@ static sv_status build_program(sv_batch *b) {
     const size_t s_ph = al(phases.size() * sizeof(Phase)), s_op = al(ops.size() * sizeof(Op));
     const size_t s_cf = al(std::max<size_t>(1, coefs.size()) * sizeof(float));
     char *d = nullptr;
-    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&d), s_items + s_parts + s_ph + s_op + s_cf, b->stream);
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&d), s_items + s_parts + s_ph + s_op + s_cf, b->prep);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return bfail(SV_ERR_OOM, std::string("batch program: ") + cudaGetErrorString(e));
@@ -361,8 +385,10 @@ static sv_status build_program(sv_batch *b) {
     std::memcpy(host.data() + s_items + s_parts, phases.data(), phases.size() * sizeof(Phase));
     std::memcpy(host.data() + s_items + s_parts + s_ph, ops.data(), ops.size() * sizeof(Op));
     std::memcpy(host.data() + s_items + s_parts + s_ph + s_op, coefs.data(), coefs.size() * sizeof(float));
-    BCUDA(cudaMemcpyAsync(d, host.data(), host.size(), cudaMemcpyHostToDevice, b->stream));
-    BCUDA(cudaStreamSynchronize(b->stream));   // the host image goes out of scope
+    BCUDA(cudaMemcpyAsync(d, host.data(), host.size(), cudaMemcpyHostToDevice, b->prep));
+    // every upload (gate lists, dense items, parts and R images) is complete
+    // before the graph can be launched on any stream
+    BCUDA(cudaStreamSynchronize(b->prep));
     BatchLaunch &B = b->launch;
     B.svbase = b->sv;
     B.items = reinterpret_cast<const BatchItem *>(d);
@@ -382,20 +408,22 @@ static sv_status build_program(sv_batch *b) {
     // one graph: zero the tile counters, the tickets and the dense passes'
     // norm slots, then the persistent launches (dense circuits, gate lists)
     const size_t ds_items = D.s_items, ds_parts = D.s_parts, ds_img = D.s_img;
-    BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaMemsetAsync(b->d_done, 0, sizeof(uint32_t) * (b->n + 2), b->stream);
+    // captured on the private stream (nothing else is ever enqueued there),
+    // launched on the caller's stream
+    BCUDA(cudaStreamBeginCapture(b->prep, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaMemsetAsync(b->d_done, 0, sizeof(uint32_t) * (b->n + 2), b->prep);
     if (ce == cudaSuccess && b->n_dense_items) {
         double *dn = reinterpret_cast<double *>(dd + ds_items + ds_parts + ds_img);
-        ce = cudaMemsetAsync(dn, 0, sizeof(double) * b->n_dense_parts, b->stream);
+        ce = cudaMemsetAsync(dn, 0, sizeof(double) * b->n_dense_parts, b->prep);
         if (ce == cudaSuccess)
             ce = launch_dense6_batch(b->sv, reinterpret_cast<const DenseBatchPart *>(dd + ds_items),
                                      reinterpret_cast<const DenseBatchItem *>(dd), b->n_dense_items,
                                      dd + ds_items + ds_parts, b->d_done, b->d_done + b->n + 1, b->d_err, dn,
-                                     b->stream);
+                                     b->prep);
     }
-    if (ce == cudaSuccess && B.n_items) ce = launch_batch(B, b->warps, n_ctas, b->stream);
+    if (ce == cudaSuccess && B.n_items) ce = launch_batch(B, b->warps, n_ctas, b->prep);
     cudaGraph_t g = nullptr;
-    cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+    cudaError_t ee = cudaStreamEndCapture(b->prep, &g);
     if (ce != cudaSuccess || ee != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return bfail(SV_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee));
@@ -539,6 +567,7 @@ sv_status sv_batch_destroy(sv_batch *b) {
         cudaStreamSynchronize(b->stream);   // the frees complete before the stream goes
         cudaStreamDestroy(b->stream);
     }
+    cudaStreamDestroy(b->prep);             // idle: drop_program synchronised it
     delete b;
     if (e != cudaSuccess) return bfail(SV_ERR_CUDA, std::string("pending batch work failed: ") + cudaGetErrorString(e));
     return SV_OK;

@@ -60,6 +60,7 @@ import time
 import numpy as np
 import torch
 
+from . import _native as N
 from . import autotune
 from .api import Plan, State
 from .batch import Batch
@@ -168,7 +169,9 @@ class Server:
     def _new_state(n, stream):
         try:
             return State(n, "c64", stream=stream)
-        except torch.cuda.OutOfMemoryError:
+        except (torch.cuda.OutOfMemoryError, N.SvError) as e:
+            if isinstance(e, N.SvError) and e.status != N.SV_ERR_OOM:
+                raise
             # blocks of other sizes cached by torch's allocator: return them and retry
             torch.cuda.synchronize()
             torch.cuda.empty_cache()
