@@ -430,6 +430,16 @@ def grid_section(n, gates, st, peak, fp32_peak=None):
                     fl = flops / (ms / 1e3)
                     row[name]["fp32_tflops"] = round(fl / 1e12, 2)
                     row[name]["fp32_frac"] = round(fl / fp32_peak, 4)
+            if k == 12:
+                # a 2^12 tile holds only the part's own qubits, so a part
+                # without the lowest qubits reads short runs; a 2^13 tile
+                # adds the lowest free qubit to every run
+                st.set_tile(13)
+                plan.specialise("c64", 13)
+                ms = _timed(st, plan, jit=True)
+                st.set_tile(0)
+                gbs = passes * 2 * st.nbytes / (ms / 1e3) / 1e9
+                row["specialised_tile13"] = {"ms": round(ms, 2), "GBs": round(gbs, 1), "frac": round(gbs / peak, 4)}
             plan.close()
             rows.append(row)
     return {"workload": "28-qubit layered circuit, complex64 state (2 GiB), gate-list parts",

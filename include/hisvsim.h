@@ -154,10 +154,14 @@ sv_status sv_device_ptr(sv_state *s, void **ptr, size_t *bytes);
  * bounded device wait that gave up (tensor-core path) returns SV_ERR_TIMEOUT. */
 sv_status sv_sync(sv_state *s);
 /* CTA tile size used by the part kernels for this state: tile_qubits t in
- * [10, 13] for SV_C64 and [10, 12] for SV_C128 (2^t amplitudes per CTA); 0
- * restores the default (13 / 12). The tile always contains the part's qubits
- * and is padded with the lowest remaining qubits (Sec. IV-B, multi-level:
- * parts smaller than the limit take extra qubits for spatial locality). */
+ * [10, 13] for SV_C64 and [10, 12] for SV_C128 and SV_C128DF (2^t
+ * amplitudes per CTA); 0 restores the default: 12 (complex64) / 11 (the
+ * complex128 forms), grown to the plan's largest part plus the lowest free
+ * qubits that make each contiguous run of the tile fill a 32-byte sector
+ * (two for complex64, one for the complex128 forms), within the limits
+ * above. The tile always contains the part's qubits and is padded with the
+ * lowest remaining qubits (Sec. IV-B, multi-level: parts smaller than the
+ * limit take extra qubits for spatial locality). */
 sv_status sv_set_tile(sv_state *s, int tile_qubits);
 
 /* ----------------------------------------------------------------- plan ---

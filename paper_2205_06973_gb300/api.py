@@ -155,6 +155,10 @@ class State:
         N.check(N.lib.sv_export_c128(self.h, ctypes.c_void_p(out.data_ptr()), out.numel() * 16))
         return out
 
+    def set_tile(self, tile_qubits):
+        """CTA tile of the part kernels for this state (sv_set_tile; 0 = default)."""
+        N.check(N.lib.sv_set_tile(self.h, tile_qubits))
+
     def set_basis(self, x):
         N.check(N.lib.sv_set_basis(self.h, x))
 
