@@ -62,6 +62,8 @@ def parse():
                     help="seconds of the request stream's arrivals served in the serving section")
     ap.add_argument("--serving-only", action="store_true",
                     help="only the serving section (what the benchmark runs in a child process), one JSON line")
+    ap.add_argument("--serving-jit-large", action="store_true",
+                    help="with --serving-full: specialised kernels for requests of >= 29 qubits")
     ap.add_argument("--serving-full", action="store_true",
                     help="serve the whole 20000-request stream (60 s of arrivals, then drain; minutes), "
                          "one JSON line, then exit")
@@ -343,9 +345,11 @@ def serving_child(window_s):
     return {"error": f"serving child exited {r.returncode}: " + " | ".join(r.stderr.strip().splitlines()[-3:])}
 
 
-def serving_full():
+def serving_full(jit_large=False):
     """The whole serving stream (20000 requests over 60 s, 10-33 qubits,
-    170 GB budget), part-fused, until drained. One JSON line."""
+    170 GB budget), part-fused, until drained. One JSON line. jit_large:
+    requests of >= 29 qubits may run their plan's specialised kernels
+    (compiled on the large-request planner threads)."""
     import torch
     from paper_2205_06973_gb300.serving import Server
     torch.cuda.set_device(0)
@@ -354,14 +358,14 @@ def serving_full():
     gen_s = time.perf_counter() - t0
     clk = ClockSampler(0)
     clk.start()
-    srv = Server(budget_bytes=170e9)
+    srv = Server(budget_bytes=170e9, jit_large=jit_large)
     res, st = srv.run(reqs)
     srv.close()
     clocks = clk.stop()
     print(json.dumps({"serving_full": {"workload": "the 20000-request stream (seed 5): Poisson arrivals over 60 s, "
                                                    "10-33 qubits (80 % <= 20), layered / QFT / parameterised, "
                                                    "complex64, admission by 8 * 2^n bytes against 170 GB",
-                                       "generate_s": round(gen_s, 1), "clocks": clocks,
+                                       "jit_large": jit_large, "generate_s": round(gen_s, 1), "clocks": clocks,
                                        "norm_min": min(r.norm for r in res), "norm_max": max(r.norm for r in res),
                                        **_serving_stats(st)}}), flush=True)
 
@@ -431,15 +435,16 @@ def grid_section(n, gates, st, peak, fp32_peak=None):
                     row[name]["fp32_tflops"] = round(fl / 1e12, 2)
                     row[name]["fp32_frac"] = round(fl / fp32_peak, 4)
             if k == 12:
-                # a 2^12 tile holds only the part's own qubits, so a part
-                # without the lowest qubits reads short runs; a 2^13 tile
-                # adds the lowest free qubit to every run
-                st.set_tile(13)
-                plan.specialise("c64", 13)
+                # the default tile for k = 12 is 2^13 (the part plus the
+                # lowest free qubit); a 2^12 tile holds only the part's own
+                # qubits, so a part without the lowest qubits reads runs of
+                # one amplitude
+                st.set_tile(12)
+                plan.specialise("c64", 12)
                 ms = _timed(st, plan, jit=True)
                 st.set_tile(0)
                 gbs = passes * 2 * st.nbytes / (ms / 1e3) / 1e9
-                row["specialised_tile13"] = {"ms": round(ms, 2), "GBs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+                row["specialised_tile12"] = {"ms": round(ms, 2), "GBs": round(gbs, 1), "frac": round(gbs / peak, 4)}
             plan.close()
             rows.append(row)
     return {"workload": "28-qubit layered circuit, complex64 state (2 GiB), gate-list parts",
@@ -611,27 +616,39 @@ def run_ours(a):
     if not a.no_e2e:
         # two states on two streams: a step's upload and download overlap the
         # other state's passes (every step still copies its input in and its
-        # result out through the C ABI)
+        # result out through the C ABI). Each step's passes wait for the
+        # previous step's passes (an event), so the two states take turns on
+        # the SMs instead of sharing them: while one runs its passes, the
+        # other's download and next upload cross the host link (one copy at
+        # a time), and the copies leave the compute timeline
         sts = [api.State(n, "c64", stream=torch.cuda.Stream(), tile=choice.get("tile", 0)) for _ in range(2)]
         host_in = torch.zeros(1 << n, dtype=torch.complex64).pin_memory()   # read by both states
         host_in[0] = 1.0
         host_out = [torch.empty(1 << n, dtype=torch.complex64).pin_memory() for _ in range(2)]
+        def step(i, last):
+            x = sts[i % 2]
+            if i >= 2:
+                x.sync()          # its step i-2 result has reached host memory
+            x.upload(host_in)
+            if last is not None:
+                x.stream.wait_event(last)
+            x.apply(plan, tc=tc, jit=jit, regbits=regbits)
+            done = torch.cuda.Event()
+            done.record(x.stream)
+            x.download(host_out[i % 2])
+            return done
+
+        last = None
         for i in range(2):
-            sts[i].upload(host_in)
-            sts[i].apply(plan, tc=tc, jit=jit, regbits=regbits)
-            sts[i].download(host_out[i])
+            last = step(i, last)
         for x in sts:
             x.sync()
         reps = 10
         barrier(ws)
         t0 = time.perf_counter()
+        last = None
         for i in range(reps):
-            x = sts[i % 2]
-            if i >= 2:
-                x.sync()          # its step i-2 result has reached host memory
-            x.upload(host_in)
-            x.apply(plan, tc=tc, jit=jit, regbits=regbits)
-            x.download(host_out[i % 2])
+            last = step(i, last)
         for x in sts:
             x.sync()
         dt = (time.perf_counter() - t0) / reps
@@ -642,7 +659,7 @@ def run_ours(a):
                "h2d_bytes_per_step": st.nbytes, "d2h_bytes_per_step": st.nbytes,
                "ms_per_step": round(dt * 1e3, 3), "steps": reps,
                "api": "sv_upload + sv_apply_parts + sv_download (pinned host buffers), two states on two "
-                      "streams so that one step's copies overlap the other's passes"}
+                      "streams taking turns on the SMs, so that one step's copies overlap the other's passes"}
 
     compare = None
     if not a.no_compare:
@@ -909,7 +926,7 @@ def main():
     if a.partition_quality:
         partition_quality()
     elif a.serving_full:
-        serving_full()
+        serving_full(a.serving_jit_large)
     elif a.serving_only:
         import torch
         torch.cuda.set_device(0)

@@ -260,3 +260,24 @@ def test_multilevel_errors(native):
         p.stats("c64")
     assert e.value.status == native.SV_ERR_PARTITION
     p.close()
+
+
+@pytest.mark.parametrize("precision,k,expect", [("c64", 8, 12), ("c64", 10, 12), ("c64", 11, 13), ("c64", 12, 13),
+                                                ("c128", 8, 11), ("c128", 10, 11), ("c128", 11, 12),
+                                                ("c128df", 12, 12)])
+def test_default_tile_fills_sectors(native, precision, k, expect):
+    """Default tile: the largest part plus the lowest free qubits that make a
+    contiguous run of the tile fill a 32-byte sector (two for complex64, one
+    for the 16-byte forms), at least 2^12 / 2^11 and at most 2^13 / 2^12.
+    The generated source of a part names its tile size, so the default's
+    source equals the source for the expected tile and no other."""
+    n, g = synth.layered_28q(n=18, depth=8)
+    p = _plan(native, g, n, "dfs", k)
+    assert p.stats(precision)["passes"] > 0
+    src = p.source(0, precision)
+    assert src == p.source(0, precision, expect)
+    tmax = 13 if precision == "c64" else 12
+    for t in range(max(k, 10), tmax + 1):
+        if t != expect:
+            assert src != p.source(0, precision, t)
+    p.close()
