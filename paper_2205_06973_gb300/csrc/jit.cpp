@@ -195,18 +195,83 @@ std::string jit_part_source(const Program &prog, size_t pi, bool df) {
       << "        (void)tpr; (void)tpi;\n";
     const std::vector<double> &cf = prog.coefs;
     auto L_ = [&](uint32_t at) { return lit(cf[at], mode); };
+    auto L_lit = [&](double v) { return lit(v, mode); };
+    // Per-thread phases (OP_TD / OP_TP2) multiply every amplitude a thread
+    // holds by one scalar, which commutes with every op of the phase. Where a
+    // phase has a merged diagonal (OP_DIAG), that scalar (and, in the last
+    // phase, the part factor) is multiplied into the diagonal's coefficients
+    // at run time, once per distinct coefficient, in place of a separate
+    // complex multiply of every amplitude (OP_TAPPLY or the store factor).
+    bool store_folded = false;
     for (uint32_t p = 0; p < nph; p++) {
         const Phase &ph = prog.phases[L.phase_begin + p];
         if (p > 0)
             o << "        __syncthreads();\n#pragma unroll\n        for (int i = 0; i < NR; i++) cur[sp" << p - 1
               << " ^ SR" << p - 1 << "[i]] = a[i];\n        __syncthreads();\n";
         o << "#pragma unroll\n        for (int i = 0; i < NR; i++) a[i] = cur[sp" << p << " ^ SR" << p << "[i]];\n";
+        const bool last = p + 1 == nph;
+        int first_diag = -1;
+        bool tapply = false;
         for (uint32_t k = 0; k < ph.op_count; k++) {
+            const uint8_t kd = prog.ops[ph.op_begin + k].kind;
+            if (kd == OP_DIAG && first_diag < 0) first_diag = (int)k;
+            if (kd == OP_TAPPLY) tapply = true;
+        }
+        const bool fold_store = last && (L.flags & PL_STORE_FACTOR) && first_diag >= 0;
+        const bool fold = first_diag >= 0 && (tapply || fold_store);
+        if (fold) store_folded = fold_store;
+        // with folding, the per-thread phase is complete before the ops run
+        std::vector<uint32_t> order;
+        if (fold)
+            for (uint32_t k = 0; k < ph.op_count; k++) {
+                const uint8_t kd = prog.ops[ph.op_begin + k].kind;
+                if (kd == OP_TD || kd == OP_TP2) order.push_back(k);
+            }
+        for (uint32_t k = 0; k < ph.op_count; k++) {
+            const uint8_t kd = prog.ops[ph.op_begin + k].kind;
+            if (fold && (kd == OP_TD || kd == OP_TP2 || kd == OP_TAPPLY)) continue;
+            order.push_back(k);
+        }
+        for (uint32_t k : order) {
             const Op &op = prog.ops[ph.op_begin + k];
             const uint32_t c = op.coef;
             const std::string tb = "((tid >> " + std::to_string(op.tb) + ") & 1)";
             const int A = op.a, B = op.b;
             o << "        ";
+            if (fold && (int)k == first_diag) {
+                // coefficient q = d_q x g x (per-thread phase), g the part
+                // factor in the last phase (else 1); one complex product per
+                // distinct d_q x g
+                double gr = 1.0, gi = 0.0;
+                if (fold_store) { gr = L.gr; gi = L.gi; }
+                std::vector<std::pair<double, double>> vals;
+                std::vector<int> which(NRr);
+                for (int q = 0; q < NRr; q++) {
+                    const double dr = cf[c + 2 * q], di = cf[c + 2 * q + 1];
+                    const double er = dr * gr - di * gi, ei = dr * gi + di * gr;
+                    int w = -1;
+                    for (size_t v = 0; v < vals.size(); v++)
+                        if (vals[v].first == er && vals[v].second == ei) w = (int)v;
+                    if (w < 0) { w = (int)vals.size(); vals.push_back({er, ei}); }
+                    which[q] = w;
+                }
+                o << "{ ";
+                for (size_t v = 0; v < vals.size(); v++) {
+                    const double er = vals[v].first, ei = vals[v].second;
+                    const std::string nm = "e" + std::to_string(v);
+                    if (er == 1.0 && ei == 0.0) o << "const Real " << nm << "r = tpr, " << nm << "i = tpi; ";
+                    else if (er == -1.0 && ei == 0.0) o << "const Real " << nm << "r = -tpr, " << nm << "i = -tpi; ";
+                    else if (er == 0.0 && ei == 1.0) o << "const Real " << nm << "r = -tpi, " << nm << "i = tpr; ";
+                    else if (er == 0.0 && ei == -1.0) o << "const Real " << nm << "r = tpi, " << nm << "i = -tpr; ";
+                    else
+                        o << "const Real " << nm << "r = " << L_lit(er) << " * tpr - " << L_lit(ei) << " * tpi, " << nm
+                          << "i = " << L_lit(er) << " * tpi + " << L_lit(ei) << " * tpr; ";
+                }
+                for (int q = 0; q < NRr; q++)
+                    o << "cmul_in(a[" << q << "], e" << which[q] << "r, e" << which[q] << "i); ";
+                o << "tpr = 1; tpi = 0; }\n";
+                continue;
+            }
             switch (op.kind) {
             case OP_H:
                 if (mode == 0) o << "op_h2<" << A << ">(a);";   // packed f32x2
@@ -249,7 +314,8 @@ std::string jit_part_source(const Program &prog, size_t pi, bool df) {
                   << L_(c + 1) << " : (Real)0); }";
                 break;
             case OP_CZT:
-                o << "{ const bool c_ = " << tb << " != 0; op_p<NR, " << A << ">(a, c_ ? (Real)-1 : (Real)1, (Real)0); }";
+                // a sign, not a complex product
+                o << "op_sgn<" << A << ">(a, " << tb << " != 0);";
                 break;
             case OP_TD:
                 o << "{ const bool c_ = " << tb << " != 0; tmul(tpr, tpi, c_ ? " << L_(c + 2) << " : " << L_(c) << ", c_ ? "
@@ -280,7 +346,7 @@ std::string jit_part_source(const Program &prog, size_t pi, bool df) {
             o << "\n";
         }
     }
-    if (L.flags & PL_STORE_FACTOR) {
+    if ((L.flags & PL_STORE_FACTOR) && !store_folded) {
         o << "        { const Real gr = " << lit(L.gr, mode) << ", gi = " << lit(L.gi, mode) << ";\n"
           << "          const Real fr = gr * tpr - gi * tpi, fi = gr * tpi + gi * tpr;\n"
           << "#pragma unroll\n          for (int i = 0; i < NR; i++) cmul_in(a[i], fr, fi); }\n";

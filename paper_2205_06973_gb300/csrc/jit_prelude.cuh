@@ -205,6 +205,37 @@ __device__ __forceinline__ void op_cxt(C (&a)[NR], bool ctl) {
         a[j] = ctl ? x : y;
     }
 }
+// The amplitudes with register bit B set are negated where neg holds (a
+// controlled Z whose control is a thread bit): one packed multiply by (s, s)
+// per amplitude for complex64, a multiply of each part otherwise.
+template <int B>
+__device__ __forceinline__ void op_sgn(C (&a)[NR], bool neg) {
+#if HISV_DF
+    const float s = neg ? -1.f : 1.f;
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+        if (i & (1 << B)) {
+            a[i].x.hi *= s; a[i].x.lo *= s;
+            a[i].y.hi *= s; a[i].y.lo *= s;
+        }
+#elif HISV_FP64
+    const double s = neg ? -1.0 : 1.0;
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+        if (i & (1 << B)) { a[i].x *= s; a[i].y *= s; }
+#else
+    const float s = neg ? -1.f : 1.f;
+    unsigned long long ss;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(ss) : "f"(s));
+#pragma unroll
+    for (int i = 0; i < NR; i++)
+        if (i & (1 << B)) {
+            unsigned long long d;
+            asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a[i])), "l"(ss));
+            a[i] = upk(d);
+        }
+#endif
+}
 // Per-thread phase *= (dr, di).
 __device__ __forceinline__ void tmul(Real &tpr, Real &tpi, Real dr, Real di) {
     const Real x = tpr, y = tpi;
