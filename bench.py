@@ -46,7 +46,8 @@ def parse():
                     help="part builder with --k (the reference arm's oracle has nat, dfs, dagp; beam maps to dagp)")
     ap.add_argument("--k", type=int, default=0, help="part qubit limit (0: autotuned default)")
     ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--tc", type=int, default=0, help="with --k: run parts of <= 6 qubits on the tensor cores")
+    ap.add_argument("--tc", type=int, default=0, help="with --k: run parts of <= 6 qubits on the tensor cores "
+                    "(2: two consecutive such parts per pass where they fit one 13-qubit tile)")
     ap.add_argument("--jit", type=int, default=0, help="with --k: gate-list parts on the plan's specialised kernels")
     ap.add_argument("--regbits", type=int, default=0, help="with --jit: register bits per thread (0 = default)")
     ap.add_argument("--no-grid", action="store_true", help="skip the builder x k grid and the complex128 line")
@@ -87,6 +88,7 @@ def peaks():
 
 KERNEL_SOURCES = {
     "k_dense6": ("dense.cu", "dense.hpp", "dense_common.cuh", "planner.cpp"),
+    "k_dense6_pair": ("dense_pair.cu", "dense.hpp", "dense_common.cuh", "planner.cpp"),
     "k_part": ("kernels.cu", "ops.cuh", "ops_core.cuh", "program.hpp", "planner.cpp"),
     "hisv_part": ("jit.cpp", "jit_prelude.cuh", "ops_core.cuh", "program.hpp", "planner.cpp"),
 }
@@ -530,7 +532,8 @@ def qft33_section(peak):
     n, g, x = synth.qft_basis(33)
     st = api.State(n, "c64")
     rows = []
-    for m, k, tc, jit in (("beam", 6, True, False), ("beam", 10, False, True), ("beam", 12, False, True)):
+    for m, k, tc, jit in (("beam", 6, True, False), ("beam", 6, 2, False), ("beam", 10, False, True),
+                          ("beam", 12, False, True)):
         plan = api.Plan(g, n, m, k, dfs_trials=64 if k <= 6 else 16)
         stt = plan.stats("c64", tc=tc)
         cs = plan.specialise("c64", tc=tc) if jit else 0.0
@@ -560,12 +563,12 @@ def run_ours(a):
     n, gates = synth.layered_28q(n=a.n)
     st = api.State(n, "c64", tile=a.tile)
     if a.k:
-        choice = {"method": a.method, "k": a.k, "tc": bool(a.tc), "tile": a.tile, "jit": bool(a.jit),
+        choice = {"method": a.method, "k": a.k, "tc": int(a.tc), "tile": a.tile, "jit": bool(a.jit),
                   "regbits": a.regbits, "trials": []}
     else:
         from paper_2205_06973_gb300 import autotune
         choice = autotune.tune_state(f"layered{n}", n, gates, "c64", state=st, use_cache=False)
-    k, tc, method = choice["k"], bool(choice["tc"]), choice["method"]
+    k, tc, method = choice["k"], int(choice["tc"]), choice["method"]   # tc: 0, 1 dense parts, 2 paired
     jit = bool(choice.get("jit"))
     regbits = int(choice.get("regbits") or 0)
     if choice.get("tile"):
@@ -604,8 +607,9 @@ def run_ours(a):
     launch_ms = ms / passes
     peak, peak_kind = peaks()
     achieved = bytes_per_pass / (launch_ms / 1e3) / 1e9
-    kernel = "k_dense6" if (tc and stats["dense"] * 2 >= passes) else ("hisv_part" if jit else "k_part")
-    wkey = (f"layered{n}_{method}_k{k}_c64_{'tc' if tc else 't' + str(choice.get('tile') or 'auto')}"
+    kernel = (("k_dense6_pair" if tc == 2 else "k_dense6") if (tc and stats["dense"] * 2 >= passes)
+              else ("hisv_part" if jit else "k_part"))
+    wkey = (f"layered{n}_{method}_k{k}_c64_{('tc2' if tc == 2 else 'tc') if tc else 't' + str(choice.get('tile') or 'auto')}"
             f"{'_jit' if jit else ''}{'_r' + str(regbits) if regbits else ''}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,

@@ -97,6 +97,11 @@ typedef struct sv_plan sv_plan;
 #define SV_FLAG_TC_DENSE 0x4u   /* complex64, n >= 13: parts of at most 6 qubits run as one fused
                                    64x64 unitary on the tensor cores (split BF16, FP32
                                    accumulation); other parts keep the gate-list kernel */
+#define SV_FLAG_TC_PAIRS 0x10u  /* with SV_FLAG_TC_DENSE: two consecutive parts of at most 6
+                                   qubits run in one pass where their qubits and qubits 0, 1
+                                   fit a 13-qubit tile (the tile is read and written once,
+                                   both unitaries applied on chip: multi-level partitioning,
+                                   Sec. IV-B); the state must be 16-byte aligned */
 /* Register bits per thread of the gate-list part kernels (amplitudes per
  * thread = 2^r, the register level of the tile): r in [3, 6] with
  * SV_FLAG_SPECIALISE (the tile must keep at least 2^5 threads, t - r >= 5);

@@ -22,6 +22,15 @@ SV_FLAG_GATEWISE = 0x1
 SV_FLAG_SYNC = 0x2
 SV_FLAG_TC_DENSE = 0x4
 SV_FLAG_SPECIALISE = 0x8
+SV_FLAG_TC_PAIRS = 0x10
+
+
+def tc_flags(tc):
+    """Tensor-core flags for tc: False/0 none, True/1 dense parts, 2 dense
+    parts with two per pass where they fit one tile."""
+    if not tc:
+        return 0
+    return SV_FLAG_TC_DENSE | (SV_FLAG_TC_PAIRS if tc == 2 else 0)
 
 
 def SV_FLAG_REGBITS(r):

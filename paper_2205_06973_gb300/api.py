@@ -51,14 +51,14 @@ class Plan:
     def stats(self, precision="c64", tile=0, tc=False, regbits=0):
         a, b, c, d = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
         N.check(N.lib.sv_plan_stats(self.h, N.PRECISIONS[precision], tile,
-                                    (N.SV_FLAG_TC_DENSE if tc else 0) | N.SV_FLAG_REGBITS(regbits),
+                                    N.tc_flags(tc) | N.SV_FLAG_REGBITS(regbits),
                                     ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
         return {"passes": a.value, "phases": b.value, "ops": c.value, "dense": d.value}
 
     def flops(self, precision="c64", tile=0, tc=False, gatewise=False):
         """(CUDA-core flops, tensor-core flops) of one apply (sv_plan_flops)."""
         a, b = ctypes.c_double(), ctypes.c_double()
-        flags = (N.SV_FLAG_TC_DENSE if tc else 0) | (N.SV_FLAG_GATEWISE if gatewise else 0)
+        flags = N.tc_flags(tc) | (N.SV_FLAG_GATEWISE if gatewise else 0)
         N.check(N.lib.sv_plan_flops(self.h, N.PRECISIONS[precision], tile, flags,
                                     ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
@@ -70,7 +70,7 @@ class Plan:
         compile time in seconds."""
         s = ctypes.c_double()
         N.check(N.lib.sv_plan_specialise(self.h, N.PRECISIONS[precision], tile,
-                                         (N.SV_FLAG_TC_DENSE if tc else 0) | N.SV_FLAG_REGBITS(regbits),
+                                         N.tc_flags(tc) | N.SV_FLAG_REGBITS(regbits),
                                          1 if load else 0, ctypes.byref(s)))
         return s.value
 
@@ -78,7 +78,7 @@ class Plan:
         """Generated CUDA source of gate-list part ``part``."""
         n = ctypes.c_size_t()
         args = (self.h, N.PRECISIONS[precision], tile,
-                (N.SV_FLAG_TC_DENSE if tc else 0) | N.SV_FLAG_REGBITS(regbits), part)
+                N.tc_flags(tc) | N.SV_FLAG_REGBITS(regbits), part)
         N.check(N.lib.sv_plan_source(*args, None, 0, ctypes.byref(n)))
         buf = ctypes.create_string_buffer(n.value + 1)
         N.check(N.lib.sv_plan_source(*args, buf, n.value + 1, ctypes.byref(n)))
@@ -182,7 +182,7 @@ class State:
 
     def apply(self, plan: Plan, gatewise=False, sync=False, tc=False, jit=False, regbits=0):
         flags = ((N.SV_FLAG_GATEWISE if gatewise else 0) | (N.SV_FLAG_SYNC if sync else 0)
-                 | (N.SV_FLAG_TC_DENSE if tc else 0) | (N.SV_FLAG_SPECIALISE if jit else 0)
+                 | N.tc_flags(tc) | (N.SV_FLAG_SPECIALISE if jit else 0)
                  | N.SV_FLAG_REGBITS(regbits))
         N.check(N.lib.sv_apply_parts(self.h, plan.h, flags))
 

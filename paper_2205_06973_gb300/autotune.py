@@ -78,6 +78,8 @@ STATE_CANDIDATES = (
     ("dagp", 10, False, 0, True), ("beam", 8, True, 0, True), ("beam", 10, False, 13, True),
     ("beam", 8, False, 13, True), ("beam", 9, False, 0, True), ("beam", 11, False, 13, True),
     ("beam", 9, False, 0, True, 4), ("beam", 10, False, 13, True, 4), ("beam", 9, False, 13, True, 4),
+    # tc = 2: two consecutive dense parts per pass where they fit one 13-qubit tile
+    ("beam", 6, 2, 0, False), ("dagp", 6, 2, 0, False), ("beam", 5, 2, 0, False),
 )
 BEAM_WIDTH = 64   # beam builder width for the tuned plans (0.3 s for 2520 gates)
 

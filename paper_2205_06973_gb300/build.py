@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libhisvsim.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "dense.cu", "dense_batch.cu", "noalloc.cu", "batch.cu", "abi.cpp", "batch_abi.cpp",
+SOURCES = ["kernels.cu", "dense.cu", "dense_pair.cu", "dense_batch.cu", "noalloc.cu", "batch.cu", "abi.cpp", "batch_abi.cpp",
            "partition.cpp", "planner.cpp", "qasm.cpp", "jit.cpp"]
 # headers handed to the run-time compiler (NVRTC) by jit.cpp, embedded as
 # string literals: name in the generated include file -> source header

@@ -344,7 +344,7 @@ static sv_status get_host_program(sv_plan *p, bool fp64, int t, int dense, const
         std::unique_ptr<Program> prog(new Program());
         std::string err;
         const int R = (dense >> 4) ? (dense >> 4) : part_R(fp64);
-        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, fp64, t, R, dense & 1, *prog, err,
+        if (!compile_program(p->gates, p->n, p->pog, p->n_parts, fp64, t, R, dense & 3, *prog, err,
                              p->inner.empty() ? nullptr : &p->inner))
             return fail(SV_ERR_PARTITION, err);
         it = p->host_progs.emplace(key, std::move(prog)).first;
@@ -354,9 +354,11 @@ static sv_status get_host_program(sv_plan *p, bool fp64, int t, int dense, const
 }
 
 // Program variant of the flags: bit 0 = tensor-core dense parts (complex64
-// only), bits 4-7 = register bits per thread when not the precision's default.
+// only), bit 1 = two of them per pass where they fit one tile, bits 4-7 =
+// register bits per thread when not the precision's default.
 static int dense_mode(uint32_t flags, bool fp64) {
-    return (((flags & SV_FLAG_TC_DENSE) && !fp64) ? 1 : 0) | (int)(((flags >> 8) & 0xFu) << 4);
+    const bool tc = (flags & SV_FLAG_TC_DENSE) && !fp64;
+    return (tc ? 1 : 0) | ((tc && (flags & SV_FLAG_TC_PAIRS)) ? 2 : 0) | (int)(((flags >> 8) & 0xFu) << 4);
 }
 
 sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int t, uint32_t flags, uint32_t *passes, uint32_t *phases,
@@ -378,7 +380,7 @@ sv_status sv_plan_stats(sv_plan *p, sv_precision prec, int t, uint32_t flags, ui
     if (passes) *passes = (uint32_t)prog->kind.size();
     if (phases) *phases = (uint32_t)prog->phases.size();
     if (ops) *ops = (uint32_t)prog->ops.size();
-    if (dense) *dense = (uint32_t)prog->dense.size();
+    if (dense) *dense = (uint32_t)(prog->dense.size() + prog->pairs.size());
     return SV_OK;
 }
 
@@ -476,6 +478,7 @@ sv_status sv_plan_destroy(sv_plan *p) {
         dev_free(kv.second.d_ops, 0);
         dev_free(kv.second.d_coefs, 0);
         dev_free(kv.second.d_aimg, 0);
+        dev_free(kv.second.d_pimg, 0);
     }
     cudaSetDevice(cur);
     delete p;
@@ -487,6 +490,7 @@ static void free_dev(DevProgram &d, cudaStream_t st) {
     dev_free(d.d_ops, st);
     dev_free(d.d_coefs, st);
     dev_free(d.d_aimg, st);
+    dev_free(d.d_pimg, st);
 }
 
 static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, int dense, const Program **hp,
@@ -509,6 +513,8 @@ static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, int dense, cons
         if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&d.d_ops), sizeof(Op) * nop, st);
         if (e == cudaSuccess) e = dev_alloc(&d.d_coefs, rsz * ncf, st);
         if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&d.d_aimg), nim, st);
+        if (e == cudaSuccess && !prog.pair_img.empty())
+            e = dev_alloc(reinterpret_cast<void **>(&d.d_pimg), prog.pair_img.size(), st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             free_dev(d, st);
@@ -528,6 +534,8 @@ static sv_status get_dev_program(sv_state *s, sv_plan *p, int t, int dense, cons
             e = cudaMemcpyAsync(d.d_coefs, cf, rsz * prog.coefs.size(), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess && !prog.a_img.empty())
             e = cudaMemcpyAsync(d.d_aimg, prog.a_img.data(), prog.a_img.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !prog.pair_img.empty())
+            e = cudaMemcpyAsync(d.d_pimg, prog.pair_img.data(), prog.pair_img.size(), cudaMemcpyHostToDevice, st);
         // the program is shared by every state that applies the plan, on any
         // stream: it is complete before it is published (cf32 also dies here)
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -593,8 +601,8 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
             st = get_jit_program(p, s->prec, t, dense_mode(flags, fp64), hp, &jp);
             if (st != SV_OK) return st;
         }
-        if (!hp->dense.empty()) {
-            const size_t need = hp->dense.size() + 1;
+        if (!hp->dense.empty() || !hp->pairs.empty()) {
+            const size_t need = hp->dense.size() + hp->pairs.size() + 1;
             if (s->dnorm_cap < need) {
                 dev_free(s->d_dnorm, s->stream);
                 s->d_dnorm = nullptr;
@@ -608,6 +616,7 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
             }
             CUDA_TRY(cudaMemsetAsync(s->d_dnorm, 0, sizeof(double) * need, s->stream));
         }
+        uint32_t didx = 0;   // tensor-core passes of this apply, in order (norm accumulators)
         for (size_t i = 0; i < hp->kind.size(); i++) {
             const uint32_t j = hp->index[i];
             cudaError_t e;
@@ -616,9 +625,12 @@ sv_status sv_apply_parts(sv_state *s, sv_plan *p, uint32_t flags) {
             else if (hp->kind[i] == 0)
                 e = launch_part(fp64, hp->t, s->buf, hp->parts[j], dp->d_phases, dp->d_ops, dp->d_coefs,
                                 hp->n_tiles[j], s->stream);
-            else
+            else if (hp->kind[i] == 1)
                 e = launch_dense6(s->buf, hp->dense[j], dp->d_aimg + (size_t)j * DENSE_A_BYTES, hp->dense_tiles[j],
-                                  s->d_err, s->d_dnorm, j, s->stream);
+                                  s->d_err, s->d_dnorm, didx++, s->stream);
+            else
+                e = launch_dense_pair(s->buf, hp->pairs[j], dp->d_pimg + (size_t)j * 2 * DENSE_A_BYTES,
+                                      hp->pair_tiles[j], s->d_err, s->d_dnorm, didx++, s->stream);
             if (e != cudaSuccess) return fail(SV_ERR_CUDA, std::string("part launch: ") + cudaGetErrorString(e));
         }
     }

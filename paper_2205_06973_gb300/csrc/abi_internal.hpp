@@ -37,6 +37,7 @@ struct DevProgram {
     Op *d_ops = nullptr;
     void *d_coefs = nullptr;
     uint8_t *d_aimg = nullptr;      // R images of the dense parts
+    uint8_t *d_pimg = nullptr;      // R images of the dense pairs (two per pass)
 };
 
 struct sv_state {
@@ -52,7 +53,7 @@ struct sv_state {
     double h_norm = 0.0;            // norm read back from the device
     int *d_err = nullptr;           // device error word of bounded waits (0 = none)
     double *d_dnorm = nullptr;      // norm accumulators of one apply's dense passes
-    size_t dnorm_cap = 0;           // (1 + dense parts), grown on demand
+    size_t dnorm_cap = 0;           // (1 + tensor-core passes), grown on demand
     void *d_stage = nullptr;        // double2 staging of double-float downloads (allocated on first use)
 };
 

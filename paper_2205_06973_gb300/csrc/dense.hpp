@@ -25,6 +25,25 @@ struct DenseLaunch {
     uint16_t pad;
 };
 
+// Launch record of a pass that applies two dense parts (by value): the tile
+// is the 13 qubits T = P1 u P2 u (lowest others); layout j has its part's
+// qubits as rows and the 7 other tile qubits as columns. s_* are the slots
+// (0..12, ascending qubit order of T) of those qubits.
+struct DensePairLaunch {
+    uint64_t outer_mask;       // qubits outside the tile
+    int32_t n;
+    uint8_t q1[DENSE_K], c1[DENSE_COLS], q2[DENSE_K], c2[DENSE_COLS];
+    uint8_t s_q1[DENSE_K], s_c1[DENSE_COLS], s_q2[DENSE_K], s_c2[DENSE_COLS];
+    uint8_t prefetch;          // f: qubits 0..f-1 are tile qubits (2 <= f <= 4): L2 warm-up by runs of 2^f
+    uint8_t pad[3];
+    // shared-buffer element offset of each tile slot (XOR-linear in the slot
+    // bits; bits above 3 keep their place, the low 4 bits pick the bank
+    // pair): chosen so that the 16 lanes of a half-warp, which run over the
+    // slots of the lowest 4 column qubits of either layout, hit 16 distinct
+    // bank pairs
+    uint16_t xsw[DENSE_K + DENSE_COLS];
+};
+
 // Host: build the A image of a 64x64 complex unitary U (row-major, interleaved
 // re/im doubles): real block form R[2i+c][2j+d], split to BF16 hi/lo, laid out
 // K-major with the 128-byte swizzle the tensor-core descriptors expect.
@@ -37,5 +56,12 @@ void dense_a_image(const double *U, std::vector<uint8_t> &img);
 // drift of the split-BF16 tensor-core arithmetic.
 cudaError_t launch_dense6(void *sv, const DenseLaunch &L, const void *a_img, uint64_t n_tiles, int *d_err,
                           double *d_norms, uint32_t dense_idx, cudaStream_t st);
+
+// One pass of two dense parts: U1 (image img2, layout 1), then U2 (image
+// img2 + DENSE_A_BYTES, layout 2), on every 13-qubit tile; the norm
+// accumulators and the rescale as for launch_dense6, dense_idx counting the
+// tensor-core passes of the apply.
+cudaError_t launch_dense_pair(void *sv, const DensePairLaunch &L, const void *img2, uint64_t n_tiles, int *d_err,
+                              double *d_norms, uint32_t dense_idx, cudaStream_t st);
 
 }  // namespace hisv

@@ -190,6 +190,49 @@ void fused_unitary(const std::vector<GateRef> &gates, const std::vector<int> &id
     }
 }
 
+// Bank bits of the pair kernel's shared buffer: slot p < 4 keeps its bit;
+// slot p >= 4 also flips the 4-bit bank-pair value v_p. A half-warp's 16
+// lanes run over the slots of the lowest 4 column qubits of layout 1 (when
+// writing) or layout 2 (when reading); the v_p are picked (fixed-seed search)
+// so that both sets of 4 slots map to independent bank vectors, i.e. 16
+// distinct bank pairs. Falls back to v_p = bit (p mod 4) if none is found.
+static void pair_swizzle(DensePairLaunch &D) {
+    const int NS = DENSE_K + DENSE_COLS;
+    auto indep = [](const uint32_t *w) {
+        uint32_t span = 1u;   // bit mask over the 16 bank values reachable
+        for (int i = 0; i < 4; i++) {
+            if ((span >> w[i]) & 1u) return false;
+            uint32_t ns = span;
+            for (uint32_t x = 0; x < 16; x++)
+                if ((span >> x) & 1u) ns |= 1u << (x ^ w[i]);
+            span = ns;
+        }
+        return true;
+    };
+    uint32_t v[DENSE_K + DENSE_COLS];
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    bool found = false;
+    for (int trial = 0; trial < 4096 && !found; trial++) {
+        for (int p = 0; p < NS; p++) {
+            if (p < 4) v[p] = 1u << p;
+            else if (trial == 0) v[p] = 1u << (p & 3);
+            else {
+                st = st * 6364136223846793005ull + 1442695040888963407ull;
+                v[p] = 1u + (uint32_t)((st >> 33) % 15u);
+            }
+        }
+        uint32_t w1[4], w2[4];
+        for (int i = 0; i < 4; i++) {
+            w1[i] = v[D.s_c1[i]];
+            w2[i] = v[D.s_c2[i]];
+        }
+        found = indep(w1) && indep(w2);
+    }
+    if (!found)
+        for (int p = 4; p < NS; p++) v[p] = 1u << (p & 3);
+    for (int p = 0; p < NS; p++) D.xsw[p] = (uint16_t)(p < 4 ? (1u << p) : ((1u << p) | v[p]));
+}
+
 bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector<uint32_t> &pog,
                      uint32_t n_parts, bool fp64, int t_cfg, int R, int dense_mode, Program &prog,
                      std::string &err, const std::vector<uint32_t> *inner) {
@@ -222,7 +265,62 @@ bool compile_program(const std::vector<GateRef> &gates, int n, const std::vector
         if (gl.empty()) continue;
         uint64_t S = 0;
         for (int g : gl) S |= gmask[g];
-        if (dense_mode == 1 && !fp64 && popc(S) <= DENSE_K && n >= DENSE_K + DENSE_COLS) {
+        if ((dense_mode & 2) && !fp64 && popc(S) <= DENSE_K && n >= DENSE_K + DENSE_COLS && pi + 1 < n_parts &&
+            !members[pi + 1].empty()) {
+            // two consecutive dense parts in one pass (multi-level
+            // partitioning, Sec. IV-B: a 13-qubit tile as the first level,
+            // two 6-qubit products as the second); each part is padded to 6
+            // with the other's qubits first, and the tile adds the lowest
+            // remaining qubits; paired only if the tile holds qubits 0 and 1
+            // (runs of 4 consecutive amplitudes: whole 32-byte sectors)
+            uint64_t S2 = 0;
+            for (int g : members[pi + 1]) S2 |= gmask[g];
+            if (popc(S2) <= DENSE_K) {
+                auto pad = [&](uint64_t P, uint64_t pref) {
+                    for (int q = n - 1; q >= 0 && popc(P) < DENSE_K; q--)
+                        if ((pref >> q) & 1) P |= 1ull << q;
+                    for (int q = n - 1; q >= 0 && popc(P) < DENSE_K; q--) P |= 1ull << q;
+                    return P;
+                };
+                const uint64_t P1 = pad(S, S2 & ~S), P2 = pad(S2, S & ~S2);
+                uint64_t T = P1 | P2;
+                for (int q = 0; q < n && popc(T) < DENSE_K + DENSE_COLS; q++) T |= 1ull << q;
+                if ((T & 3ull) == 3ull && popc(T) == DENSE_K + DENSE_COLS) {
+                    DensePairLaunch D;
+                    std::memset(&D, 0, sizeof(D));
+                    D.n = n;
+                    D.outer_mask = all & ~T;
+                    int f = 0;
+                    while (f < 4 && ((T >> f) & 1)) f++;
+                    D.prefetch = (uint8_t)f;
+                    int slot = 0, j1 = 0, c1 = 0, j2 = 0, c2 = 0, qs1[DENSE_K], qs2[DENSE_K];
+                    for (int q = 0; q < n; q++) {
+                        if (!((T >> q) & 1)) continue;
+                        if ((P1 >> q) & 1) { qs1[j1] = q; D.s_q1[j1] = (uint8_t)slot; D.q1[j1++] = (uint8_t)q; }
+                        else { D.s_c1[c1] = (uint8_t)slot; D.c1[c1++] = (uint8_t)q; }
+                        if ((P2 >> q) & 1) { qs2[j2] = q; D.s_q2[j2] = (uint8_t)slot; D.q2[j2++] = (uint8_t)q; }
+                        else { D.s_c2[c2] = (uint8_t)slot; D.c2[c2++] = (uint8_t)q; }
+                        slot++;
+                    }
+                    pair_swizzle(D);
+                    std::vector<double> U;
+                    std::vector<uint8_t> img;
+                    fused_unitary(gates, gl, qs1, DENSE_K, U);
+                    dense_a_image(U.data(), img);
+                    prog.pair_img.insert(prog.pair_img.end(), img.begin(), img.end());
+                    fused_unitary(gates, members[pi + 1], qs2, DENSE_K, U);
+                    dense_a_image(U.data(), img);
+                    prog.pair_img.insert(prog.pair_img.end(), img.begin(), img.end());
+                    prog.kind.push_back(2);
+                    prog.index.push_back((uint32_t)prog.pairs.size());
+                    prog.pairs.push_back(D);
+                    prog.pair_tiles.push_back(1ull << (n - DENSE_K - DENSE_COLS));
+                    pi++;   // the second part is done
+                    continue;
+                }
+            }
+        }
+        if ((dense_mode & 1) && !fp64 && popc(S) <= DENSE_K && n >= DENSE_K + DENSE_COLS) {
             // dense part: the part's qubits padded to 6 with the highest others
             // (the unitary is the identity on them), columns on the lowest 7
             // remaining qubits, so that the 32 lanes of a warp (columns) stay
@@ -668,8 +766,8 @@ void program_flops(const Program &prog, double &alu_per_amp, double &tensor_per_
     tensor_per_amp = 0.0;
     const int NR = 1 << prog.R;
     for (size_t i = 0; i < prog.kind.size(); i++) {
-        if (prog.kind[i] == 1) {
-            tensor_per_amp += 2.0 * 3.0 * 2.0 * 128.0;
+        if (prog.kind[i] == 1 || prog.kind[i] == 2) {
+            tensor_per_amp += (prog.kind[i] == 2 ? 2.0 : 1.0) * 2.0 * 3.0 * 2.0 * 128.0;
             continue;
         }
         const PartLaunch &L = prog.parts[prog.index[i]];

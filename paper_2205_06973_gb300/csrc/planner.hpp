@@ -19,12 +19,17 @@ struct Program {
     std::vector<Op> ops;
     std::vector<double> coefs;
     // execution order over all parts: kind 0 = gate-list part parts[index],
-    // kind 1 = dense tensor-core part dense[index] (A image a_img[index])
+    // kind 1 = dense tensor-core part dense[index] (A image a_img[index]),
+    // kind 2 = two dense parts in one pass pairs[index] (images
+    // pair_img[2 index], pair_img[2 index + 1])
     std::vector<uint8_t> kind;
     std::vector<uint32_t> index;
     std::vector<DenseLaunch> dense;
     std::vector<uint64_t> dense_tiles;
     std::vector<uint8_t> a_img;           // DENSE_A_BYTES per dense part
+    std::vector<DensePairLaunch> pairs;
+    std::vector<uint64_t> pair_tiles;
+    std::vector<uint8_t> pair_img;        // 2 x DENSE_A_BYTES per pair
 };
 
 // Gate matrices of the library (row-major complex, interleaved re/im):
@@ -35,8 +40,9 @@ bool gate_is_two_qubit(int kind);
 
 // Compile the parts (part_of_gate numbered in execution order) for a tile of
 // t_cfg qubits (t = min(n, t_cfg)) and R register bits.
-// dense_mode: 0 = gate lists only; 1 = every part of at most 6 qubits runs
-// as a dense tensor-core part (complex64, n >= 13).
+// dense_mode: bit 0 = every part of at most 6 qubits runs as a dense
+// tensor-core part (complex64, n >= 13); bit 1 = two consecutive such parts
+// run in one pass where their qubits and qubits 0, 1 fit a 13-qubit tile.
 // inner (optional): the second-level part of every gate (multi-level
 // partitioning, Sec. IV-B); each becomes one register phase of its
 // first-level part instead of the greedy phase split (error if one needs
