@@ -74,9 +74,9 @@ def _check(api, n, g, ref, method, k, tc=False, gatewise=False, dfs_trials=16, j
 
 
 def test_benchmark_plans_match_oracle(layered28):
-    """Every candidate of the state autotuner (the benchmark times the fastest
-    of them, the beam builder's 140-pass tensor-core plan on GB300) against
-    the oracle."""
+    """Every candidate of the state autotuner against the oracle (the
+    benchmark times the fastest of them: on GB300 the beam builder's k = 9
+    plan on the specialised kernels, 79 passes)."""
     _, api = native()
     from paper_2205_06973_gb300.autotune import BEAM_WIDTH, STATE_CANDIDATES
     n, g, ref = layered28
@@ -99,6 +99,46 @@ def test_paper_builders_match_oracle(layered28, method, k):
     _check(api, n, g, ref, method, k, jit=True)
 
 
+@pytest.mark.parametrize("method,k", [("nat", 8), ("nat", 12), ("dfs", 8), ("dfs", 12)])
+def test_builder_grid_matches_oracle(layered28, method, k):
+    """The rest of the builder x k grid that bench.py times (Nat and DFS at
+    k = 8 and 12), on both gate-list kernels."""
+    _, api = native()
+    n, g, ref = layered28
+    _check(api, n, g, ref, method, k)
+    _check(api, n, g, ref, method, k, jit=True)
+
+
+@pytest.mark.parametrize("method", ["nat", "dfs", "dagp"])
+def test_k12_on_its_own_tile_matches_oracle(layered28, method):
+    """k = 12 parts on a 2^12 tile (the part's own qubits only, so a part
+    without qubit 0 gathers runs of one amplitude), specialised kernels."""
+    _, api = native()
+    n, g, ref = layered28
+    _check(api, n, g, ref, method, 12, jit=True, tile=12)
+
+
+@pytest.mark.parametrize("method,k", [("dagp", 10), ("beam", 10), ("beam", 12)])
+def test_multilevel_plans_match_oracle(layered28, method, k):
+    """Two-level plans (Sec. IV-B): the first-level parts re-partitioned by a
+    second builder under k2 = 5, whose parts are the register phases of the
+    specialised kernels; the plans bench.py times beside one level."""
+    _, api = native()
+    n, g, ref = layered28
+    for inner in (("dagp", 5), ("beam", 5)):
+        plan = api.Plan(g, n, method, k, inner=inner)
+        st = api.State(n, "c64")
+        st.apply(plan, sync=True, jit=True)
+        mx, rel, fid, nrm = _compare(ref, st.amplitudes())
+        st.close()
+        plan.close()
+        tag = f"{method} k={k} inner={inner}"
+        assert mx <= MAX_ABS, f"{tag}: max-abs {mx:.3e}"
+        assert rel <= REL_L2, f"{tag}: rel-L2 {rel:.3e}"
+        assert fid >= FIDELITY, f"{tag}: fidelity {fid}"
+        assert abs(nrm - 1.0) <= NORM, f"{tag}: norm {nrm}"
+
+
 def test_gate_by_gate_matches_oracle(layered28):
     _, api = native()
     n, g, ref = layered28
@@ -111,13 +151,17 @@ def test_complex128_paths_match_oracle(layered28):
     double-float arithmetic (SV_C128DF): max-abs <= 1e-12 against the oracle."""
     _, api = native()
     n, g, ref = layered28
-    plan = api.Plan(g, n, "beam", 10, dfs_trials=16)
-    for precision, jit in (("c128", False), ("c128", True), ("c128df", True)):
+    # every row of the benchmark's complex128 section
+    cases = (("dagp", 10, "c128", False), ("dagp", 10, "c128", True), ("beam", 10, "c128", False),
+             ("beam", 10, "c128", True), ("beam", 10, "c128df", True), ("beam", 8, "c128df", True),
+             ("dagp", 10, "c128df", True))
+    for method, k, precision, jit in cases:
+        plan = api.Plan(g, n, method, k, dfs_trials=16)
         st = api.State(n, precision)
         st.apply(plan, sync=True, jit=jit)
         out = st.amplitudes() if precision == "c128" else st.export_c128()
         mx = float(max((out[s:s + (1 << 24)] - ref[s:s + (1 << 24)]).abs().max() for s in range(0, 1 << n, 1 << 24)))
         del out
         st.close()
-        assert mx <= 1e-12, (precision, jit, mx)
-    plan.close()
+        plan.close()
+        assert mx <= 1e-12, (method, k, precision, jit, mx)
