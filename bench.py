@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-grid", action="store_true", help="skip the builder x k grid and the complex128 line")
     ap.add_argument("--n", type=int, default=28)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-states", type=int, default=3,
+                    help="states in turn in the end-to-end loop (copies of one overlap the others' passes)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 4096-circuit batched launch")
@@ -618,32 +620,35 @@ def run_ours(a):
 
     e2e = None
     if not a.no_e2e:
-        # two states on two streams: a step's upload and download overlap the
-        # other state's passes (every step still copies its input in and its
-        # result out through the C ABI). Each step's passes wait for the
-        # previous step's passes (an event), so the two states take turns on
-        # the SMs instead of sharing them: while one runs its passes, the
-        # other's download and next upload cross the host link (one copy at
-        # a time), and the copies leave the compute timeline
-        sts = [api.State(n, "c64", stream=torch.cuda.Stream(), tile=choice.get("tile", 0)) for _ in range(2)]
-        host_in = torch.zeros(1 << n, dtype=torch.complex64).pin_memory()   # read by both states
+        # S states on S streams (S = 3 by default), used in turn: a step's
+        # upload and download overlap the other states' passes. Each step's
+        # passes wait for the previous step's passes (an event), so the
+        # states take turns on the SMs instead of sharing them, and the
+        # copies leave the compute timeline. A state is reused only after
+        # its download of S steps back has reached host memory, which gives
+        # a download and the next upload S - 1 steps of passes to hide in
+        # (the host link's rate varies from box to box and under the host
+        # memory traffic of other jobs)
+        S = max(2, a.e2e_states)
+        sts = [api.State(n, "c64", stream=torch.cuda.Stream(), tile=choice.get("tile", 0)) for _ in range(S)]
+        host_in = torch.zeros(1 << n, dtype=torch.complex64).pin_memory()   # read by every state
         host_in[0] = 1.0
-        host_out = [torch.empty(1 << n, dtype=torch.complex64).pin_memory() for _ in range(2)]
+        host_out = [torch.empty(1 << n, dtype=torch.complex64).pin_memory() for _ in range(S)]
         def step(i, last):
-            x = sts[i % 2]
-            if i >= 2:
-                x.sync()          # its step i-2 result has reached host memory
+            x = sts[i % S]
+            if i >= S:
+                x.sync()          # its result of step i - S has reached host memory
             x.upload(host_in)
             if last is not None:
                 x.stream.wait_event(last)
             x.apply(plan, tc=tc, jit=jit, regbits=regbits)
             done = torch.cuda.Event()
             done.record(x.stream)
-            x.download(host_out[i % 2])
+            x.download(host_out[i % S])
             return done
 
         last = None
-        for i in range(2):
+        for i in range(S):
             last = step(i, last)
         for x in sts:
             x.sync()
@@ -663,8 +668,9 @@ def run_ours(a):
         e2e = {"value": round(ws * bytes_per_step / dt / 1e9, 1), "unit": UNIT,
                "h2d_bytes_per_step": st.nbytes, "d2h_bytes_per_step": st.nbytes,
                "ms_per_step": round(dt * 1e3, 3), "steps": reps,
-               "api": "sv_upload + sv_apply_parts + sv_download (pinned host buffers), two states on two "
-                      "streams taking turns on the SMs, so that one step's copies overlap the other's passes"}
+               "states": S,
+               "api": f"sv_upload + sv_apply_parts + sv_download (pinned host buffers), {S} states on {S} "
+                      "streams taking turns on the SMs, so that a step's copies overlap the other states' passes"}
 
     compare = None
     if not a.no_compare:
