@@ -36,6 +36,11 @@ WORKLOAD = ("random layered circuit, 28 qubits, depth 60 (H/RX/RZ on every qubit
             "random disjoint pairing; 2520 gates, seed 2), complex64 state, part-fused passes")
 
 
+
+def workload_text(n, n_gates):
+    """The workload line for the layered circuit on n qubits (28 by default)."""
+    return WORKLOAD.replace("28 qubits", f"{n} qubits").replace("2520 gates", f"{n_gates} gates")
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -723,7 +728,8 @@ def run_ours(a):
         line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
                 "warmup": max(a.warmup, 3), "ms_per_step": round(ms, 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_TC if tc else DTYPE_FP32, "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_qubits": n, "gates": len(gates), "method": method,
+                "config": {"workload": workload_text(n, len(gates)), "n_qubits": n,
+                           "gates": len(gates), "method": method,
                            "k": k, "tensor_core_dense_parts": stats["dense"], "passes": passes,
                            "specialised_kernels": jit, "tile": choice.get("tile") or "default",
                            "register_bits": regbits or "default",
@@ -786,7 +792,8 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64 arithmetic)", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("complex64 state", "complex128 state (the oracle's type)"),
+            "config": {"workload": workload_text(n, len(gates)).replace(
+                           "complex64 state", "complex128 state (the oracle's type)"),
                        "n_qubits": n, "method": a.method, "k": k, "passes": P,
                        "parallelism": "host cores (OpenMP)"},
             "cpu_baseline": cpu,
