@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--no-grid", action="store_true", help="skip the builder x k grid and the complex128 line")
     ap.add_argument("--n", type=int, default=28)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-e2e-child", action="store_true",
+                    help="measure the end-to-end loop only in this process")
+    ap.add_argument("--e2e-only", action="store_true",
+                    help="run only the end-to-end loop for the plan given by --method/--k/--tc/--jit/--regbits/--tile")
     ap.add_argument("--e2e-states", type=int, default=3,
                     help="states in turn in the end-to-end loop (copies of one overlap the others' passes)")
     ap.add_argument("--no-compare", action="store_true")
@@ -338,6 +342,113 @@ def serving_section(window_s=3.0):
     return out
 
 
+
+def e2e_loop(n, plan, tc, jit, regbits, tile, S, host_in, host_out, ws, dev, bytes_per_step, reps=12):
+    """The end-to-end metric through the C ABI: every step uploads its input
+    from pinned host memory (sv_upload), applies the plan (sv_apply_parts)
+    and downloads its result (sv_download). S states on S streams are used
+    in turn, so a step's upload and download overlap the other states'
+    passes; each step's passes wait for the previous step's passes (an
+    event), so the states take turns on the SMs instead of sharing them and
+    the copies leave the compute timeline. A state is reused only after its
+    download of S steps back has reached host memory, which gives a
+    download and the next upload S - 1 steps of passes to hide in (the host
+    link's rate varies from box to box and under other jobs' host memory
+    traffic)."""
+    import torch
+    from paper_2205_06973_gb300 import api
+    sts = [api.State(n, "c64", stream=torch.cuda.Stream(), tile=tile) for _ in range(S)]
+
+    def step(i, last):
+        x = sts[i % S]
+        if i >= S:
+            x.sync()          # its result of step i - S has reached host memory
+        x.upload(host_in)
+        if last is not None:
+            x.stream.wait_event(last)
+        x.apply(plan, tc=tc, jit=jit, regbits=regbits)
+        done = torch.cuda.Event()
+        done.record(x.stream)
+        x.download(host_out[i % S])
+        return done
+
+    last = None
+    for i in range(S):
+        last = step(i, last)
+    for x in sts:
+        x.sync()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    last = None
+    for i in range(reps):
+        last = step(i, last)
+    for x in sts:
+        x.sync()
+    dt = (time.perf_counter() - t0) / reps
+    dt = max_over_ranks(ws, dt, dev)
+    nbytes = sts[0].nbytes
+    for x in sts:
+        x.close()
+    return {"value": round(ws * bytes_per_step / dt / 1e9, 1), "unit": UNIT,
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "ms_per_step": round(dt * 1e3, 3), "steps": reps, "states": S,
+            "api": f"sv_upload + sv_apply_parts + sv_download (pinned host buffers), {S} states on {S} "
+                   "streams taking turns on the SMs, so that a step's copies overlap the other states' passes"}
+
+
+def pinned_buffers(n, S):
+    """The end-to-end loop's pinned host buffers: one input (|0...0>) read by
+    every state, one output per state."""
+    import torch
+    host_in = torch.zeros(1 << n, dtype=torch.complex64).pin_memory()
+    host_in[0] = 1.0
+    return host_in, [torch.empty(1 << n, dtype=torch.complex64).pin_memory() for _ in range(S)]
+
+
+def e2e_child(n, method, k, tc, jit, regbits, tile, S):
+    """e2e_loop in a fresh process on the same GPU with the given plan
+    (bench.py --e2e-only); its e2e object, or {"error": ...}."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--e2e-only", "--n", str(n), "--method", method,
+           "--k", str(k), "--tc", str(int(tc)), "--jit", str(int(jit)), "--regbits", str(regbits),
+           "--tile", str(tile), "--e2e-states", str(S)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+    except subprocess.TimeoutExpired:
+        return {"error": "fresh-process end-to-end run timed out"}
+    for line in reversed(r.stdout.strip().splitlines()):
+        if line.startswith("{"):
+            try:
+                out = json.loads(line)["e2e"]
+                out["process"] = "fresh process: loads the tuned plan and runs only this loop"
+                return out
+            except (ValueError, KeyError):
+                break
+    return {"error": f"e2e child exited {r.returncode}: " + " | ".join(r.stderr.strip().splitlines()[-3:])}
+
+
+def run_e2e_only(a):
+    """bench.py --e2e-only: the end-to-end loop alone, for the plan given on
+    the command line (one JSON line {"e2e": ...})."""
+    import torch
+    torch.cuda.set_device(0)
+    import synth
+    from paper_2205_06973_gb300 import api
+    from paper_2205_06973_gb300.autotune import BEAM_WIDTH
+    n, gates = synth.layered_28q(n=a.n)
+    S = max(2, a.e2e_states)
+    host_in, host_out = pinned_buffers(n, S)
+    plan = api.Plan(gates, n, a.method, a.k, dfs_trials=BEAM_WIDTH if a.method == "beam" else 16)
+    tc, jit = int(a.tc), bool(a.jit)
+    if jit:
+        plan.specialise("c64", a.tile, tc=tc, regbits=a.regbits)
+    passes = plan.stats("c64", a.tile, tc=tc, regbits=a.regbits)["passes"]
+    e2e = e2e_loop(n, plan, tc, jit, a.regbits, a.tile, S, host_in, host_out, 1, torch.device("cuda", 0),
+                   passes * 2 * (8 << n))
+    e2e["host_buffers"] = "pinned, allocated at process start"
+    plan.close()
+    print(json.dumps({"e2e": e2e}), flush=True)
+
 def serving_child(window_s):
     """serving_section in a child process on the same GPU: the serving loop
     runs many streams and host threads at once, and a device fault there
@@ -573,9 +684,7 @@ def run_ours(a):
     # run-time compilations take and return host memory
     S = max(2, a.e2e_states)
     if not a.no_e2e:
-        host_in = torch.zeros(1 << n, dtype=torch.complex64).pin_memory()   # read by every state
-        host_in[0] = 1.0
-        host_out = [torch.empty(1 << n, dtype=torch.complex64).pin_memory() for _ in range(S)]
+        host_in, host_out = pinned_buffers(n, S)
     st = api.State(n, "c64", tile=a.tile)
     if a.k:
         choice = {"method": a.method, "k": a.k, "tc": int(a.tc), "tile": a.tile, "jit": bool(a.jit),
@@ -633,54 +742,19 @@ def run_ours(a):
 
     e2e = None
     if not a.no_e2e:
-        # S states on S streams (S = 3 by default), used in turn: a step's
-        # upload and download overlap the other states' passes. Each step's
-        # passes wait for the previous step's passes (an event), so the
-        # states take turns on the SMs instead of sharing them, and the
-        # copies leave the compute timeline. A state is reused only after
-        # its download of S steps back has reached host memory, which gives
-        # a download and the next upload S - 1 steps of passes to hide in
-        # (the host link's rate varies from box to box and under the host
-        # memory traffic of other jobs)
-        sts = [api.State(n, "c64", stream=torch.cuda.Stream(), tile=choice.get("tile", 0)) for _ in range(S)]
-        def step(i, last):
-            x = sts[i % S]
-            if i >= S:
-                x.sync()          # its result of step i - S has reached host memory
-            x.upload(host_in)
-            if last is not None:
-                x.stream.wait_event(last)
-            x.apply(plan, tc=tc, jit=jit, regbits=regbits)
-            done = torch.cuda.Event()
-            done.record(x.stream)
-            x.download(host_out[i % S])
-            return done
-
-        last = None
-        for i in range(S):
-            last = step(i, last)
-        for x in sts:
-            x.sync()
-        torch.cuda.synchronize()
-        reps = 12
-        barrier(ws)
-        t0 = time.perf_counter()
-        last = None
-        for i in range(reps):
-            last = step(i, last)
-        for x in sts:
-            x.sync()
-        dt = (time.perf_counter() - t0) / reps
-        dt = max_over_ranks(ws, dt, dev)
-        for x in sts:
-            x.close()
+        e2e = e2e_loop(n, plan, tc, jit, regbits, choice.get("tile", 0) or 0, S, host_in, host_out, ws, dev,
+                       bytes_per_step)
+        e2e["host_buffers"] = "pinned, allocated at process start (before the autotuner)"
         del host_in, host_out
-        e2e = {"value": round(ws * bytes_per_step / dt / 1e9, 1), "unit": UNIT,
-               "h2d_bytes_per_step": st.nbytes, "d2h_bytes_per_step": st.nbytes,
-               "ms_per_step": round(dt * 1e3, 3), "steps": reps,
-               "states": S, "host_buffers": "pinned, allocated at process start",
-               "api": f"sv_upload + sv_apply_parts + sv_download (pinned host buffers), {S} states on {S} "
-                      "streams taking turns on the SMs, so that a step's copies overlap the other states' passes"}
+        if ws == 1 and not a.no_e2e_child:
+            # the same loop in a fresh process that loads the tuned plan, as a
+            # service does after tuning (the autotuner caches its choice)
+            fresh = e2e_child(n, method, k, tc, jit, regbits, choice.get("tile", 0) or 0, S)
+            if "value" in fresh:
+                fresh["in_process_after_autotune"] = {"value": e2e["value"], "ms_per_step": e2e["ms_per_step"]}
+                e2e = fresh
+            else:
+                e2e["fresh_process"] = fresh
 
     compare = None
     if not a.no_compare:
@@ -958,6 +1032,8 @@ def main():
         oracle_report()
     elif a.impl == "reference":
         run_reference(a)
+    elif a.e2e_only:
+        run_e2e_only(a)
     else:
         run_ours(a)
 
