@@ -679,9 +679,8 @@ def run_ours(a):
     from paper_2205_06973_gb300 import api
 
     n, gates = synth.layered_28q(n=a.n)
-    # pinned host buffers of the end-to-end loop, allocated at start (as a
-    # service allocates its staging buffers), before the autotuner's
-    # run-time compilations take and return host memory
+    # pinned host buffers of the end-to-end loop, allocated once at start
+    # (as a service allocates its staging buffers)
     S = max(2, a.e2e_states)
     if not a.no_e2e:
         host_in, host_out = pinned_buffers(n, S)
@@ -744,7 +743,7 @@ def run_ours(a):
     if not a.no_e2e:
         e2e = e2e_loop(n, plan, tc, jit, regbits, choice.get("tile", 0) or 0, S, host_in, host_out, ws, dev,
                        bytes_per_step)
-        e2e["host_buffers"] = "pinned, allocated at process start (before the autotuner)"
+        e2e["host_buffers"] = "pinned, allocated at process start"
         del host_in, host_out
         if ws == 1 and not a.no_e2e_child:
             # the same loop in a fresh process that loads the tuned plan, as a
