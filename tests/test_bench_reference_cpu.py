@@ -1,7 +1,8 @@
 """bench.py's reference arm (the oracle timed on the host cores) keeps the
 benchmark's one-line JSON contract: the same metric and unit as the GPU
 arm, impl "reference", a cpu_baseline describing the run, an e2e object
-with no host-device bytes, and no output on ranks other than 0."""
+with no host-device bytes, and no output on ranks other than 0. Also the
+failure path of the GPU arm's fresh-process end-to-end run."""
 import json
 import os
 import subprocess
@@ -41,3 +42,16 @@ def test_reference_other_ranks_are_silent():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_e2e_child_failure_is_reported_not_raised():
+    """Where the fresh-process end-to-end run cannot run (here: no GPU), the
+    benchmark gets an error record instead of an exception, and keeps its
+    in-process measurement."""
+    import pytest
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("the child run succeeds where a GPU is present")
+    import bench
+    out = bench.e2e_child(12, "beam", 9, 0, True, 0, 0, 3)
+    assert set(out) == {"error"} and out["error"].startswith("e2e child exited")
