@@ -1,6 +1,6 @@
 """The distributed state vector (Sec. III-D) on CPU ranks: the exchange plan's
 invariants, the exchange index algebra emulated in one process, and gloo
-worlds of 2 and 4 ranks against the single-state oracle. The local step of
+worlds of 2, 4 and 8 ranks against the single-state oracle. The local step of
 each rank (a part's gates on its slice) is the oracle here, standing in for
 the library's kernels, which need a GPU; the exchanges are the real
 torch.distributed all-to-alls."""
@@ -163,7 +163,7 @@ def _worker(rank, ws, port, n, k, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("ws,n,k", [(2, 10, 7), (4, 10, 6)])
+@pytest.mark.parametrize("ws,n,k", [(2, 10, 7), (4, 10, 6), (8, 11, 7)])
 def test_gloo_ranks_match_oracle(ws, n, k):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
