@@ -343,7 +343,8 @@ def serving_section(window_s=3.0):
 
 
 
-def e2e_loop(n, plan, tc, jit, regbits, tile, S, host_in, host_out, ws, dev, bytes_per_step, reps=12):
+def e2e_loop(n, plan, tc, jit, regbits, tile, S, host_in, host_out, ws, dev, bytes_per_step, reps=12,
+             states=None):
     """The end-to-end metric through the C ABI: every step uploads its input
     from pinned host memory (sv_upload), applies the plan (sv_apply_parts)
     and downloads its result (sv_download). S states on S streams are used
@@ -354,10 +355,15 @@ def e2e_loop(n, plan, tc, jit, regbits, tile, S, host_in, host_out, ws, dev, byt
     download of S steps back has reached host memory, which gives a
     download and the next upload S - 1 steps of passes to hide in (the host
     link's rate varies from box to box and under other jobs' host memory
-    traffic)."""
+    traffic). ``states``: S states to use (each on its own stream; kept
+    open), else S are allocated here and closed at the end."""
     import torch
     from paper_2205_06973_gb300 import api
-    sts = [api.State(n, "c64", stream=torch.cuda.Stream(), tile=tile) for _ in range(S)]
+    own = states is None
+    sts = [api.State(n, "c64", stream=torch.cuda.Stream(), tile=tile) for _ in range(S)] if own else states
+    if not own:
+        for x in sts:
+            x.set_tile(tile)
 
     def step(i, last):
         x = sts[i % S]
@@ -388,8 +394,9 @@ def e2e_loop(n, plan, tc, jit, regbits, tile, S, host_in, host_out, ws, dev, byt
     dt = (time.perf_counter() - t0) / reps
     dt = max_over_ranks(ws, dt, dev)
     nbytes = sts[0].nbytes
-    for x in sts:
-        x.close()
+    if own:
+        for x in sts:
+            x.close()
     return {"value": round(ws * bytes_per_step / dt / 1e9, 1), "unit": UNIT,
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
             "ms_per_step": round(dt * 1e3, 3), "steps": reps, "states": S,
@@ -679,11 +686,13 @@ def run_ours(a):
     from paper_2205_06973_gb300 import api
 
     n, gates = synth.layered_28q(n=a.n)
-    # pinned host buffers of the end-to-end loop, allocated once at start
-    # (as a service allocates its staging buffers)
+    # the end-to-end loop's pinned host buffers and device states, allocated
+    # once at start (as a service allocates its staging buffers and states),
+    # before the autotuner's many allocations
     S = max(2, a.e2e_states)
     if not a.no_e2e:
         host_in, host_out = pinned_buffers(n, S)
+        e2e_states = [api.State(n, "c64", stream=torch.cuda.Stream()) for _ in range(S)]
     st = api.State(n, "c64", tile=a.tile)
     if a.k:
         choice = {"method": a.method, "k": a.k, "tc": int(a.tc), "tile": a.tile, "jit": bool(a.jit),
@@ -742,9 +751,12 @@ def run_ours(a):
     e2e = None
     if not a.no_e2e:
         e2e = e2e_loop(n, plan, tc, jit, regbits, choice.get("tile", 0) or 0, S, host_in, host_out, ws, dev,
-                       bytes_per_step)
+                       bytes_per_step, states=e2e_states)
         e2e["host_buffers"] = "pinned, allocated at process start"
-        del host_in, host_out
+        e2e["device_states"] = "allocated at process start"
+        for x in e2e_states:
+            x.close()
+        del host_in, host_out, e2e_states
         if ws == 1 and not a.no_e2e_child:
             # the same loop in a fresh process that loads the tuned plan, as a
             # service does after tuning (the autotuner caches its choice)
