@@ -252,3 +252,75 @@ def test_nested_algorithm1_catches_a_misplaced_gate():
     ref = sim.run(n, g)
     assert np.abs(sim.run_alg1_nested(n, g, outer, good) - ref).max() <= 1e-13
     assert np.abs(sim.run_alg1_nested(n, g, outer, bad) - ref).max() > 1e-3
+
+
+def _part_graph(gates, n, pog):
+    """Parts' qubit sets and the part graph: an edge a -> b when a gate of a
+    is the previous gate on some qubit of a gate of b (the wire order of
+    Sec. IV-A), written here from the gate list alone."""
+    P = max(pog) + 1
+    qs = [set() for _ in range(P)]
+    succ = [set() for _ in range(P)]
+    last = [None] * n
+    for i, (_, qubits, _) in enumerate(gates):
+        for q in qubits:
+            qs[pog[i]].add(q)
+            if last[q] is not None and pog[last[q]] != pog[i]:
+                succ[pog[last[q]]].add(pog[i])
+            last[q] = i
+    return qs, succ
+
+
+def _reach(succ):
+    """reach[a] = the parts reachable from a by a path of length >= 1."""
+    P = len(succ)
+    reach = [set() for _ in range(P)]
+    for a in range(P):
+        stack = list(succ[a])
+        while stack:
+            v = stack.pop()
+            if v not in reach[a]:
+                reach[a].add(v)
+                stack.extend(succ[v])
+    return reach
+
+
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("k", [3, 4, 6])
+def test_nat_cuts_only_where_the_next_gate_overflows(seed, k):
+    """Nat (Sec. IV-B, reading R5): parts are runs of the natural gate order,
+    and each part ends only because the next gate would take its working
+    set above k."""
+    n = 8
+    g = _rand(n, 120, 2000 + seed)
+    pog = pt.partition(g, n, "nat", k)
+    run = [pog[0]]
+    for i in range(1, len(g)):
+        if pog[i] != pog[i - 1]:
+            assert pog[i] not in run, "a part is not one run of the gate order"
+            run.append(pog[i])
+            qs = {q for j in range(len(g)) if pog[j] == pog[i - 1] for q in g[j][1]}
+            assert len(qs | set(g[i][1])) > k, i
+
+
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("k", [3, 4, 6])
+def test_dagp_merge_phase_leaves_no_mergeable_neighbours(seed, k):
+    """dagP's merges (reading R7: the clustering of phase 1 and the merge
+    phase 3) run until no valid merge of two parts that share a qubit
+    remains: for every such pair, either the merged working set exceeds k
+    or a path through a third part joins them (merging would close a
+    cycle). Validity alone does not see a builder that stops merging early
+    (say at k - 1); this does."""
+    n = 8
+    g = _rand(n, 150, 3000 + seed)
+    pog = pt.partition(g, n, "dagp", k)
+    qs, succ = _part_graph(g, n, pog)
+    reach = _reach(succ)
+    P = len(qs)
+    for a in range(P):
+        for b in range(a + 1, P):
+            if not (qs[a] & qs[b]) or len(qs[a] | qs[b]) > k:
+                continue
+            via = any(b in reach[c] for c in succ[a]) or any(a in reach[c] for c in succ[b])
+            assert via, f"parts {a} and {b} could still merge (k={k})"
