@@ -324,3 +324,23 @@ def test_dagp_merge_phase_leaves_no_mergeable_neighbours(seed, k):
                 continue
             via = any(b in reach[c] for c in succ[a]) or any(a in reach[c] for c in succ[b])
             assert via, f"parts {a} and {b} could still merge (k={k})"
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("k", [3, 5])
+def test_builders_acyclic_by_an_independent_check(seed, k):
+    """Acyclicity and the working-set limit of every builder's partition
+    (Sec. IV-A), checked by the part graph built above from the gate list
+    alone (not the oracle's own checker): no part reaches itself, every
+    part has at most k qubits, and the schedule runs a part only after the
+    parts it depends on."""
+    n = 8
+    g = _rand(n, 120, 4000 + seed)
+    for m in ("nat", "dfs", "dagp", "beam"):
+        pog = pt.partition(g, n, m, k, seed=seed)
+        qs, succ = _part_graph(g, n, pog)
+        reach = _reach(succ)
+        assert all(a not in reach[a] for a in range(len(qs))), m
+        assert all(len(q) <= k for q in qs), m
+        # part ids are the schedule: every edge goes from an earlier part to a later one
+        assert all(b > a for a in range(len(qs)) for b in succ[a]), m
