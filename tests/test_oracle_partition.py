@@ -344,3 +344,47 @@ def test_builders_acyclic_by_an_independent_check(seed, k):
         assert all(len(q) <= k for q in qs), m
         # part ids are the schedule: every edge goes from an earlier part to a later one
         assert all(b > a for a in range(len(qs)) for b in succ[a]), m
+
+
+def _wire_preds(gates, n):
+    """For each gate, the gates just before it on its qubits (wire order)."""
+    last = [None] * n
+    preds = []
+    for i, (_, qubits, _) in enumerate(gates):
+        preds.append({last[q] for q in qubits if last[q] is not None})
+        for q in qubits:
+            last[q] = i
+    return preds
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_dfs_order_is_a_depth_first_topological_order(seed):
+    """The DFS builder's visiting order (Sec. IV-B, reading R6): every gate
+    once, after the gates before it on its qubits, and depth first — when a
+    gate makes successors ready, the next gate visited is one of them."""
+    n = 8
+    g = _rand(n, 120, 5000 + seed)
+    preds = _wire_preds(g, n)
+    dag = P.Dag(g, n)
+    order = P.dfs_order(dag, P._SplitMix64(seed))
+    assert sorted(order) == list(range(len(g)))
+    pos = {x: i for i, x in enumerate(order)}
+    assert all(pos[p] < pos[x] for x in range(len(g)) for p in preds[x])
+    done = set()
+    for i, x in enumerate(order[:-1]):
+        done.add(x)
+        ready_now = {s for s in range(len(g)) if s not in done and x in preds[s] and preds[s] <= done}
+        if ready_now:
+            assert order[i + 1] in ready_now, i
+
+
+def test_dfs_keeps_the_best_trial():
+    """DFS over r trials keeps the order with the fewest parts: more trials
+    never give more parts, and one trial equals the Nat cut of its order."""
+    n = 8
+    g = _rand(n, 150, 6000)
+    dag = P.Dag(g, n)
+    counts = [max(P.dfs(g, n, 4, seed=7, trials=t)) + 1 for t in (1, 2, 4, 16)]
+    assert counts == sorted(counts, reverse=True)
+    one = P.cut_order(dag, P.dfs_order(dag, P._SplitMix64(7)), 4)
+    assert counts[0] == len(one)
