@@ -177,3 +177,48 @@ def test_gloo_ranks_match_oracle(ws, n, k):
         assert pr.exitcode == 0
     assert err <= 1e-12, err
     assert stats["exchanges"] >= 1 and stats["parts"] >= 1
+
+
+def _dying_worker(rank, ws, port, q):
+    """Rank 1 fails in its first local step (before any exchange); rank 0
+    must get an error from its next all-to-all instead of waiting forever."""
+    import datetime
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws, timeout=datetime.timedelta(seconds=10))
+    n, k = 10, 6
+    g = _circuit(n, 3 * n + ws)
+    parts = _parts(g, n, k)
+    psi = _rand_state(n, 11 + ws)
+    l = n - 1
+    local = torch.from_numpy(psi[rank << l:(rank + 1) << l].copy())
+
+    def step(sl, gates, nl):
+        if rank == 1:
+            raise RuntimeError("injected failure of rank 1")
+        return torch.from_numpy(sim.run(nl, gates, sl.numpy()))
+    try:
+        D.ShardedState(n, local, rank, ws, local_apply=step).run(g, parts)
+        q.put((rank, "finished"))
+    except Exception as e:   # rank 1: the injected failure; rank 0: the failed collective
+        q.put((rank, type(e).__name__ + ": " + str(e)[:200]))
+    # no destroy_process_group: the peer is gone
+
+
+def test_rank_failure_is_reported_not_hung():
+    """A rank that dies between steps (a host-side failure, no GPU involved)
+    is seen by the other rank as an error of its next exchange, within the
+    process group's timeout."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    got = dict(q.get(timeout=120) for _ in range(2))
+    for pr in procs:
+        pr.join(timeout=60)
+        if pr.is_alive():
+            pr.kill()
+    assert got[1].startswith("RuntimeError: injected failure"), got
+    assert got[0] != "finished", got
