@@ -331,7 +331,7 @@ sv_status sv_plan_export_inner(const sv_plan *p, uint32_t *inner, size_t n_gates
 sv_status sv_plan_export(const sv_plan *p, uint32_t *pog, size_t n_gates, uint32_t *n_parts) {
     if (!p) return fail(SV_ERR_ARG, "plan is NULL");
     if (n_gates != p->gates.size()) return fail(SV_ERR_ARG, "n_gates does not match the plan");
-    if (pog) std::memcpy(pog, p->pog.data(), sizeof(uint32_t) * n_gates);
+    if (pog && n_gates) std::memcpy(pog, p->pog.data(), sizeof(uint32_t) * n_gates);
     if (n_parts) *n_parts = p->n_parts;
     return SV_OK;
 }

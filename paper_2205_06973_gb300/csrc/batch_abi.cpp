@@ -380,11 +380,15 @@ static sv_status build_program(sv_batch *b) {
     }
     b->d_prog = d;
     std::vector<char> host(s_items + s_parts + s_ph + s_op + s_cf, 0);
-    std::memcpy(host.data(), items.data(), items.size() * sizeof(BatchItem));
-    std::memcpy(host.data() + s_items, parts.data(), parts.size() * sizeof(PartLaunch));
-    std::memcpy(host.data() + s_items + s_parts, phases.data(), phases.size() * sizeof(Phase));
-    std::memcpy(host.data() + s_items + s_parts + s_ph, ops.data(), ops.size() * sizeof(Op));
-    std::memcpy(host.data() + s_items + s_parts + s_ph + s_op, coefs.data(), coefs.size() * sizeof(float));
+    // (an empty vector's data() may be null, which memcpy must not get)
+    auto put = [&](size_t at, const void *src, size_t bytes) {
+        if (bytes) std::memcpy(host.data() + at, src, bytes);
+    };
+    put(0, items.data(), items.size() * sizeof(BatchItem));
+    put(s_items, parts.data(), parts.size() * sizeof(PartLaunch));
+    put(s_items + s_parts, phases.data(), phases.size() * sizeof(Phase));
+    put(s_items + s_parts + s_ph, ops.data(), ops.size() * sizeof(Op));
+    put(s_items + s_parts + s_ph + s_op, coefs.data(), coefs.size() * sizeof(float));
     BCUDA(cudaMemcpyAsync(d, host.data(), host.size(), cudaMemcpyHostToDevice, b->prep));
     // every upload (gate lists, dense items, parts and R images) is complete
     // before the graph can be launched on any stream
@@ -504,7 +508,7 @@ sv_status sv_batch_probs(sv_batch *b, void *dev_out, double *norms_host) {
         BCUDA(cudaMemcpyAsync(b->h_norms.data(), b->d_norms, sizeof(double) * b->n, cudaMemcpyDeviceToHost,
                               b->stream));
         BCUDA(cudaStreamSynchronize(b->stream));
-        std::memcpy(norms_host, b->h_norms.data(), sizeof(double) * b->n);
+        if (b->n) std::memcpy(norms_host, b->h_norms.data(), sizeof(double) * b->n);
     }
     return SV_OK;
 }
